@@ -1,0 +1,141 @@
+/* rbffd.h -- C ABI of the GB300 library that forms the sparse Laplacian differentiation
+ * matrix L of the overlapped RBF-FD method (V. Shankar, "The Overlapped Radial Basis
+ * Function-Finite Difference (RBF-FD) Method: A Generalization of RBF-FD").
+ *
+ * The method (§4.1): every node x_k has a stencil P_k = x_k and its n-1 nearest
+ * neighbours.  Visiting nodes in index order, a node not yet given a row becomes a stencil
+ * center; its retention ball of radius (1-delta) rho_k (rho_k = stencil width) selects
+ * the nodes whose Laplacian weights this one stencil computes: one factorization of the
+ * (n+M) x (n+M) block system [Phi P; P^T 0] (polyharmonic spline r^m, monomials of total
+ * degree <= ell, M of them) and one solve per retained node.  §4.2.1 keeps a retained
+ * node only if its local L-Lebesgue value ||w||_1 does not exceed that of the center.
+ * Rows are never recomputed by a later stencil.  The result is CSR.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 on success or a negative RBFFD_E* code; nothing throws, traps or exits.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is enqueued on it; device outputs are valid once the stream has completed.
+ *   - Device pointers are plain CUDA device (or managed) pointers on the current device.
+ *   - Nodes are row-major [N][d] FP64; all indices are 0-based int32.
+ *   - One plan may be used by one host thread at a time; distinct plans may run
+ *     concurrently on distinct streams.
+ */
+#ifndef RBFFD_H
+#define RBFFD_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ error codes */
+#define RBFFD_OK 0
+#define RBFFD_EINVAL -1      /* bad argument (see each call) */
+#define RBFFD_EDUPLICATE -2  /* two nodes coincide: some stencil system is singular */
+#define RBFFD_ENOMEM -3      /* device allocation failed */
+#define RBFFD_ESINGULAR -4   /* an exactly zero pivot in some local system */
+#define RBFFD_ETIMEOUT -5    /* a bounded device-side wait ran out (work queue stalled) */
+#define RBFFD_ECUDA -6       /* a CUDA runtime call failed */
+#define RBFFD_ESTATE -7      /* call out of order (e.g. apply before assemble) */
+
+/* ------------------------------------------------------------------ options */
+#define RBFFD_STAB_SEQ 0      /* §4.2.1 test as printed; rejected nodes stay uncovered and are
+                                 reached later by the traversal (default) */
+#define RBFFD_STAB_OFF 1      /* no Lebesgue test: every retained node is kept */
+#define RBFFD_STAB_FALLBACK 2 /* coverage as OFF; a node failing the test gets its row from
+                                 its own delta = 1 stencil */
+
+typedef struct {
+    int stab_mode;      /* RBFFD_STAB_* */
+    int nodes_on_host;  /* 1: `nodes` is a host pointer, copied to the device by rbffd_plan */
+    int timeout_ms;     /* limit for any single device-side wait; <= 0 means 5000 */
+    int sync;           /* 1 (default): rbffd_assemble waits for the stream and reports device
+                           errors; 0: fully asynchronous, errors surface in rbffd_stats */
+} rbffd_opts;
+
+typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */
+
+/* CSR of L.  Device pointers owned by the plan; valid until the next rbffd_assemble on
+ * the same plan or rbffd_destroy.  Each row has n entries, columns ascending. */
+typedef struct {
+    int64_t n_rows;
+    int64_t nnz;
+    const int64_t* row_ptr; /* [n_rows + 1] */
+    const int32_t* col;     /* [nnz] */
+    const double* val;      /* [nnz] */
+} rbffd_csr;
+
+typedef struct {
+    int64_t n_nodes;        /* N */
+    int64_t n_centers;      /* N_delta: stencils factored for the final matrix */
+    int64_t n_fallback;     /* rows recomputed by their own delta = 1 stencil */
+    int64_t n_rejected;     /* retained nodes that failed the Lebesgue test at their
+                               final owner-candidate stencils (all solved columns) */
+    int64_t sum_cols;       /* right-hand sides solved in total */
+    int64_t max_ball;       /* largest retention ball (columns per stencil, upper bound) */
+    int64_t n_singular;     /* stencils with an exactly zero pivot */
+    int32_t status;         /* device status of the last assemble (RBFFD_OK or an error) */
+    int32_t n, M, K, d;     /* stencil size, monomials, n + M, dimension */
+    double alg_flops;       /* paper's cost model for the result: sum over centers of
+                               (2/3) K^3 + 2 K^2 q_k  (§4.3), q_k = rows the center kept */
+} rbffd_stats;
+
+/* rbffd_plan -- build the stencils of §4.1 for one node set.
+ *   nodes   [N][d] FP64, device pointer (or host if opts->nodes_on_host); copied, so the
+ *           caller may free it once the stream has completed.
+ *   N       number of nodes, n <= N <= 2^31 - 1.
+ *   d       2 or 3.
+ *   n       stencil size (x_k and its n-1 nearest neighbours by (squared distance,
+ *           index)), M <= n <= 128.
+ *   ell     degree of the appended polynomial (§2), 0 <= ell <= 8; M = C(ell+d, d).
+ *   m       PHS exponent, odd, 3 <= m <= 15.
+ *   delta   overlap parameter (§4.1), 0 < delta <= 1; delta = 1 is standard RBF-FD.
+ *   opts    NULL for defaults.
+ *   out     receives the plan.
+ * Runs the exact kNN search and the retention balls on the device and waits for the
+ * stream once (to size the local systems).  Errors: RBFFD_EINVAL, RBFFD_EDUPLICATE,
+ * RBFFD_ENOMEM, RBFFD_ECUDA.  On error *out is NULL and nothing leaks. */
+int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
+               const rbffd_opts* opts, void* stream, rbffd_plan_t* out);
+
+/* rbffd_assemble -- the traversal of §4.1 with the stabilization of §4.2.1: greedy center
+ * selection, one factorization per center, multi-right-hand-side solves, Lebesgue test
+ * and scatter into CSR (owned by the plan, described through *out, which may be NULL).
+ * With opts.sync = 1 it waits for the stream and returns RBFFD_ESINGULAR / RBFFD_ETIMEOUT
+ * from the device; the CSR pointers are valid either way once the stream completes. */
+int rbffd_assemble(rbffd_plan_t plan, void* stream, rbffd_csr* out);
+
+/* rbffd_apply -- y = L u (§5 use of L).  u [N], y [N]: FP64 device pointers owned by the
+ * caller; must not overlap.  RBFFD_ESTATE before the first assemble. */
+int rbffd_apply(rbffd_plan_t plan, const double* u, double* y, void* stream);
+
+/* rbffd_stats -- counters of the last plan/assemble (waits for nothing; values produced by
+ * an asynchronous assemble are complete once its stream has completed and a later call
+ * refreshed them: rbffd_stats itself synchronises the plan's last stream). */
+int rbffd_stats(rbffd_plan_t plan, rbffd_stats* out);
+
+/* rbffd_export -- copy L and the stencil ownership to host memory (tests, serving).
+ * row_ptr [N+1], col [N*n], val [N*n], owner [N] (stencil that produced each row;
+ * a FALLBACK row names itself).  Any pointer may be NULL to skip it.  Synchronous. */
+int rbffd_export(rbffd_plan_t plan, int64_t* row_ptr, int32_t* col, double* val,
+                 int32_t* owner);
+
+/* rbffd_export_stencils -- copy the kNN stencils to host memory: nbr [N][n] (nbr[k][0] ==
+ * k, ordered by (squared distance, index)), rho2 [N] (squared stencil width), ball_len [N]
+ * (retention-ball size; the ball is the prefix nbr[k][0..ball_len)).  NULL skips. */
+int rbffd_export_stencils(rbffd_plan_t plan, int32_t* nbr, double* rho2, int32_t* ball_len);
+
+/* rbffd_export_lambda -- scaled local Lebesgue value of every row under the stencil that
+ * produced it (§4.2.1), and is_center [N] (1 center, 2 fallback stencil, 0 otherwise). */
+int rbffd_export_lambda(rbffd_plan_t plan, double* lam_row, uint8_t* is_center);
+
+/* rbffd_destroy -- free the plan and everything it owns (waits for its last stream). */
+void rbffd_destroy(rbffd_plan_t plan);
+
+/* rbffd_strerror -- static description of an error code. */
+const char* rbffd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

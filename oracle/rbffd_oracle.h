@@ -1,0 +1,76 @@
+/* rbffd_oracle.h -- TEST INFRASTRUCTURE, not part of the library.
+ *
+ * A plain, slow, single-threaded CPU restatement in FP64 of the overlapped RBF-FD
+ * construction of the sparse Laplacian differentiation matrix (Shankar, "The Overlapped
+ * RBF-FD Method", §2 and §4.1-§4.2.1).  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the CUDA library never does.
+ *
+ * Every structural quantity (squared distances, retention radii, comparisons) is evaluated
+ * in a fixed left-to-right order with no fused multiply-add (compile with
+ * -ffp-contract=off), so the CUDA path can reproduce kNN tables and retention balls
+ * bit-for-bit.
+ */
+#ifndef RBFFD_ORACLE_H
+#define RBFFD_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_EDUPLICATE = -2, ORA_ENOMEM = -3, ORA_ESINGULAR = -4 };
+enum { ORA_OP_LAPLACIAN = 0, ORA_OP_IDENTITY = 1 };
+enum { ORA_STAB_SEQ = 0, ORA_STAB_OFF = 1, ORA_STAB_FALLBACK = 2 };
+
+typedef struct {
+    int64_t n_centers;      /* N_delta: stencils whose weights were kept (fallback stencils excluded) */
+    int64_t n_fallback;     /* rows recomputed by their own delta=1 stencil (FALLBACK mode) */
+    int64_t n_decisions;    /* Lebesgue tests made for non-center retained nodes */
+    int64_t n_rejected;     /* of which failed  Lambda_i <= Lambda_center */
+    int64_t n_near_tie;     /* of which |margin| <= 1e-9 */
+    int64_t sum_q;          /* rows written by centers (== N in SEQ/OFF) */
+    int64_t sum_cols;       /* right-hand sides solved in total */
+    double min_abs_margin;  /* min over decisions of |(L_c - L_i) / L_c| (inf if none) */
+} ora_stats;
+
+/* Degree rule of §2: 2D closed form s = floor((sqrt(4n+1)-3)/2); 3D: largest s with
+ * C(s+3,3) <= n/2.  Returns s, and the number of monomials M through *M_out. */
+int ora_degree_for_n(int n, int d, int* M_out);
+
+/* Number of total-degree-<=ell monomials in d dimensions, and their exponents in graded
+ * order (degree 0,1,...,ell; within a degree the first exponent descending, then the
+ * second).  exps has room for M*d ints (may be NULL). */
+int ora_poly_terms(int d, int ell, int* exps);
+
+/* Brute-force exact kNN (§2, §4.1): for every node k the n nodes nearest to x_k ordered by
+ * (squared distance, index); nbr[k*n+0] == k.  d2[k*n+t] is the squared distance of the
+ * t-th neighbour.  Returns ORA_EDUPLICATE if some other node sits at distance 0. */
+int ora_knn(const double* X, int64_t N, int d, int n, int32_t* nbr, double* d2);
+
+/* Retention-ball sizes (§4.1): ball_len[k] = #{t : d2[k*n+t] <= ((1-delta)(1-delta)) rho_k^2},
+ * rho_k^2 = d2[k*n+n-1]; always >= 1. */
+int ora_ball_len(const double* d2, int64_t N, int n, double delta, int32_t* ball_len);
+
+/* One local system (§4.1, the block system of the augmented method and its overlapped
+ * multi-right-hand-side form): stencil nodes X[idx[0..n)] with idx[0] the center,
+ * PHS r^m plus monomials of degree <= ell, operator `op` evaluated at the q points
+ * Y[e*d..], e < q.  W[j*q+e] receives the weight of stencil node j for point e in the
+ * original (unscaled) coordinates; lam[e] (may be NULL) the local L-Lebesgue value
+ * sum_j |w| in the stencil's scaled coordinates. */
+int ora_local_weights(const double* X, int d, const int32_t* idx, int n, int ell, int m, int op,
+                      const double* Y, int q, double* W, double* lam);
+
+/* Full sequential construction of L (§4.1 traversal in index order, §4.2.1 stabilization).
+ * Inputs: nodes X [N][d], the kNN table from ora_knn.  Outputs (all caller-allocated):
+ * CSR row_ptr[N+1], col[N*n], val[N*n] with columns ascending; owner[N] = stencil that
+ * produced each row; is_center[N] = 1 for centers, 2 for FALLBACK stencils, 0 otherwise;
+ * lam_row[N] (may be NULL) = scaled Lebesgue value of each row under its stencil. */
+int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, double delta, int mode,
+                 const int32_t* nbr, const double* d2, int64_t* row_ptr, int32_t* col,
+                 double* val, int32_t* owner, uint8_t* is_center, double* lam_row,
+                 ora_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,374 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: printed values of the
+paper (§2 degree rule), hand derivations (tests/golden), closed forms (5-point and 7-point
+Laplacians, Kronecker property), an independent 40-digit solve built with sympy/mpmath from
+the definitions of §4.1, library routines (numpy sorting for kNN), exact invariances, and
+convergence of L f to the Laplacian of f.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1606_03135_gb300 import nodesets as NS
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng_points(N, d, seed):
+    return NS.uniform(seed, N * d).reshape(N, d)
+
+
+# ------------------------------------------------------------------ §2 degree rule
+def test_degree_rule_matches_paper_examples():
+    g = json.load(open(os.path.join(GOLDEN, "degree_rule.json")))
+    for c in g["cases"]:
+        assert O.degree_for_n(c["n"], c["d"]) == (c["s"], c["M"])
+
+
+def test_degree_rule_is_largest_fitting_degree():
+    for d in (2, 3):
+        for n in range(2, 400):
+            s, M = O.degree_for_n(n, d)
+            assert M == math.comb(s + d, d)
+            assert 2 * math.comb(s + d, d) <= n < 2 * math.comb(s + 1 + d, d)
+
+
+def test_poly_terms_span_all_monomials_in_graded_order():
+    for d in (2, 3):
+        for ell in range(0, 7):
+            e = O.poly_terms(d, ell)
+            want = {a for a in itertools.product(range(ell + 1), repeat=d) if sum(a) <= ell}
+            assert len(e) == math.comb(ell + d, d) == len(want)
+            assert {tuple(r) for r in e} == want
+            deg = e.sum(axis=1)
+            assert np.all(np.diff(deg) >= 0)
+
+
+# ------------------------------------------------------------------ kNN (§2, §4.1)
+def _knn_numpy(X, n):
+    N, d = X.shape
+    nbr = np.zeros((N, n), np.int32)
+    d2 = np.zeros((N, n))
+    for k in range(N):
+        diff = X[k][None, :] - X
+        s = diff[:, 0] * diff[:, 0]
+        s = s + diff[:, 1] * diff[:, 1]
+        if d == 3:
+            s = s + diff[:, 2] * diff[:, 2]
+        order = np.lexsort((np.arange(N), s))[:n]
+        nbr[k] = order
+        d2[k] = s[order]
+    return nbr, d2
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_knn_matches_numpy_sort_with_exact_ties(d):
+    # an integer lattice has many exactly equal distances: the (d2, index) order decides
+    side = 9 if d == 2 else 5
+    P = np.array(list(itertools.product(range(side), repeat=d)), dtype=np.float64)
+    P = P[NS.permutation(5, P.shape[0])]
+    for n in (1, 5, 13, 27):
+        nbr, d2 = O.knn(P, n)
+        nb2, d22 = _knn_numpy(P, n)
+        assert np.array_equal(nbr, nb2)
+        assert np.array_equal(d2, d22)
+        assert np.all(nbr[:, 0] == np.arange(P.shape[0]))
+
+
+def test_knn_random_matches_numpy():
+    X = _rng_points(700, 2, 11)
+    nbr, d2 = O.knn(X, 17)
+    nb2, d22 = _knn_numpy(X, 17)
+    assert np.array_equal(nbr, nb2) and np.array_equal(d2, d22)
+
+
+def test_knn_duplicate_is_an_error():
+    X = _rng_points(50, 2, 3)
+    X[31] = X[7]
+    with pytest.raises(O.OracleError) as e:
+        O.knn(X, 5)
+    assert e.value.code == O.EDUPLICATE
+
+
+# ------------------------------------------------------------------ retention balls (§4.1)
+def test_ball_len_special_cases_and_definition():
+    X = NS.disk2d(500, seed=9)
+    nbr, d2 = O.knn(X, 12)
+    assert np.all(O.ball_len(d2, 1.0) == 1)  # delta = 1: the ball is the center alone
+    assert np.all(O.ball_len(d2, 1e-17) == 12)  # (1-delta) rounds to 1: the whole stencil
+    for delta in (0.2, 0.5, 0.75):
+        f = (1.0 - delta) * (1.0 - delta)
+        want = (d2 <= (f * d2[:, -1])[:, None]).sum(axis=1)
+        assert np.array_equal(O.ball_len(d2, delta), want)
+    with pytest.raises(O.OracleError):
+        O.ball_len(d2, 0.0)
+
+
+# ------------------------------------------------------------------ local system (§4.1)
+def test_five_point_laplacian_is_recovered_when_n_equals_M():
+    # n = M = 6 (ell = 2): P is square, the weights are those of quadratic interpolation,
+    # which on {0, +-h e1, +-h e2, (h,h)} is the 5-point Laplacian.
+    for h in (1.0, 0.125, 3e-3):
+        X = np.array([[0, 0], [h, 0], [-h, 0], [0, h], [0, -h], [h, h]], dtype=np.float64) + 0.3
+        W, _ = O.local_weights(X, np.arange(6), 2, 3, X[:1])
+        np.testing.assert_allclose(W[:, 0] * h * h, [-4, 1, 1, 1, 1, 0], atol=1e-11)
+
+
+def test_seven_point_laplacian_3d_when_n_equals_M():
+    h = 0.5
+    pts = [[0, 0, 0], [h, 0, 0], [-h, 0, 0], [0, h, 0], [0, -h, 0], [0, 0, h], [0, 0, -h],
+           [h, h, 0], [h, 0, h], [0, h, h]]
+    X = np.array(pts, dtype=np.float64) - 0.2
+    W, _ = O.local_weights(X, np.arange(10), 2, 5, X[:1])
+    np.testing.assert_allclose(W[:, 0] * h * h, [-6, 1, 1, 1, 1, 1, 1, 0, 0, 0], atol=1e-11)
+
+
+def _mp_weights(X, idx, ell, m, Y, dps=40):
+    """Independent high-precision weights from the definitions of §4.1, in the ORIGINAL
+    coordinates with raw monomials x^a y^b (z^c); Laplacians by sympy differentiation."""
+    import mpmath as mp
+    import sympy as sp
+    mp.mp.dps = dps
+    d = X.shape[1]
+    syms = sp.symbols("x0:%d" % d)
+    cs = sp.symbols("c0:%d" % d)
+    r = sp.sqrt(sum((s - c) ** 2 for s, c in zip(syms, cs)))
+    lap = lambda f: sum(sp.diff(f, s, 2) for s in syms)
+    phi = r ** m
+    lphi = sp.simplify(lap(phi))
+    f_lphi = sp.lambdify(syms + cs, lphi, "mpmath")
+    exps = [a for g in range(ell + 1) for a in itertools.product(range(g + 1), repeat=d)
+            if sum(a) == g]
+    monos = [sp.Mul(*[s ** a for s, a in zip(syms, al)]) for al in exps]
+    f_mono = [sp.lambdify(syms, p, "mpmath") for p in monos]
+    f_lmono = [sp.lambdify(syms, lap(p), "mpmath") for p in monos]
+    n, M = len(idx), len(monos)
+    K = n + M
+    P = [[mp.mpf(float(v)) for v in X[i]] for i in idx]
+    A = mp.zeros(K, K)
+    for a in range(n):
+        for b in range(n):
+            A[a, b] = mp.sqrt(sum((P[a][t] - P[b][t]) ** 2 for t in range(d))) ** m
+        for l in range(M):
+            A[a, n + l] = f_mono[l](*P[a])
+            A[n + l, a] = A[a, n + l]
+    out = []
+    for y in Y:
+        yy = [mp.mpf(float(v)) for v in y]
+        b = mp.zeros(K, 1)
+        for a in range(n):
+            same = all(yy[t] == P[a][t] for t in range(d))
+            b[a] = 0 if same else f_lphi(*(yy + P[a]))
+        for l in range(M):
+            b[n + l] = f_lmono[l](*yy)
+        x = mp.lu_solve(A, b)
+        out.append([float(x[j]) for j in range(n)])
+    return np.array(out).T
+
+
+@pytest.mark.parametrize("d,n,ell,m,seed", [(2, 8, 1, 3, 1), (2, 10, 2, 5, 2), (3, 12, 1, 3, 3),
+                                            (3, 14, 2, 7, 4), (2, 15, 3, 7, 5)])
+def test_local_weights_match_independent_40_digit_solve(d, n, ell, m, seed):
+    X = 0.05 * _rng_points(n, d, seed) + 0.4
+    idx = np.arange(n)
+    Y = X[[0, 1, n // 2]]
+    W, _ = O.local_weights(X, idx, ell, m, Y)
+    Wmp = _mp_weights(X, idx, ell, m, Y)
+    for e in range(Y.shape[0]):
+        scale = np.abs(Wmp[:, e]).max()
+        assert np.abs(W[:, e] - Wmp[:, e]).max() <= 1e-9 * scale
+
+
+@pytest.mark.parametrize("d,n,ell,m", [(2, 31, 4, 7), (3, 45, 3, 7), (2, 12, 2, 3)])
+def test_polynomial_reproduction(d, n, ell, m):
+    # the augmented system reproduces every polynomial of degree <= ell exactly (§2, §4.1)
+    X = NS.jittered_grid(14 if d == 2 else 7, d, seed=3)
+    nbr, _ = O.knn(X, n)
+    rng_k = [5, 77, 150]
+    for k in rng_k:
+        idx = nbr[k]
+        Y = X[idx[:6]]
+        W, _ = O.local_weights(X, idx, ell, m, Y)
+        c = X[k] + 0.01
+        for al in itertools.product(range(ell + 1), repeat=d):
+            if sum(al) > ell:
+                continue
+            pv = np.prod((X[idx] - c) ** np.array(al), axis=1)
+            for e in range(Y.shape[0]):
+                y = Y[e] - c
+                lap = 0.0
+                for a in range(d):
+                    if al[a] >= 2:
+                        t = al[a] * (al[a] - 1)
+                        for b in range(d):
+                            t *= y[b] ** (al[b] - 2 if b == a else al[b])
+                        lap += t
+                got = W[:, e] @ pv
+                scale = np.abs(W[:, e]) @ np.abs(pv) + abs(lap) + 1e-300
+                assert abs(got - lap) <= 1e-10 * scale
+
+
+def test_identity_operator_has_kronecker_property_and_lebesgue_at_least_one():
+    # interpolation Lagrange functions (§4.2.1): l_j(x_i) = delta_ij, sum_j l_j = 1,
+    # hence Lambda = sum_j |l_j| >= 1 everywhere and == 1 at the nodes.
+    X = NS.jittered_grid(12, 2, seed=4)
+    nbr, _ = O.knn(X, 21)
+    idx = nbr[40]
+    W, lam = O.local_weights(X, idx, 3, 5, X[idx], op=O.OP_IDENTITY)
+    np.testing.assert_allclose(W, np.eye(21), atol=1e-10)
+    np.testing.assert_allclose(lam, 1.0, atol=1e-10)
+    lo, hi = X[idx].min(axis=0), X[idx].max(axis=0)
+    Y = lo + (hi - lo) * NS.uniform(8, 60).reshape(30, 2)
+    W, lam = O.local_weights(X, idx, 3, 5, Y, op=O.OP_IDENTITY)
+    np.testing.assert_allclose(W.sum(axis=0), 1.0, atol=1e-10)
+    assert np.all(lam >= 1.0 - 1e-10)
+
+
+def test_laplacian_lebesgue_lower_bound():
+    # p(xi) = |xi - xi_R|^2 has Laplacian 2d and is reproduced (ell >= 2), so in scaled
+    # units Lambda(x_R) >= 2d / max_j |xi_j - xi_R|^2.
+    for d, side, n, ell in ((2, 14, 31, 4), (3, 7, 45, 3)):
+        X = NS.jittered_grid(side, d, seed=6)
+        nbr, d2 = O.knn(X, n)
+        for k in (3, 50, 150):
+            idx = nbr[k]
+            W, lam = O.local_weights(X, idx, ell, 7, X[idx[:8]])
+            rho = math.sqrt(d2[k, -1])
+            for e in range(8):
+                far = (((X[idx] - X[idx[e]]) / rho) ** 2).sum(axis=1).max()
+                assert lam[e] >= 2 * d / far * (1 - 1e-12)
+
+
+# ------------------------------------------------------------------ traversal (§4.1, §4.2.1)
+def test_hand_derived_traversal_line8():
+    g = json.load(open(os.path.join(GOLDEN, "line8_off.json")))
+    X = np.array([[k, 0.001 * (k % 2)] for k in range(8)], dtype=np.float64)
+    r = O.assemble(X, g["n"], g["ell"], g["m"], g["delta"], mode=O.STAB_OFF)
+    assert np.array_equal(r["nbr"], np.array(g["nbr"]))
+    assert np.array_equal(O.ball_len(r["d2"], g["delta"]), g["ball_len"])
+    assert np.array_equal(np.flatnonzero(r["is_center"] == 1), g["centers"])
+    assert np.array_equal(r["owner"], g["owner"])
+
+
+def _acc(X, nbr, bl, j, ell, m):
+    idx = nbr[j]
+    W, lam = O.local_weights(X, idx, ell, m, X[idx[:bl[j]]])
+    return W, lam, lam <= lam[0]
+
+
+@pytest.mark.parametrize("mode", [O.STAB_SEQ, O.STAB_OFF, O.STAB_FALLBACK])
+@pytest.mark.parametrize("delta", [0.25, 0.5, 0.8])
+def test_traversal_satisfies_its_unique_characterisation(mode, delta):
+    # The index-order traversal is the unique assignment in which node k is a center iff no
+    # earlier center keeps it, and each kept row belongs to the earliest center keeping it.
+    X = NS.disk2d(300, seed=21)
+    n, ell, m = 12, 2, 3
+    r = O.assemble(X, n, ell, m, delta, mode=mode)
+    nbr, d2 = r["nbr"], r["d2"]
+    bl = O.ball_len(d2, delta)
+    N = X.shape[0]
+    centers = np.flatnonzero(r["is_center"] == 1)
+    acc = {j: _acc(X, nbr, bl, j, ell, m) for j in centers}
+    keep = lambda j, t: bool(acc[j][2][t]) if mode == O.STAB_SEQ else True
+    first = np.full(N, -1)
+    for j in centers:  # ascending
+        for t in range(bl[j]):
+            i = nbr[j, t]
+            if i >= j and keep(j, t) and first[i] < 0:
+                first[i] = j
+    for k in range(N):
+        earlier = [j for j in centers if j < k and k in nbr[j, :bl[j]] and
+                   keep(j, int(np.flatnonzero(nbr[j, :bl[j]] == k)[0]))]
+        assert (r["is_center"][k] == 1) == (len(earlier) == 0)
+    n_fb = 0
+    for i in range(N):
+        j = first[i]
+        assert j >= 0
+        t = int(np.flatnonzero(nbr[j] == i)[0])
+        W, lam, ok = acc[j]
+        if mode == O.STAB_FALLBACK and not ok[t]:
+            n_fb += 1
+            assert r["owner"][i] == i and r["is_center"][i] == 2
+            Wf, _ = O.local_weights(X, nbr[i], ell, m, X[i:i + 1])
+            src_cols, src_w = nbr[i], Wf[:, 0]
+        else:
+            assert r["owner"][i] == j
+            src_cols, src_w = nbr[j], W[:, t]
+        o = np.argsort(src_cols)
+        sl = slice(r["row_ptr"][i], r["row_ptr"][i + 1])
+        assert np.array_equal(r["col"][sl], src_cols[o])
+        assert np.array_equal(r["val"][sl], src_w[o])
+    assert r["stats"]["n_fallback"] == n_fb
+
+
+def test_delta_one_is_standard_rbffd():
+    X = NS.disk2d(400, seed=5)
+    r = O.assemble(X, 12, 2, 3, 1.0)
+    assert np.all(r["is_center"] == 1) and np.array_equal(r["owner"], np.arange(400))
+    assert r["stats"]["n_centers"] == 400 and r["stats"]["n_decisions"] == 0
+
+
+def test_stabilization_is_active_on_small_stencils():
+    X = NS.disk2d(2000, seed=1)
+    nbr, d2 = O.knn(X, 12)
+    seq = O.assemble(X, 12, 2, 3, 0.5, O.STAB_SEQ, nbr, d2)
+    off = O.assemble(X, 12, 2, 3, 0.5, O.STAB_OFF, nbr, d2)
+    assert seq["stats"]["n_rejected"] > 0
+    assert seq["stats"]["n_centers"] > off["stats"]["n_centers"]
+    assert off["stats"]["n_centers"] < 2000
+
+
+def test_power_of_two_scaling_is_exact():
+    X = NS.disk2d(500, seed=12)
+    a = O.assemble(X, 12, 2, 3, 0.5)
+    b = O.assemble(X * 2.0, 12, 2, 3, 0.5)
+    assert np.array_equal(a["owner"], b["owner"]) and np.array_equal(a["col"], b["col"])
+    assert np.array_equal(a["val"], b["val"] * 4.0)
+
+
+def test_translation_invariance():
+    X = NS.disk2d(500, seed=13)
+    a = O.assemble(X, 12, 2, 3, 0.5)
+    b = O.assemble(X + np.array([0.375, -0.25]), 12, 2, 3, 0.5)
+    assert np.array_equal(a["owner"], b["owner"]) and np.array_equal(a["col"], b["col"])
+    for i in range(500):
+        sl = slice(i * 12, (i + 1) * 12)
+        assert np.abs(a["val"][sl] - b["val"][sl]).max() <= 1e-9 * np.abs(a["val"][sl]).max()
+
+
+# ------------------------------------------------------------------ accuracy (§7)
+def _interior_error(X, r, f, lapf, margin):
+    y = O.csr_matvec(r["row_ptr"], r["col"], r["val"], f(X))
+    inner = np.all((X > margin) & (X < 1 - margin), axis=1)
+    return np.abs(y - lapf(X))[inner].max()
+
+
+@pytest.mark.parametrize("delta,mode", [(1.0, O.STAB_SEQ), (0.5, O.STAB_SEQ)])
+def test_laplacian_converges_2d(delta, mode):
+    f = lambda P: np.sin(np.pi * P[:, 0]) * np.cos(np.pi * P[:, 1])
+    lapf = lambda P: -2 * np.pi ** 2 * f(P)
+    errs = []
+    for side in (20, 40):
+        X = NS.jittered_grid(side, 2, amp=0.2, seed=31)
+        r = O.assemble(X, 31, 4, 7, delta, mode)
+        errs.append(_interior_error(X, r, f, lapf, 0.2))
+    order = math.log2(errs[0] / errs[1])
+    assert order > 2.3, (errs, order)  # ell = 4: expected order about ell - 1 = 3
+
+
+def test_laplacian_converges_3d():
+    f = lambda P: np.sin(np.pi * P[:, 0]) * np.cos(np.pi * P[:, 1]) * np.sin(np.pi * P[:, 2])
+    lapf = lambda P: -3 * np.pi ** 2 * f(P)
+    errs = []
+    for side in (9, 18):
+        X = NS.jittered_grid(side, 3, amp=0.2, seed=32)
+        r = O.assemble(X, 45, 3, 7, 0.6)
+        errs.append(_interior_error(X, r, f, lapf, 0.25))
+    order = math.log2(errs[0] / errs[1])
+    assert order > 1.5, (errs, order)  # ell = 3: expected order about 2
