@@ -51,6 +51,8 @@ typedef struct {
     int timeout_ms;     /* limit for any single device-side wait; <= 0 means 5000 */
     int sync;           /* 1 (default): rbffd_assemble waits for the stream and reports device
                            errors; 0: fully asynchronous, errors surface in rbffd_stats */
+    int fault_inject;   /* tests only: 1 = seed no work, so every traversal wait runs out and
+                           rbffd_assemble returns RBFFD_ETIMEOUT after timeout_ms; 0 = off */
 } rbffd_opts;
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */
@@ -78,7 +80,12 @@ typedef struct {
     int32_t n, M, K, d;     /* stencil size, monomials, n + M, dimension */
     double alg_flops;       /* paper's cost model for the result: sum over centers of
                                (2/3) K^3 + 2 K^2 q_k  (§4.3), q_k = rows the center kept */
-} rbffd_stats;
+    int64_t n_launches;     /* kernels this plan has launched so far (cumulative) */
+    float ms_stencils;      /* device time of the kNN/retention-ball phase of rbffd_plan */
+    float ms_traversal;     /* device time of the traversal + local-solve kernel */
+    float ms_fallback;      /* device time of the FALLBACK re-solves (0 otherwise) */
+    float ms_finalize;      /* device time of the CSR scatter */
+} rbffd_stats_t;
 
 /* rbffd_plan -- build the stencils of §4.1 for one node set.
  *   nodes   [N][d] FP64, device pointer (or host if opts->nodes_on_host); copied, so the
@@ -112,7 +119,7 @@ int rbffd_apply(rbffd_plan_t plan, const double* u, double* y, void* stream);
 /* rbffd_stats -- counters of the last plan/assemble (waits for nothing; values produced by
  * an asynchronous assemble are complete once its stream has completed and a later call
  * refreshed them: rbffd_stats itself synchronises the plan's last stream). */
-int rbffd_stats(rbffd_plan_t plan, rbffd_stats* out);
+int rbffd_stats(rbffd_plan_t plan, rbffd_stats_t* out);
 
 /* rbffd_export -- copy L and the stencil ownership to host memory (tests, serving).
  * row_ptr [N+1], col [N*n], val [N*n], owner [N] (stencil that produced each row;

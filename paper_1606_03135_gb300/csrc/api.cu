@@ -1,0 +1,379 @@
+// api.cu -- the C ABI declared in include/rbffd.h: argument checks, device memory of a plan
+// (stream-ordered allocations), the launch sequence and error reporting.  No call throws,
+// traps, asserts or exits; every CUDA error becomes an RBFFD_* code.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "rbffd_internal.cuh"
+
+using namespace rbffd;
+
+struct rbffd_plan_s {
+    int64_t N = 0;
+    int d = 0, n = 0, ell = 0, m = 0, M = 0, K = 0;
+    double delta = 1.0;
+    rbffd_opts opts{};
+    int device = 0;
+    cudaStream_t last = nullptr;
+    // stencils
+    double* X = nullptr;
+    int* nbr = nullptr;
+    double* rho2 = nullptr;
+    int* ball_len = nullptr;
+    int* indeg = nullptr;
+    long long* slot_off = nullptr;
+    signed char* alpha = nullptr;
+    DevCounters* ctr = nullptr;
+    DevCounters* h_ctr = nullptr;  // pinned
+    long long* h_slots = nullptr;  // pinned
+    int max_ball = 0;
+    long long total_slots = 0;
+    int qcap = 0, stride = 0, wpb = 1;
+    // traversal and results
+    bool have_asm = false, assembled = false;
+    int* state = nullptr;
+    int* pending = nullptr;
+    int* owner = nullptr;
+    int* queue = nullptr;
+    unsigned char* fb_flag = nullptr;
+    int* fb_list = nullptr;
+    double* slot_w = nullptr;
+    double* slot_lam = nullptr;
+    unsigned char* slot_pass = nullptr;
+    long long* row_ptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;
+    double* lam_row = nullptr;
+    unsigned char* is_center = nullptr;
+    cudaEvent_t ev[8] = {};
+    int launches = 0;
+};
+
+namespace {
+
+int bad(cudaError_t e) {
+    if (e == cudaSuccess) return RBFFD_OK;
+    cudaGetLastError();  // clear a sticky-free error
+    return e == cudaErrorMemoryAllocation ? RBFFD_ENOMEM : RBFFD_ECUDA;
+}
+
+template <typename T>
+int alloc(T** p, size_t count, cudaStream_t s) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return bad(cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), s));
+}
+
+template <typename T>
+void release(T** p, cudaStream_t s) {
+    if (*p) cudaFreeAsync(*p, s);
+    *p = nullptr;
+}
+
+long long binom(int a, int b) {
+    if (b < 0 || b > a) return 0;
+    long long r = 1;
+    for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+    return r;
+}
+
+// exponents of the total-degree <= ell monomials in graded order: degree 0, 1, ..., ell;
+// within a degree the first exponent descending, then the second
+int monomial_table(int d, int ell, signed char* out) {
+    int M = 0;
+    for (int g = 0; g <= ell; ++g)
+        for (int a = g; a >= 0; --a) {
+            if (d == 2) {
+                if (out) { out[2 * M] = (signed char)a; out[2 * M + 1] = (signed char)(g - a); }
+                ++M;
+            } else {
+                for (int b = g - a; b >= 0; --b) {
+                    if (out) {
+                        out[3 * M] = (signed char)a;
+                        out[3 * M + 1] = (signed char)b;
+                        out[3 * M + 2] = (signed char)(g - a - b);
+                    }
+                    ++M;
+                }
+            }
+        }
+    return M;
+}
+
+void free_assemble(rbffd_plan_s* p, cudaStream_t s) {
+    release(&p->state, s); release(&p->pending, s); release(&p->owner, s);
+    release(&p->queue, s); release(&p->fb_flag, s); release(&p->fb_list, s);
+    release(&p->slot_w, s); release(&p->slot_lam, s); release(&p->slot_pass, s);
+    release(&p->row_ptr, s); release(&p->col, s); release(&p->val, s);
+    release(&p->lam_row, s); release(&p->is_center, s);
+    p->have_asm = false;
+    p->assembled = false;
+}
+
+void free_plan(rbffd_plan_s* p) {
+    if (!p) return;
+    cudaStream_t s = p->last;
+    if (s) cudaStreamSynchronize(s);
+    free_assemble(p, s);
+    release(&p->X, s); release(&p->nbr, s); release(&p->rho2, s); release(&p->ball_len, s);
+    release(&p->indeg, s); release(&p->slot_off, s); release(&p->alpha, s); release(&p->ctr, s);
+    cudaStreamSynchronize(s);
+    if (p->h_ctr) cudaFreeHost(p->h_ctr);
+    if (p->h_slots) cudaFreeHost(p->h_slots);
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+    delete p;
+}
+
+int max_optin_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rbffd_strerror(int code) {
+    switch (code) {
+        case RBFFD_OK: return "ok";
+        case RBFFD_EINVAL: return "invalid argument";
+        case RBFFD_EDUPLICATE: return "two nodes coincide (singular stencil)";
+        case RBFFD_ENOMEM: return "device allocation failed";
+        case RBFFD_ESINGULAR: return "exactly zero pivot in a local system";
+        case RBFFD_ETIMEOUT: return "a bounded device-side wait ran out";
+        case RBFFD_ECUDA: return "CUDA runtime error";
+        case RBFFD_ESTATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
+               const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
+    if (!out) return RBFFD_EINVAL;
+    *out = nullptr;
+    if (!nodes || (d != 2 && d != 3) || n < 1 || n > kMaxStencil || N < n || N > 0x7ffffffeLL ||
+        ell < 0 || ell > kMaxEll || m < 3 || m > 15 || (m % 2) == 0 || !(delta > 0.0) ||
+        !(delta <= 1.0))
+        return RBFFD_EINVAL;
+    const int M = (int)binom(ell + d, d);
+    if (M > n) return RBFFD_EINVAL;
+    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0};
+    if (opts) o = *opts;
+    if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1)
+        return RBFFD_EINVAL;
+    if (o.timeout_ms <= 0) o.timeout_ms = 5000;
+
+    rbffd_plan_s* p = new (std::nothrow) rbffd_plan_s();
+    if (!p) return RBFFD_ENOMEM;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    p->N = N; p->d = d; p->n = n; p->ell = ell; p->m = m; p->M = M; p->K = n + M;
+    p->delta = delta; p->opts = o; p->last = s;
+    cudaGetDevice(&p->device);
+    int rc = RBFFD_OK;
+    void* scratch = nullptr;
+    const int Ni = (int)N;
+    const int ncell_max = 2 * Ni + 64;
+    const size_t sbytes = grid_scratch_bytes(Ni, d, ncell_max);
+    signed char h_alpha[kMaxTerms * 3];
+    monomial_table(d, ell, h_alpha);
+    for (auto& e : p->ev)
+        if ((rc = bad(cudaEventCreate(&e))) != RBFFD_OK) goto fail;
+    if ((rc = bad(cudaMallocHost(reinterpret_cast<void**>(&p->h_ctr), sizeof(DevCounters)))) ||
+        (rc = bad(cudaMallocHost(reinterpret_cast<void**>(&p->h_slots), sizeof(long long)))))
+        goto fail;
+    if ((rc = alloc(&p->X, (size_t)N * d, s)) || (rc = alloc(&p->nbr, (size_t)N * n, s)) ||
+        (rc = alloc(&p->rho2, (size_t)N, s)) || (rc = alloc(&p->ball_len, (size_t)N, s)) ||
+        (rc = alloc(&p->indeg, (size_t)N, s)) || (rc = alloc(&p->slot_off, (size_t)N + 1, s)) ||
+        (rc = alloc(&p->alpha, (size_t)M * d, s)) || (rc = alloc(&p->ctr, 1, s)))
+        goto fail;
+    if ((rc = bad(cudaMallocAsync(&scratch, sbytes, s)))) goto fail;
+    if ((rc = bad(cudaMemcpyAsync(p->X, nodes, (size_t)N * d * sizeof(double),
+                                  o.nodes_on_host ? cudaMemcpyHostToDevice
+                                                  : cudaMemcpyDeviceToDevice,
+                                  s))))
+        goto fail;
+    if ((rc = bad(cudaMemcpyAsync(p->alpha, h_alpha, (size_t)M * d, cudaMemcpyHostToDevice, s))) ||
+        (rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s))))
+        goto fail;
+    cudaEventRecord(p->ev[0], s);
+    rc = launch_grid_and_knn(d, p->X, Ni, n, (1.0 - delta) * (1.0 - delta), scratch, sbytes,
+                             ncell_max, p->nbr, p->rho2, p->ball_len, p->indeg, p->ctr, s,
+                             &p->launches);
+    if (rc) goto fail;
+    rc = launch_scan_i32_to_i64(p->ball_len, p->slot_off, Ni, s, &p->launches);
+    if (rc) goto fail;
+    cudaEventRecord(p->ev[1], s);
+    if ((rc = bad(cudaMemcpyAsync(p->h_ctr, p->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                  s))) ||
+        (rc = bad(cudaMemcpyAsync(p->h_slots, p->slot_off + N, sizeof(long long),
+                                  cudaMemcpyDeviceToHost, s))))
+        goto fail;
+    cudaFreeAsync(scratch, s);
+    scratch = nullptr;
+    if ((rc = bad(cudaStreamSynchronize(s)))) goto fail;
+    if (p->h_ctr->status) { rc = p->h_ctr->status; goto fail; }
+    p->max_ball = p->h_ctr->max_ball;
+    p->total_slots = *p->h_slots;
+    p->qcap = p->max_ball < 1 ? 1 : p->max_ball;
+    {
+        int stride = 0;
+        const size_t per_warp = solve_smem_per_warp(n, p->K, p->qcap, d, &stride);
+        const size_t avail = (size_t)max_optin_smem() - 64;
+        p->stride = stride;
+        if (per_warp > avail) { rc = RBFFD_EINVAL; goto fail; }
+        p->wpb = (2 * per_warp <= avail) ? 2 : 1;
+    }
+    *out = p;
+    return RBFFD_OK;
+fail:
+    if (scratch) cudaFreeAsync(scratch, s);
+    free_plan(p);
+    return rc;
+}
+
+int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
+    if (!p) return RBFFD_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    p->last = s;
+    const size_t N = (size_t)p->N, n = (size_t)p->n;
+    int rc = RBFFD_OK;
+    if (!p->have_asm) {
+        if ((rc = alloc(&p->state, N, s)) || (rc = alloc(&p->pending, N, s)) ||
+            (rc = alloc(&p->owner, N, s)) || (rc = alloc(&p->queue, N, s)) ||
+            (rc = alloc(&p->fb_flag, N, s)) || (rc = alloc(&p->fb_list, N, s)) ||
+            (rc = alloc(&p->slot_w, (size_t)p->total_slots * n, s)) ||
+            (rc = alloc(&p->slot_lam, (size_t)p->total_slots, s)) ||
+            (rc = alloc(&p->slot_pass, (size_t)p->total_slots, s)) ||
+            (rc = alloc(&p->row_ptr, N + 1, s)) || (rc = alloc(&p->col, N * n, s)) ||
+            (rc = alloc(&p->val, N * n, s)) || (rc = alloc(&p->lam_row, N, s)) ||
+            (rc = alloc(&p->is_center, N, s))) {
+            free_assemble(p, s);
+            return rc;
+        }
+        p->have_asm = true;
+    }
+    SolveArgs a{};
+    a.X = p->X; a.nbr = p->nbr; a.rho2 = p->rho2; a.ball_len = p->ball_len;
+    a.slot_off = p->slot_off; a.alpha = p->alpha;
+    a.N = (int)p->N; a.n = p->n; a.M = p->M; a.K = p->K; a.m = p->m; a.ell = p->ell;
+    a.qcap = p->qcap; a.stride = p->stride; a.mode = p->opts.stab_mode;
+    a.coef = (double)(p->m * (p->m + p->d - 2));
+    a.timeout_ns = (unsigned long long)p->opts.timeout_ms * 1000000ull;
+    a.state = p->state; a.pending = p->pending; a.owner = p->owner; a.queue = p->queue;
+    a.fb_flag = p->fb_flag; a.fb_list = p->fb_list;
+    a.slot_w = p->slot_w; a.slot_lam = p->slot_lam; a.slot_pass = p->slot_pass; a.ctr = p->ctr;
+    a.no_seed = p->opts.fault_inject == 1;
+    if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
+    rc = launch_traversal(p->d, a, p->indeg, p->wpb, s, &p->launches, p->ev[2], p->ev[3]);
+    if (rc) return rc;
+    cudaEventRecord(p->ev[4], s);
+    if (p->opts.stab_mode == RBFFD_STAB_FALLBACK) {
+        rc = launch_fallback(p->d, a, s, &p->launches);
+        if (rc) return rc;
+    }
+    cudaEventRecord(p->ev[5], s);
+    rc = launch_finalize(a, p->row_ptr, p->col, p->val, p->lam_row, p->is_center, s,
+                         &p->launches);
+    if (rc) return rc;
+    cudaEventRecord(p->ev[6], s);
+    if ((rc = bad(cudaMemcpyAsync(p->h_ctr, p->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                  s))))
+        return rc;
+    p->assembled = true;
+    if (out) {
+        out->n_rows = p->N;
+        out->nnz = p->N * p->n;
+        out->row_ptr = reinterpret_cast<const int64_t*>(p->row_ptr);
+        out->col = p->col;
+        out->val = p->val;
+    }
+    if (p->opts.sync) {
+        if ((rc = bad(cudaStreamSynchronize(s)))) return rc;
+        return p->h_ctr->status;
+    }
+    return RBFFD_OK;
+}
+
+int rbffd_apply(rbffd_plan_t p, const double* u, double* y, void* stream) {
+    if (!p || !u || !y) return RBFFD_EINVAL;
+    if (!p->assembled) return RBFFD_ESTATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return launch_spmv((int)p->N, p->n, p->row_ptr, p->col, p->val, u, y, s, &p->launches);
+}
+
+int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
+    if (!p || !out) return RBFFD_EINVAL;
+    int rc = bad(cudaStreamSynchronize(p->last));
+    if (rc) return rc;
+    memset(out, 0, sizeof(*out));
+    const DevCounters& c = *p->h_ctr;
+    out->n_nodes = p->N;
+    out->max_ball = p->max_ball;
+    out->n = p->n; out->M = p->M; out->K = p->K; out->d = p->d;
+    out->n_launches = p->launches;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) out->ms_stencils = ms;
+    if (p->assembled) {
+        out->n_centers = (int64_t)c.n_centers;
+        out->n_fallback = (int64_t)c.n_fallback;
+        out->n_rejected = (int64_t)c.n_rejected;
+        out->sum_cols = (int64_t)c.sum_cols;
+        out->n_singular = c.n_singular;
+        out->status = c.status;
+        const double K = p->K;
+        const double lu = 2.0 / 3.0 * K * K * K, col = 2.0 * K * K;
+        out->alg_flops = (double)c.n_centers * lu + (double)(p->N - (int64_t)c.n_fallback) * col +
+                         (double)c.n_fallback * (lu + col);
+        if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) out->ms_traversal = ms;
+        if (cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) out->ms_fallback = ms;
+        if (cudaEventElapsedTime(&ms, p->ev[5], p->ev[6]) == cudaSuccess) out->ms_finalize = ms;
+    }
+    cudaGetLastError();
+    return RBFFD_OK;
+}
+
+int rbffd_export(rbffd_plan_t p, int64_t* row_ptr, int32_t* col, double* val, int32_t* owner) {
+    if (!p) return RBFFD_EINVAL;
+    if (!p->assembled) return RBFFD_ESTATE;
+    cudaStream_t s = p->last;
+    const size_t N = (size_t)p->N, n = (size_t)p->n;
+    int rc = RBFFD_OK;
+    if (row_ptr && (rc = bad(cudaMemcpyAsync(row_ptr, p->row_ptr, (N + 1) * 8, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (col && (rc = bad(cudaMemcpyAsync(col, p->col, N * n * 4, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (val && (rc = bad(cudaMemcpyAsync(val, p->val, N * n * 8, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (owner && (rc = bad(cudaMemcpyAsync(owner, p->owner, N * 4, cudaMemcpyDeviceToHost, s)))) return rc;
+    return bad(cudaStreamSynchronize(s));
+}
+
+int rbffd_export_stencils(rbffd_plan_t p, int32_t* nbr, double* rho2, int32_t* ball_len) {
+    if (!p) return RBFFD_EINVAL;
+    cudaStream_t s = p->last;
+    const size_t N = (size_t)p->N, n = (size_t)p->n;
+    int rc = RBFFD_OK;
+    if (nbr && (rc = bad(cudaMemcpyAsync(nbr, p->nbr, N * n * 4, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (rho2 && (rc = bad(cudaMemcpyAsync(rho2, p->rho2, N * 8, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (ball_len && (rc = bad(cudaMemcpyAsync(ball_len, p->ball_len, N * 4, cudaMemcpyDeviceToHost, s)))) return rc;
+    return bad(cudaStreamSynchronize(s));
+}
+
+int rbffd_export_lambda(rbffd_plan_t p, double* lam_row, uint8_t* is_center) {
+    if (!p) return RBFFD_EINVAL;
+    if (!p->assembled) return RBFFD_ESTATE;
+    cudaStream_t s = p->last;
+    const size_t N = (size_t)p->N;
+    int rc = RBFFD_OK;
+    if (lam_row && (rc = bad(cudaMemcpyAsync(lam_row, p->lam_row, N * 8, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (is_center && (rc = bad(cudaMemcpyAsync(is_center, p->is_center, N, cudaMemcpyDeviceToHost, s)))) return rc;
+    return bad(cudaStreamSynchronize(s));
+}
+
+void rbffd_destroy(rbffd_plan_t p) { free_plan(p); }
+
+}  // extern "C"

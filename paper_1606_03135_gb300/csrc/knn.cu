@@ -1,0 +1,380 @@
+// knn.cu -- stencil formation (§2, §4.1): exact k-nearest neighbours by (squared distance,
+// index) on a uniform cell grid, the stencil width rho_k, the retention ball of radius
+// (1 - delta) rho_k and the traversal dependencies (in-degree) of every node.
+//
+// Bit-exactness with a brute-force search: squared distances are formed without FMA in a
+// fixed order, candidates are compared by (IEEE bits of d2, index), and the search ring
+// stops only once n candidates lie strictly inside a radius that no point outside the
+// searched cells can reach.
+#include <cuda_runtime.h>
+
+#include "rbffd_internal.cuh"
+
+namespace rbffd {
+
+// ------------------------------------------------------------------ exclusive scans
+// Single-CTA tiled exclusive scan: out[0..count] with out[count] = total.  Used for cell
+// offsets and weight-slot offsets (a few hundred thousand entries at most).
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(1024) k_scan(const TI* __restrict__ in, TO* __restrict__ out,
+                                               int count) {
+    constexpr int kPer = 4;
+    constexpr int kTile = 1024 * kPer;
+    __shared__ TO tile[kTile];
+    __shared__ TO warp_tot[32];
+    __shared__ TO carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < count; base += kTile) {
+        for (int r = 0; r < kPer; ++r) {
+            int i = base + r * 1024 + tid;
+            tile[r * 1024 + tid] = (i < count) ? (TO)in[i] : (TO)0;
+        }
+        __syncthreads();
+        TO v[kPer];
+        TO s = 0;
+        for (int r = 0; r < kPer; ++r) { v[r] = tile[tid * kPer + r]; s += v[r]; }
+        TO incl = s;  // inclusive warp scan of thread totals
+        for (int o = 1; o < 32; o <<= 1) {
+            TO t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            TO w = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                TO t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            warp_tot[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        TO run = carry_s + (wid > 0 ? warp_tot[wid - 1] : (TO)0) + (incl - s);
+        for (int r = 0; r < kPer; ++r) { tile[tid * kPer + r] = run; run += v[r]; }
+        __syncthreads();
+        for (int r = 0; r < kPer; ++r) {
+            int i = base + r * 1024 + tid;
+            if (i < count) out[i] = tile[r * 1024 + tid];
+        }
+        if (tid == 0) carry_s += warp_tot[31];
+        __syncthreads();
+    }
+    if (tid == 0) out[count] = carry_s;
+}
+
+int launch_scan_i32_to_i64(const int* in, long long* out, int count, cudaStream_t s,
+                           int* launches) {
+    k_scan<int, long long><<<1, 1024, 0, s>>>(in, out, count);
+    ++*launches;
+    return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+}
+
+// ------------------------------------------------------------------ grid build
+// One CTA: bounding box, cell size for about 2 nodes per cell, first search ring.
+template <int D>
+__global__ void __launch_bounds__(1024) k_grid_params(const double* __restrict__ X, int N, int n,
+                                                      int ncell_max, GridParams* gp) {
+    __shared__ double smin[3][32], smax[3][32];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        for (int a = 0; a < D; ++a) {
+            double v = X[(size_t)i * D + a];
+            lo[a] = fmin(lo[a], v);
+            hi[a] = fmax(hi[a], v);
+        }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int a = 0; a < D; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        if (lane == 0) { smin[a][wid] = lo[a]; smax[a][wid] = hi[a]; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x / 32;
+        double L[3], H[3], ext[3];
+        double vol = 1.0, maxext = 0.0;
+        for (int a = 0; a < D; ++a) {
+            L[a] = smin[a][0]; H[a] = smax[a][0];
+            for (int w = 1; w < nw; ++w) { L[a] = fmin(L[a], smin[a][w]); H[a] = fmax(H[a], smax[a][w]); }
+            ext[a] = H[a] - L[a];
+            maxext = fmax(maxext, ext[a]);
+        }
+        if (!(maxext > 0.0)) maxext = 1.0;
+        for (int a = 0; a < D; ++a) vol *= fmax(ext[a], 1e-3 * maxext);
+        const double ppc = 2.0;  // target nodes per cell
+        double h = (D == 2) ? sqrt(vol * ppc / N) : cbrt(vol * ppc / N);
+        if (!(h > 0.0)) h = maxext;
+        int dims[3] = {1, 1, 1};
+        long long nc = 1;
+        for (int it = 0; it < 200; ++it) {
+            nc = 1;
+            for (int a = 0; a < D; ++a) {
+                double c = floor(ext[a] / h) + 1.0;
+                dims[a] = (int)fmin(c, 1048576.0);
+                nc *= dims[a];
+            }
+            if (nc <= ncell_max) break;
+            h *= 1.1;
+        }
+        for (int a = 0; a < D; ++a) gp->lo[a] = L[a];
+        for (int a = D; a < 3; ++a) { gp->lo[a] = 0.0; dims[a] = 1; }
+        gp->h = h;
+        gp->inv_h = 1.0 / h;
+        for (int a = 0; a < 3; ++a) gp->dims[a] = dims[a];
+        gp->ncell = (int)nc;
+        // ring whose ball holds about n nodes at the average density
+        double per = (double)N / (double)nc;
+        double w = (D == 2) ? 3.14159265358979 : 4.18879020478639;
+        double r = (D == 2) ? sqrt(n / (per * w)) : cbrt(n / (per * w));
+        gp->r0 = (int)fmax(1.0, ceil(r));
+    }
+}
+
+template <int D>
+__device__ __forceinline__ int cell_coord(const GridParams& g, double x, int a) {
+    double t = __dmul_rn(__dsub_rn(x, g.lo[a]), g.inv_h);
+    int c = (int)t;  // x >= lo, so truncation is floor
+    return min(max(c, 0), g.dims[a] - 1);
+}
+
+template <int D>
+__device__ __forceinline__ int cell_index(const GridParams& g, const int* c) {
+    int idx = c[0];
+    if (D >= 2) idx += g.dims[0] * c[1];
+    if (D == 3) idx += g.dims[0] * g.dims[1] * c[2];
+    return idx;
+}
+
+template <int D>
+__global__ void k_cell_count(const double* __restrict__ X, int N, const GridParams* __restrict__ gp,
+                             int* __restrict__ cell_of, int* __restrict__ count) {
+    const GridParams g = *gp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int c[3];
+        for (int a = 0; a < D; ++a) c[a] = cell_coord<D>(g, X[(size_t)i * D + a], a);
+        int id = cell_index<D>(g, c);
+        cell_of[i] = id;
+        atomicAdd(&count[id], 1);
+    }
+}
+
+template <int D>
+__global__ void k_cell_fill(const double* __restrict__ X, int N, const int* __restrict__ cell_of,
+                            const int* __restrict__ cell_start, int* __restrict__ cursor,
+                            int* __restrict__ sorted_idx, double* __restrict__ sorted_X) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        int c = cell_of[i];
+        int pos = cell_start[c] + atomicAdd(&cursor[c], 1);
+        sorted_idx[pos] = i;
+        for (int a = 0; a < D; ++a) sorted_X[(size_t)pos * D + a] = X[(size_t)i * D + a];
+    }
+}
+
+// ------------------------------------------------------------------ kNN
+__device__ __forceinline__ bool key_less(unsigned long long ka, int ia, unsigned long long kb,
+                                         int ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// One warp per query node.  The warp keeps the n best candidates seen so far as a sorted
+// list in shared memory and merges batches of 32 candidates into it (ranks computed by
+// comparison counting, so the order is exact).
+template <int D>
+__global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N, int n,
+                                             double omd2, const GridParams* __restrict__ gp,
+                                             const int* __restrict__ cell_start,
+                                             const int* __restrict__ sorted_idx,
+                                             const double* __restrict__ sorted_X,
+                                             int* __restrict__ nbr, double* __restrict__ rho2,
+                                             int* __restrict__ ball_len, int* __restrict__ indeg,
+                                             DevCounters* ctr) {
+    extern __shared__ unsigned long long knn_smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    // per warp: keys[2][n], ids[2][n], batch keys[32], batch ids[32]
+    unsigned long long* lk = knn_smem + (size_t)wib * (2 * n + 32);
+    unsigned long long* bk = lk + 2 * n;
+    int* ids_base = reinterpret_cast<int*>(knn_smem + (size_t)wpb * (2 * n + 32));
+    int* li = ids_base + (size_t)wib * (2 * n + 32);
+    int* bi = li + 2 * n;
+    const GridParams g = *gp;
+
+    for (int q = blockIdx.x * wpb + wib; q < N; q += gridDim.x * wpb) {
+        double xq[3];
+        int c0[3];
+        for (int a = 0; a < D; ++a) {
+            xq[a] = X[(size_t)q * D + a];
+            c0[a] = cell_coord<D>(g, xq[a], a);
+        }
+        int r = g.r0;
+        int cnt = 0, cur = 0;
+        for (;;) {
+            int clo[3], chi[3];
+            bool all = true;
+            for (int a = 0; a < D; ++a) {
+                clo[a] = max(c0[a] - r, 0);
+                chi[a] = min(c0[a] + r, g.dims[a] - 1);
+                all = all && clo[a] == 0 && chi[a] == g.dims[a] - 1;
+            }
+            double rb = (double)r * g.h;
+            double bound = all ? __longlong_as_double(0x7ff0000000000000LL)  // +inf
+                               : rb * rb * (1.0 - 1e-8);
+            const unsigned long long bkey = dkey(bound);
+            cnt = 0;
+            cur = 0;
+            const int ny = chi[1] - clo[1] + 1;
+            const int nz = (D == 3) ? chi[2] - clo[2] + 1 : 1;
+            for (int rz = 0; rz < nz; ++rz)
+                for (int ry = 0; ry < ny; ++ry) {
+                    int cc[3] = {clo[0], clo[1] + ry, (D == 3) ? clo[2] + rz : 0};
+                    int row0 = cell_index<D>(g, cc);
+                    int beg = cell_start[row0];
+                    int end = cell_start[row0 + (chi[0] - clo[0]) + 1];
+                    for (int b0 = beg; b0 < end; b0 += 32) {
+                        int p = b0 + lane;
+                        bool valid = p < end;
+                        unsigned long long key = ~0ull;
+                        int id = 0x7fffffff;
+                        if (valid) {
+                            double xp[3];
+                            for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)p * D + a];
+                            double s = sqdist_rn<D>(xq, xp);
+                            key = dkey(s);
+                            id = sorted_idx[p];
+                            valid = key < bkey;
+                            if (valid && cnt == n) valid = key_less(key, id, lk[cur * n + n - 1], li[cur * n + n - 1]);
+                        }
+                        unsigned bal = __ballot_sync(0xffffffffu, valid);
+                        if (bal == 0) continue;
+                        // rank among the valid batch members
+                        int rb_ = 0;
+                        for (int s2 = 0; s2 < 32; ++s2) {
+                            unsigned long long ks = __shfl_sync(0xffffffffu, key, s2);
+                            int is = __shfl_sync(0xffffffffu, id, s2);
+                            if (((bal >> s2) & 1u) && key_less(ks, is, key, id)) ++rb_;
+                        }
+                        // position in the current list
+                        int lo_ = 0, hi_ = cnt;
+                        while (lo_ < hi_) {
+                            int mid = (lo_ + hi_) >> 1;
+                            if (key_less(lk[cur * n + mid], li[cur * n + mid], key, id)) lo_ = mid + 1;
+                            else hi_ = mid;
+                        }
+                        bk[lane] = valid ? key : ~0ull;
+                        bi[lane] = valid ? id : 0x7fffffff;
+                        __syncwarp();
+                        const int nxt = cur ^ 1;
+                        for (int e = lane; e < cnt; e += 32) {
+                            unsigned long long ke = lk[cur * n + e];
+                            int ie = li[cur * n + e];
+                            int before = 0;
+                            for (int s2 = 0; s2 < 32; ++s2)
+                                if (((bal >> s2) & 1u) && key_less(bk[s2], bi[s2], ke, ie)) ++before;
+                            int np = e + before;
+                            if (np < n) { lk[nxt * n + np] = ke; li[nxt * n + np] = ie; }
+                        }
+                        if (valid) {
+                            int np = lo_ + rb_;
+                            if (np < n) { lk[nxt * n + np] = key; li[nxt * n + np] = id; }
+                        }
+                        __syncwarp();
+                        cnt = min(cnt + __popc(bal), n);
+                        cur = nxt;
+                    }
+                }
+            if (cnt == n || all) break;
+            ++r;
+        }
+        // write the stencil, its width and retention ball
+        const double r2k = __longlong_as_double((long long)lk[cur * n + n - 1]);
+        const double rball = __dmul_rn(omd2, r2k);
+        int blen = 0;
+        for (int t0 = 0; t0 < n; t0 += 32) {
+            int t = t0 + lane;
+            bool inb = false;
+            if (t < n) {
+                int id = li[cur * n + t];
+                double dd = __longlong_as_double((long long)lk[cur * n + t]);
+                nbr[(size_t)q * n + t] = id;
+                inb = dd <= rball;
+                if (t >= 1 && dd == 0.0) set_error(ctr, RBFFD_EDUPLICATE);
+            }
+            blen += __popc(__ballot_sync(0xffffffffu, inb));
+        }
+        if (lane == 0) {
+            if (li[cur * n] != q) set_error(ctr, RBFFD_EDUPLICATE);
+            rho2[q] = r2k;
+            ball_len[q] = blen;
+            atomicMax(&ctr->max_ball, blen);
+        }
+        for (int t = 1 + lane; t < blen; t += 32) {
+            int i = li[cur * n + t];
+            if (i > q) atomicAdd(&indeg[i], 1);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ launcher
+size_t grid_scratch_bytes(int N, int D, int ncell_max) {
+    size_t b = 256;                                   // GridParams
+    b += (size_t)(ncell_max + 1) * sizeof(int) * 3;   // count, start, cursor
+    b += (size_t)N * sizeof(int) * 2;                 // cell_of, sorted_idx
+    b += (size_t)N * D * sizeof(double) + 64;         // sorted_X
+    return b + 256;
+}
+
+template <int D>
+static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratch,
+                        int ncell_max, int* nbr, double* rho2, int* ball_len, int* indeg,
+                        DevCounters* ctr, cudaStream_t s, int* launches) {
+    char* p = static_cast<char*>(scratch);
+    auto take = [&](size_t bytes) {
+        char* r = p;
+        p += (bytes + 255) & ~size_t(255);
+        return r;
+    };
+    GridParams* gp = reinterpret_cast<GridParams*>(take(sizeof(GridParams)));
+    int* count = reinterpret_cast<int*>(take((size_t)(ncell_max + 1) * sizeof(int)));
+    int* start = reinterpret_cast<int*>(take((size_t)(ncell_max + 1) * sizeof(int)));
+    int* cursor = reinterpret_cast<int*>(take((size_t)(ncell_max + 1) * sizeof(int)));
+    int* cell_of = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
+    int* sorted_idx = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
+    double* sorted_X = reinterpret_cast<double*>(take((size_t)N * D * sizeof(double)));
+
+    if (cudaMemsetAsync(count, 0, (size_t)(ncell_max + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(cursor, 0, (size_t)(ncell_max + 1) * sizeof(int), s) != cudaSuccess ||
+        cudaMemsetAsync(indeg, 0, (size_t)N * sizeof(int), s) != cudaSuccess)
+        return RBFFD_ECUDA;
+    k_grid_params<D><<<1, 1024, 0, s>>>(X, N, n, ncell_max, gp);
+    const int tb = 256;
+    const int nb = (N + tb - 1) / tb;
+    k_cell_count<D><<<nb, tb, 0, s>>>(X, N, gp, cell_of, count);
+    k_scan<int, int><<<1, 1024, 0, s>>>(count, start, ncell_max);
+    k_cell_fill<D><<<nb, tb, 0, s>>>(X, N, cell_of, start, cursor, sorted_idx, sorted_X);
+    const int wpb = 8;
+    size_t smem = (size_t)wpb * (2 * n + 32) * (sizeof(unsigned long long) + sizeof(int));
+    int blocks = (N + wpb - 1) / wpb;
+    k_knn<D><<<blocks, wpb * 32, smem, s>>>(X, N, n, omd2, gp, start, sorted_idx, sorted_X, nbr,
+                                            rho2, ball_len, indeg, ctr);
+    *launches += 5;
+    return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+}
+
+int launch_grid_and_knn(int D, const double* X, int N, int n, double omd2, void* scratch,
+                        size_t scratch_bytes, int ncell_max, int* nbr, double* rho2, int* ball_len,
+                        int* indeg, DevCounters* ctr, cudaStream_t s, int* launches) {
+    if (scratch_bytes < grid_scratch_bytes(N, D, ncell_max)) return RBFFD_EINVAL;
+    if (D == 2)
+        return grid_and_knn<2>(X, N, n, omd2, scratch, ncell_max, nbr, rho2, ball_len, indeg, ctr,
+                               s, launches);
+    return grid_and_knn<3>(X, N, n, omd2, scratch, ncell_max, nbr, rho2, ball_len, indeg, ctr, s,
+                           launches);
+}
+
+}  // namespace rbffd

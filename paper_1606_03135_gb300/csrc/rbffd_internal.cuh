@@ -1,0 +1,136 @@
+// rbffd_internal.cuh -- shared declarations of the GB300 overlapped RBF-FD library.
+//
+// Device memory layout of one plan (N nodes, stencil size n, dimension D):
+//   X        [N][D]  f64   node coordinates (copied from the caller)
+//   nbr      [N][n]  i32   kNN stencil of every node, ordered by (squared distance, index)
+//   rho2     [N]     f64   squared stencil width rho_k^2 (distance of the n-th neighbour)
+//   ball_len [N]     i32   retention-ball size; the ball is the prefix nbr[k][0..ball_len)
+//   indeg    [N]     i32   #{j < k : k in ball(j)}  (dependencies of k in the traversal)
+//   slot_off [N+1]   i64   exclusive prefix sum of ball_len: weight slot of (stencil j, ball
+//                          position t) is slot_off[j] + t
+//   slot_w   [S][n]  f64   weights of a solved column (S = slot_off[N])
+//   CSR      row_ptr [N+1] i64, col [N n] i32, val [N n] f64
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rbffd.h"
+
+namespace rbffd {
+
+constexpr int kMaxStencil = 128;  // n
+constexpr int kMaxEll = 8;
+constexpr int kMaxTerms = 165;    // C(8 + 3, 3)
+constexpr int kWarp = 32;
+
+// node states of the traversal
+constexpr int kUndecided = 0;
+constexpr int kCenter = 1;
+constexpr int kCovered = 2;
+constexpr int kNoOwner = 0x7fffffff;
+
+struct GridParams {
+    double lo[3];
+    double h;      // cell edge
+    double inv_h;  // 1 / h
+    int dims[3];
+    int ncell;
+    int r0;        // first search ring (in cells)
+};
+
+// Device-side counters and status of one plan (one 256-byte block; zeroed per call).
+struct DevCounters {
+    int status;              // first error code (RBFFD_*), 0 = OK
+    int n_singular;
+    int max_ball;
+    int q_head;              // next queue slot to claim
+    int q_tail;              // next queue slot to fill
+    int fb_count;            // fallback rows
+    int done;                // nodes whose traversal state is final
+    int abort;               // set when a bounded wait ran out: every worker leaves
+    unsigned long long n_centers;
+    unsigned long long n_rejected;
+    unsigned long long sum_cols;
+    unsigned long long n_fallback;
+    unsigned long long pad[22];
+};
+
+__device__ __forceinline__ void set_error(DevCounters* c, int code) {
+    atomicCAS(&c->status, 0, code);
+}
+
+// ((dx*dx + dy*dy) + dz*dz), every operation rounded separately (no FMA), x_a - y_a order.
+template <int D>
+__device__ __forceinline__ double sqdist_rn(const double* a, const double* b) {
+    double t = __dsub_rn(a[0], b[0]);
+    double s = __dmul_rn(t, t);
+    t = __dsub_rn(a[1], b[1]);
+    s = __dadd_rn(s, __dmul_rn(t, t));
+    if (D == 3) {
+        t = __dsub_rn(a[2], b[2]);
+        s = __dadd_rn(s, __dmul_rn(t, t));
+    }
+    return s;
+}
+
+// squared distances are >= 0, so their IEEE bit patterns order like the values
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------------ host-side launchers
+struct PlanDev;  // defined in api.cu
+
+int launch_grid_and_knn(int D, const double* X, int N, int n, double omd2, void* scratch_grid,
+                        size_t scratch_bytes, int ncell_max, int* nbr, double* rho2, int* ball_len,
+                        int* indeg, DevCounters* ctr, cudaStream_t s, int* launches);
+size_t grid_scratch_bytes(int N, int D, int ncell_max);
+
+int launch_scan_i32_to_i64(const int* in, long long* out, int count, cudaStream_t s,
+                           int* launches);
+
+struct SolveArgs {
+    const double* X;
+    const int* nbr;
+    const double* rho2;
+    const int* ball_len;
+    const long long* slot_off;
+    const signed char* alpha;  // [M][D] monomial exponents, graded order
+    int N, n, M, K, m, ell;
+    int qcap;                  // columns room per stencil
+    int stride;                // row stride of the local system in shared memory (odd)
+    int mode;                  // RBFFD_STAB_*
+    double coef;               // m (m + D - 2)
+    int no_seed;               // fault injection: push no initial center (waits run out)
+    unsigned long long timeout_ns;
+    // traversal state
+    int* state;
+    int* pending;
+    int* owner;
+    int* queue;
+    unsigned char* fb_flag;
+    int* fb_list;
+    // results
+    double* slot_w;
+    double* slot_lam;
+    unsigned char* slot_pass;
+    DevCounters* ctr;
+};
+
+size_t solve_smem_per_warp(int n, int K, int qcap, int D, int* stride_out);
+int launch_traversal(int D, const SolveArgs& a, const int* indeg, int warps_per_block,
+                     cudaStream_t s, int* launches, cudaEvent_t ev0, cudaEvent_t ev1);
+int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches);
+int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* val,
+                    double* lam_row, unsigned char* is_center, cudaStream_t s, int* launches);
+int launch_spmv(int N, int n, const long long* row_ptr, const int* col, const double* val,
+                const double* u, double* y, cudaStream_t s, int* launches);
+
+}  // namespace rbffd

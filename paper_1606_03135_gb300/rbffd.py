@@ -1,0 +1,230 @@
+"""Python binding of librbffd.so (include/rbffd.h): argument marshalling only.
+
+Every step of the differentiation-matrix construction runs in the library's CUDA kernels.
+The functions below carry the C names; ``Plan`` wraps them for torch users (torch provides
+device memory and the current CUDA stream, nothing else).  Importing this module never
+falls back to anything: if the shared library cannot be built or loaded, it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, EDUPLICATE, ENOMEM, ESINGULAR, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+STAB_SEQ, STAB_OFF, STAB_FALLBACK = 0, 1, 2
+
+
+class rbffd_opts(C.Structure):
+    _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
+                ("sync", C.c_int), ("fault_inject", C.c_int)]
+
+
+class rbffd_csr(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class rbffd_stats_t(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_centers", C.c_int64), ("n_fallback", C.c_int64),
+                ("n_rejected", C.c_int64), ("sum_cols", C.c_int64), ("max_ball", C.c_int64),
+                ("n_singular", C.c_int64), ("status", C.c_int32), ("n", C.c_int32),
+                ("M", C.c_int32), ("K", C.c_int32), ("d", C.c_int32), ("alg_flops", C.c_double),
+                ("n_launches", C.c_int64), ("ms_stencils", C.c_float),
+                ("ms_traversal", C.c_float), ("ms_fallback", C.c_float),
+                ("ms_finalize", C.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "rbffd_plan": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
+                             C.c_double, C.POINTER(rbffd_opts), C.c_void_p,
+                             C.POINTER(C.c_void_p)]),
+    "rbffd_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(rbffd_csr)]),
+    "rbffd_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_stats": (C.c_int, [C.c_void_p, C.POINTER(rbffd_stats_t)]),
+    "rbffd_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_export_stencils": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_export_lambda": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_destroy": (None, [C.c_void_p]),
+    "rbffd_strerror": (C.c_char_p, [C.c_int]),
+}
+
+
+def load() -> C.CDLL:
+    """Build (if stale) and load librbffd.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class RbffdError(RuntimeError):
+    def __init__(self, code, what):
+        msg = load().rbffd_strerror(code).decode()
+        super().__init__(f"{what}: {msg} ({code})")
+        self.code = code
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise RbffdError(rc, what)
+
+
+def _p(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())  # torch tensor
+
+
+# ------------------------------------------------------------------ C names
+def rbffd_plan(nodes_ptr, N, d, n, ell, m, delta, opts=None, stream=None):
+    out = C.c_void_p()
+    rc = load().rbffd_plan(nodes_ptr, N, d, n, ell, m, float(delta),
+                           C.byref(opts) if opts is not None else None, stream, C.byref(out))
+    return rc, out
+
+
+def rbffd_assemble(plan, stream=None):
+    csr = rbffd_csr()
+    rc = load().rbffd_assemble(plan, stream, C.byref(csr))
+    return rc, csr
+
+
+def rbffd_apply(plan, u_ptr, y_ptr, stream=None):
+    return load().rbffd_apply(plan, u_ptr, y_ptr, stream)
+
+
+def rbffd_stats(plan):
+    st = rbffd_stats_t()
+    rc = load().rbffd_stats(plan, C.byref(st))
+    return rc, st
+
+
+def rbffd_export(plan, row_ptr, col, val, owner):
+    return load().rbffd_export(plan, _p(row_ptr), _p(col), _p(val), _p(owner))
+
+
+def rbffd_export_stencils(plan, nbr, rho2, ball_len):
+    return load().rbffd_export_stencils(plan, _p(nbr), _p(rho2), _p(ball_len))
+
+
+def rbffd_export_lambda(plan, lam_row, is_center):
+    return load().rbffd_export_lambda(plan, _p(lam_row), _p(is_center))
+
+
+def rbffd_destroy(plan):
+    if plan:
+        load().rbffd_destroy(plan)
+
+
+def rbffd_strerror(code):
+    return load().rbffd_strerror(code).decode()
+
+
+# ------------------------------------------------------------------ torch-facing wrapper
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Plan:
+    """Stencils of one node set (``rbffd_plan``); ``assemble()`` forms L on the device.
+
+    nodes: a torch float64 tensor [N, d] on the GPU (or a numpy array on the host, copied by
+    the library inside ``rbffd_plan``)."""
+
+    def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
+                 stream=None, fault_inject=0):
+        self._plan = None
+        self._stream = stream
+        if isinstance(nodes, np.ndarray):
+            self._nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+            on_host = 1
+        else:
+            import torch
+            if nodes.dtype != torch.float64 or not nodes.is_cuda:
+                raise TypeError("nodes must be a float64 CUDA tensor or a numpy array")
+            self._nodes = nodes.contiguous()
+            on_host = 0
+        self.N, self.d = self._nodes.shape
+        self.n, self.ell, self.m, self.delta, self.mode = n, ell, m, delta, mode
+        opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject)
+        rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
+                              _stream_handle(stream))
+        _check(rc, "rbffd_plan")
+        self._plan = plan
+
+    def assemble(self):
+        rc, csr = rbffd_assemble(self._plan, _stream_handle(self._stream))
+        _check(rc, "rbffd_assemble")
+        return csr
+
+    def apply(self, u, y):
+        _check(rbffd_apply(self._plan, _p(u), _p(y), _stream_handle(self._stream)),
+               "rbffd_apply")
+
+    def stats(self) -> dict:
+        rc, st = rbffd_stats(self._plan)
+        _check(rc, "rbffd_stats")
+        return st.as_dict()
+
+    def export(self):
+        N, n = self.N, self.n
+        row_ptr = np.zeros(N + 1, np.int64)
+        col = np.zeros(N * n, np.int32)
+        val = np.zeros(N * n, np.float64)
+        owner = np.zeros(N, np.int32)
+        _check(rbffd_export(self._plan, row_ptr, col, val, owner), "rbffd_export")
+        return row_ptr, col, val, owner
+
+    def export_stencils(self):
+        N, n = self.N, self.n
+        nbr = np.zeros((N, n), np.int32)
+        rho2 = np.zeros(N, np.float64)
+        bl = np.zeros(N, np.int32)
+        _check(rbffd_export_stencils(self._plan, nbr, rho2, bl), "rbffd_export_stencils")
+        return nbr, rho2, bl
+
+    def export_lambda(self):
+        lam = np.zeros(self.N, np.float64)
+        isc = np.zeros(self.N, np.uint8)
+        _check(rbffd_export_lambda(self._plan, lam, isc), "rbffd_export_lambda")
+        return lam, isc
+
+    def close(self):
+        if self._plan:
+            rbffd_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,187 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+The bar: kNN stencils, stencil widths, retention balls, stencil ownership and the CSR
+structure bit-exact; weights within 1e-9 of the row's largest weight (the tolerance the
+method's specification states); Lebesgue values within 1e-9 relative.  Structural parity is
+asserted where the oracle saw no Lebesgue decision within 1e-9 of a tie.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1606_03135_gb300 import nodesets as NS
+from paper_1606_03135_gb300 import rbffd as R
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def gpu_run(X, n, ell, m, delta, mode=R.STAB_SEQ, host=False, **kw):
+    nodes = X if host else torch.from_numpy(X).cuda()
+    with R.Plan(nodes, n, ell, m, delta, mode=mode, **kw) as p:
+        p.assemble()
+        row_ptr, col, val, owner = p.export()
+        nbr, rho2, bl = p.export_stencils()
+        lam, isc = p.export_lambda()
+        st = p.stats()
+    return dict(row_ptr=row_ptr, col=col, val=val, owner=owner, nbr=nbr, rho2=rho2,
+                ball_len=bl, lam_row=lam, is_center=isc, stats=st)
+
+
+def check_rows(g, ref, n, rows=None):
+    N = g["row_ptr"].size - 1
+    rows = range(N) if rows is None else rows
+    worst = 0.0
+    for i in rows:
+        a = g["val"][i * n:(i + 1) * n]
+        b = ref["val"][i * n:(i + 1) * n]
+        err = np.abs(a - b).max() / np.abs(b).max()
+        worst = max(worst, err)
+        assert err <= TOL, f"row {i}: relative weight error {err:.3e}"
+    return worst
+
+
+def compare(X, n, ell, m, delta, mode=R.STAB_SEQ, ref=None):
+    g = gpu_run(X, n, ell, m, delta, mode)
+    if ref is None:
+        ref = O.assemble(X, n, ell, m, delta, mode)
+    assert np.array_equal(g["nbr"], ref["nbr"])
+    assert np.array_equal(g["rho2"], ref["d2"][:, -1])
+    assert np.array_equal(g["ball_len"], O.ball_len(ref["d2"], delta))
+    assert ref["stats"]["n_near_tie"] == 0
+    assert np.array_equal(g["owner"], ref["owner"])
+    assert np.array_equal(g["is_center"], ref["is_center"])
+    assert np.array_equal(g["row_ptr"], ref["row_ptr"])
+    assert np.array_equal(g["col"], ref["col"])
+    check_rows(g, ref, n)
+    np.testing.assert_allclose(g["lam_row"], ref["lam_row"], rtol=TOL, atol=0)
+    assert g["stats"]["n_centers"] == ref["stats"]["n_centers"]
+    assert g["stats"]["n_fallback"] == ref["stats"]["n_fallback"]
+    assert g["stats"]["status"] == 0
+    return g, ref
+
+
+# ------------------------------------------------------------------ small workload, all modes
+@pytest.mark.parametrize("delta", [1.0, 0.5])
+def test_disk2d_N2000_seq(delta):
+    X = NS.disk2d(2000, seed=1)
+    g, ref = compare(X, 12, 2, 3, delta)
+    if delta == 1.0:
+        assert g["stats"]["n_centers"] == 2000
+    else:
+        assert ref["stats"]["n_rejected"] > 0
+
+
+@pytest.mark.parametrize("mode", [R.STAB_OFF, R.STAB_FALLBACK])
+def test_disk2d_N2000_other_modes(mode):
+    X = NS.disk2d(2000, seed=1)
+    g, ref = compare(X, 12, 2, 3, 0.5, mode)
+    if mode == R.STAB_FALLBACK:
+        assert ref["stats"]["n_fallback"] > 0
+
+
+@pytest.mark.parametrize("N,n,ell,m,delta", [
+    (12, 12, 2, 3, 0.5),     # N == n: every stencil is the whole node set
+    (13, 12, 2, 3, 0.3),
+    (37, 10, 2, 5, 0.4),     # ragged sizes
+    (1, 1, 0, 3, 0.5),       # one node, one-term polynomial
+    (300, 6, 2, 3, 0.6),     # n == M
+    (1000, 31, 4, 7, 0.3),
+    (777, 80, 6, 7, 0.25),   # wide stencils: more than 32 columns per stencil
+])
+def test_small_and_ragged_2d(N, n, ell, m, delta):
+    X = NS.disk2d(N, seed=N)
+    compare(X, n, ell, m, delta)
+
+
+@pytest.mark.parametrize("side,n,ell,m,delta", [(6, 20, 2, 5, 0.5), (9, 45, 3, 7, 0.3),
+                                                (7, 35, 3, 5, 1.0)])
+def test_small_3d(side, n, ell, m, delta):
+    X = NS.jittered_grid(side, 3, seed=side)
+    compare(X, n, ell, m, delta)
+
+
+def test_raster_order_has_deep_dependency_chains():
+    X = NS.square2d(10000, seed=2, order="raster")
+    compare(X, 31, 4, 7, 0.5)
+
+
+def test_lattice_with_exact_distance_ties():
+    # exact ties in distance are broken by index on both sides
+    P = np.array([[i, j] for i in range(30) for j in range(30)], dtype=np.float64) * 0.125
+    P = P[NS.permutation(3, P.shape[0])]
+    g = gpu_run(P, 13, 2, 3, 1.0, mode=R.STAB_OFF)
+    nbr, d2 = O.knn(P, 13)
+    assert np.array_equal(g["nbr"], nbr)
+
+
+# ------------------------------------------------------------------ full-size 2D workload
+@pytest.mark.slow
+def test_square2d_N40000_full_oracle_all_deltas():
+    X = NS.square2d(40000, seed=2)
+    nbr, d2 = O.knn(X, 31)
+    for delta in (1.0, 0.5, 0.3):
+        ref = O.assemble(X, 31, 4, 7, delta, O.STAB_SEQ, nbr, d2)
+        ref["nbr"], ref["d2"] = nbr, d2
+        compare(X, 31, 4, 7, delta, ref=ref)
+
+
+# ------------------------------------------------------------------ apply, repeatability, API
+def test_apply_matches_csr_product():
+    X = NS.disk2d(2000, seed=1)
+    ref = O.assemble(X, 12, 2, 3, 0.5)
+    with R.Plan(torch.from_numpy(X).cuda(), 12, 2, 3, 0.5) as p:
+        p.assemble()
+        u = torch.from_numpy(np.cos(2 * X[:, 0]) + X[:, 1] ** 2).cuda()
+        y = torch.zeros_like(u)
+        p.apply(u, y)
+        torch.cuda.synchronize()
+    yr = O.csr_matvec(ref["row_ptr"], ref["col"], ref["val"], u.cpu().numpy())
+    scale = O.csr_matvec(ref["row_ptr"], ref["col"], np.abs(ref["val"]),
+                         np.abs(u.cpu().numpy()))
+    assert np.all(np.abs(y.cpu().numpy() - yr) <= TOL * scale)
+
+
+def test_reassembly_is_bitwise_repeatable_and_host_nodes_work():
+    X = NS.square2d(10000, seed=5)
+    with R.Plan(torch.from_numpy(X).cuda(), 31, 4, 7, 0.3) as p:
+        p.assemble()
+        a = p.export()
+        p.assemble()
+        b = p.export()
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    c = gpu_run(X, 31, 4, 7, 0.3, host=True)
+    assert np.array_equal(c["val"], a[2]) and np.array_equal(c["owner"], a[3])
+
+
+def test_errors_are_reported_not_raised_on_device():
+    X = NS.disk2d(500, seed=3)
+    X[100] = X[17]
+    with pytest.raises(R.RbffdError) as e:
+        R.Plan(torch.from_numpy(X).cuda(), 12, 2, 3, 0.5)
+    assert e.value.code == R.EDUPLICATE
+    X = NS.disk2d(500, seed=3)
+    with R.Plan(torch.from_numpy(X).cuda(), 12, 2, 3, 0.5) as p:
+        u = torch.zeros(500, dtype=torch.float64, device="cuda")
+        with pytest.raises(R.RbffdError) as e:
+            p.apply(u, u.clone())
+        assert e.value.code == R.ESTATE
+
+
+def test_bounded_wait_runs_out_and_context_survives():
+    # fault injection on the host side of the kernel: no initial center is seeded, so every
+    # worker's bounded wait for work runs out and the kernel returns RBFFD_ETIMEOUT
+    X = NS.disk2d(2000, seed=1)
+    t0 = time.time()
+    with R.Plan(torch.from_numpy(X).cuda(), 12, 2, 3, 0.5, timeout_ms=300,
+                fault_inject=1) as p:
+        with pytest.raises(R.RbffdError) as e:
+            p.assemble()
+        assert e.value.code == R.ETIMEOUT
+    assert time.time() - t0 < 30
+    compare(X, 12, 2, 3, 0.5)  # the context is still usable
