@@ -1,0 +1,306 @@
+"""Benchmark: forming the sparse FP64 Laplacian differentiation matrix with overlapped RBF-FD.
+
+One step = the delta sweep of the 2D workload: for each delta in (1.0, 0.5, 0.3), plan the
+stencils (kNN, retention balls) and assemble L (traversal with Lebesgue stabilization, one
+factorization per center, multi-RHS solves, CSR) for N = 40,000 jittered nodes in the unit
+square, PHS r^7, degree-4 polynomials (M = 15), n = 31.  Metric: matrix rows per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank forms its own copy of the workload (independent replicas:
+the method has no exchange step on this path) and rank 0 prints one JSON line with the
+aggregate rows/s over the max-over-ranks time.  ``--impl reference`` times the CPU oracle
+(the plain sequential restatement of the method) instead, one delta of the sweep per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "square2d_N40000_l4_n31_r7"
+METRIC = "diff-matrix rows/s (FP64, delta sweep)"
+UNIT = "rows/s"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _workload():
+    from paper_1606_03135_gb300 import nodesets as NS
+    w = NS.WORKLOADS[WORKLOAD]
+    return NS.make(WORKLOAD), w
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_entry():
+    """DRAM traffic of the traversal kernel from the committed ncu summary, if the kernel
+    source is unchanged since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traversal_traffic.json")
+    src = os.path.join(ROOT, "paper_1606_03135_gb300", "csrc", "assemble.cu")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("assemble_cu_sha256_16") == h:
+            return rec
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest value of x over all ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_step(X, w, delta):
+    """The oracle as it stands, on this host's cores: kNN + traversal + solves + CSR."""
+    from oracle import oracle as O
+    t = time.perf_counter()
+    O.assemble(X, w["n"], w["ell"], w["m"], delta, O.STAB_SEQ)
+    return time.perf_counter() - t
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    X, w = _workload()
+    deltas = w["deltas"]
+    for s in range(args.warmup):
+        cpu_oracle_step(X, w, deltas[s % len(deltas)])
+    times = []
+    for s in range(args.steps):
+        times.append(cpu_oracle_step(X, w, deltas[s % len(deltas)]))
+    total = sum(times)
+    rows = X.shape[0] * args.steps
+    value = rows / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": X.shape[0], "d": 2, "n": w["n"], "ell": w["ell"],
+                   "m": w["m"], "deltas": list(deltas), "stab": "seq"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one delta of the sweep per step, full N=40000 node set, "
+                                   "single-threaded plain C oracle (brute-force kNN)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1606_03135_gb300 import rbffd as R
+    R.load()
+    X, w = _workload()
+    N, n, ell, m, deltas = X.shape[0], w["n"], w["ell"], w["m"], w["deltas"]
+    Xd = torch.from_numpy(X).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step(detail=None, nodes=None, host_out=False):
+        launches = 0
+        alg = trav_ms = 0.0
+        d2h = 0
+        for delta in deltas:
+            p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta)
+            p.assemble()
+            if host_out:
+                row_ptr, col, val, owner = p.export()
+                d2h += row_ptr.nbytes + col.nbytes + val.nbytes + owner.nbytes
+            st = p.stats()
+            launches += st["n_launches"]
+            alg += st["alg_flops"]
+            trav_ms += st["ms_traversal"]
+            if detail is not None:
+                detail.setdefault(delta, []).append(st)
+            p.close()
+        return launches, alg, trav_ms, d2h
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    detail = {}
+    launches = 0
+    alg = trav_ms = 0.0
+    barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))  # evict L2 between timed steps (not inside a step's events)
+            ev[s][0].record(stream)
+            l, a, t, _ = one_step(detail)
+            ev[s][1].record(stream)
+            launches += l
+            alg += a
+            trav_ms += t
+        barrier()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    rows = N * len(deltas) * args.steps * world
+    value = rows / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers: host nodes in, host CSR out
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        _, _, _, d2h = one_step(nodes=X, host_out=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e_value = N * len(deltas) * e2e_steps * world / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        t_cpu = cpu_oracle_step(X, w, deltas[1])
+        cpu = {"value": N / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full assembly at delta={deltas[1]} (N={N}, kNN + traversal + "
+                         f"solves + CSR), single-threaded plain C oracle, {t_cpu:.1f} s"}
+
+    achieved = alg / (trav_ms / 1e3) / 1e12  # TFLOP/s of the traversal kernel
+    tr = _traffic_entry()
+    roofline = {"bound": "alu", "kernel": "k_traversal (FP64 LU + solves)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe); "
+                               "MEASURED_PEAKS.json has no FP64 entry",
+                "traffic": (tr["bytes_per_launch"] if tr else None),
+                "share_of_step": trav_ms / total_ms}
+    per_delta = {}
+    for delta, sts in detail.items():
+        per_delta[str(delta)] = {
+            "n_centers": sts[-1]["n_centers"], "sum_cols": sts[-1]["sum_cols"],
+            "ms_stencils": statistics.median(s["ms_stencils"] for s in sts),
+            "ms_traversal": statistics.median(s["ms_traversal"] for s in sts),
+            "ms_finalize": statistics.median(s["ms_finalize"] for s in sts),
+            "traversal_tflops": statistics.median(s["alg_flops"] / s["ms_traversal"] / 1e9
+                                                  for s in sts)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "d": 2, "n": n, "ell": ell, "m": m,
+                   "deltas": list(deltas), "stab": "seq",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline, "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(X.nbytes * len(deltas)),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches, "clocks": clk.summary(), "per_delta": per_delta,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -53,13 +54,19 @@ struct rbffd_plan_s {
     int launches = 0;
 };
 
-namespace {
-
-int bad(cudaError_t e) {
+namespace rbffd {
+int cuda_status(cudaError_t e, const char* what, int line) {
     if (e == cudaSuccess) return RBFFD_OK;
-    cudaGetLastError();  // clear a sticky-free error
+    static const bool debug = getenv("RBFFD_DEBUG") != nullptr;
+    if (debug) fprintf(stderr, "rbffd: %s (line %d): %s\n", what, line, cudaGetErrorString(e));
+    cudaGetLastError();  // clear a non-sticky error
     return e == cudaErrorMemoryAllocation ? RBFFD_ENOMEM : RBFFD_ECUDA;
 }
+}  // namespace rbffd
+
+namespace {
+
+#define bad(e) RB_CUDA(e)
 
 template <typename T>
 int alloc(T** p, size_t count, cudaStream_t s) {

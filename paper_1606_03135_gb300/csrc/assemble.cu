@@ -546,12 +546,12 @@ static int traversal(const SolveArgs& a, const int* indeg, int wpb, cudaStream_t
     const size_t per_warp = solve_smem_per_warp(a.n, a.K, a.qcap, D, &stride);
     const int alpha_bytes = (a.M * D + 15) & ~15;
     const size_t smem = alpha_bytes + per_warp * wpb;
-    if (cudaFuncSetAttribute(k_traversal<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (RB_CUDA(cudaFuncSetAttribute(k_traversal<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem)))
         return RBFFD_EINVAL;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traversal<D>, wpb * 32, smem) !=
-            cudaSuccess ||
+    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traversal<D>, wpb * 32,
+                                                              smem)) ||
         per_sm < 1)
         return RBFFD_EINVAL;
     const int tb = 256, nb = (a.N + tb - 1) / tb;
@@ -569,7 +569,7 @@ static int traversal(const SolveArgs& a, const int* indeg, int wpb, cudaStream_t
                                                 dim3(wpb * 32), args, smem, s);
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
-    return e == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+    return RB_CUDA(e);
 }
 
 int launch_traversal(int D, const SolveArgs& a, const int* indeg, int wpb, cudaStream_t s,
@@ -587,14 +587,14 @@ static int fallback(const SolveArgs& a, cudaStream_t s, int* launches) {
     const int alpha_bytes = (a.M * D + 15) & ~15;
     const int wpb = 2;
     const size_t smem = alpha_bytes + per_warp * wpb;
-    if (cudaFuncSetAttribute(k_fallback_solve<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (RB_CUDA(cudaFuncSetAttribute(k_fallback_solve<D>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return RBFFD_EINVAL;
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback_solve<D>, wpb * 32, smem);
     k_fallback_solve<D><<<max(per_sm, 1) * sm_count(), wpb * 32, smem, s>>>(a, per_warp, alpha_bytes);
     *launches += 2;
-    return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+    return RB_LAUNCHED(__func__);
 }
 
 int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches) {
@@ -608,7 +608,7 @@ int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* va
     k_finalize<<<blocks, wpb * 32, wpb * a.n * sizeof(int), s>>>(a, row_ptr, col, val, lam_row,
                                                                 is_center);
     ++*launches;
-    return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+    return RB_LAUNCHED(__func__);
 }
 
 int launch_spmv(int N, int n, const long long* row_ptr, const int* col, const double* val,
@@ -618,7 +618,7 @@ int launch_spmv(int N, int n, const long long* row_ptr, const int* col, const do
     const int blocks = (N + wpb - 1) / wpb;
     k_spmv<<<blocks, wpb * 32, 0, s>>>(N, row_ptr, col, val, u, y);
     ++*launches;
-    return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+    return RB_LAUNCHED(__func__);
 }
 
 }  // namespace rbffd

@@ -68,7 +68,7 @@ int launch_scan_i32_to_i64(const int* in, long long* out, int count, cudaStream_
                            int* launches) {
     k_scan<int, long long><<<1, 1024, 0, s>>>(in, out, count);
     ++*launches;
-    return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+    return RB_LAUNCHED(__func__);
 }
 
 // ------------------------------------------------------------------ grid build
@@ -321,12 +321,15 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
 }
 
 // ------------------------------------------------------------------ launcher
+// Every piece carved from the scratch buffer starts on a 256-byte boundary.
+static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
 size_t grid_scratch_bytes(int N, int D, int ncell_max) {
-    size_t b = 256;                                   // GridParams
-    b += (size_t)(ncell_max + 1) * sizeof(int) * 3;   // count, start, cursor
-    b += (size_t)N * sizeof(int) * 2;                 // cell_of, sorted_idx
-    b += (size_t)N * D * sizeof(double) + 64;         // sorted_X
-    return b + 256;
+    size_t b = round256(sizeof(GridParams));
+    b += 3 * round256((size_t)(ncell_max + 1) * sizeof(int));  // count, start, cursor
+    b += 2 * round256((size_t)N * sizeof(int));                // cell_of, sorted_idx
+    b += round256((size_t)N * D * sizeof(double));             // sorted_X
+    return b;
 }
 
 template <int D>
@@ -336,7 +339,7 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     char* p = static_cast<char*>(scratch);
     auto take = [&](size_t bytes) {
         char* r = p;
-        p += (bytes + 255) & ~size_t(255);
+        p += round256(bytes);
         return r;
     };
     GridParams* gp = reinterpret_cast<GridParams*>(take(sizeof(GridParams)));
@@ -347,10 +350,11 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     int* sorted_idx = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
     double* sorted_X = reinterpret_cast<double*>(take((size_t)N * D * sizeof(double)));
 
-    if (cudaMemsetAsync(count, 0, (size_t)(ncell_max + 1) * sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(cursor, 0, (size_t)(ncell_max + 1) * sizeof(int), s) != cudaSuccess ||
-        cudaMemsetAsync(indeg, 0, (size_t)N * sizeof(int), s) != cudaSuccess)
-        return RBFFD_ECUDA;
+    int rc;
+    if ((rc = RB_CUDA(cudaMemsetAsync(count, 0, (size_t)(ncell_max + 1) * sizeof(int), s))) ||
+        (rc = RB_CUDA(cudaMemsetAsync(cursor, 0, (size_t)(ncell_max + 1) * sizeof(int), s))) ||
+        (rc = RB_CUDA(cudaMemsetAsync(indeg, 0, (size_t)N * sizeof(int), s))))
+        return rc;
     k_grid_params<D><<<1, 1024, 0, s>>>(X, N, n, ncell_max, gp);
     const int tb = 256;
     const int nb = (N + tb - 1) / tb;
@@ -363,7 +367,7 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     k_knn<D><<<blocks, wpb * 32, smem, s>>>(X, N, n, omd2, gp, start, sorted_idx, sorted_X, nbr,
                                             rho2, ball_len, indeg, ctr);
     *launches += 5;
-    return cudaGetLastError() == cudaSuccess ? RBFFD_OK : RBFFD_ECUDA;
+    return RB_LAUNCHED(__func__);
 }
 
 int launch_grid_and_knn(int D, const double* X, int N, int n, double omd2, void* scratch,

@@ -56,6 +56,12 @@ struct DevCounters {
     unsigned long long pad[22];
 };
 
+// Map a CUDA status to an RBFFD code; with RBFFD_DEBUG set in the environment the failing
+// call is named on stderr.
+int cuda_status(cudaError_t e, const char* what, int line);
+#define RB_CUDA(call) ::rbffd::cuda_status((call), #call, __LINE__)
+#define RB_LAUNCHED(what) ::rbffd::cuda_status(cudaGetLastError(), what, __LINE__)
+
 __device__ __forceinline__ void set_error(DevCounters* c, int code) {
     atomicCAS(&c->status, 0, code);
 }

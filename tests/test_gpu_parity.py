@@ -39,7 +39,7 @@ def check_rows(g, ref, n, rows=None):
     for i in rows:
         a = g["val"][i * n:(i + 1) * n]
         b = ref["val"][i * n:(i + 1) * n]
-        err = np.abs(a - b).max() / np.abs(b).max()
+        err = np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)  # an all-zero row must match exactly
         worst = max(worst, err)
         assert err <= TOL, f"row {i}: relative weight error {err:.3e}"
     return worst
@@ -52,7 +52,8 @@ def compare(X, n, ell, m, delta, mode=R.STAB_SEQ, ref=None):
     assert np.array_equal(g["nbr"], ref["nbr"])
     assert np.array_equal(g["rho2"], ref["d2"][:, -1])
     assert np.array_equal(g["ball_len"], O.ball_len(ref["d2"], delta))
-    assert ref["stats"]["n_near_tie"] == 0
+    if mode != R.STAB_OFF:  # with the test off, no Lebesgue decision shapes the result
+        assert ref["stats"]["n_near_tie"] == 0
     assert np.array_equal(g["owner"], ref["owner"])
     assert np.array_equal(g["is_center"], ref["is_center"])
     assert np.array_equal(g["row_ptr"], ref["row_ptr"])
@@ -89,13 +90,21 @@ def test_disk2d_N2000_other_modes(mode):
     (13, 12, 2, 3, 0.3),
     (37, 10, 2, 5, 0.4),     # ragged sizes
     (1, 1, 0, 3, 0.5),       # one node, one-term polynomial
-    (300, 6, 2, 3, 0.6),     # n == M
     (1000, 31, 4, 7, 0.3),
-    (777, 80, 6, 7, 0.25),   # wide stencils: more than 32 columns per stencil
+    (900, 70, 4, 5, 0.2),    # wide stencils: more than 32 columns per stencil
 ])
 def test_small_and_ragged_2d(N, n, ell, m, delta):
     X = NS.disk2d(N, seed=N)
     compare(X, n, ell, m, delta)
+
+
+@pytest.mark.parametrize("delta,mode", [(0.6, R.STAB_OFF), (1.0, R.STAB_SEQ)])
+def test_n_equals_M(delta, mode):
+    # n == M: the weights are those of polynomial interpolation, whose Laplacian is the same
+    # at every retained node, so every Lebesgue comparison is an exact tie decided by
+    # rounding; only tie-free modes have a unique structure here
+    X = NS.disk2d(300, seed=300)
+    compare(X, 6, 2, 3, delta, mode)
 
 
 @pytest.mark.parametrize("side,n,ell,m,delta", [(6, 20, 2, 5, 0.5), (9, 45, 3, 7, 0.3),
@@ -117,6 +126,30 @@ def test_lattice_with_exact_distance_ties():
     g = gpu_run(P, 13, 2, 3, 1.0, mode=R.STAB_OFF)
     nbr, d2 = O.knn(P, 13)
     assert np.array_equal(g["nbr"], nbr)
+
+
+def test_ill_conditioned_stencils_are_as_accurate_as_the_oracle():
+    # n = 80, ell = 6: the local systems are ill-conditioned enough that rounding alone moves
+    # some weights by about 1e-9 of the row scale on either side.  Both are compared with a
+    # 40-digit solve of the same stencils; the GPU must be no less accurate than the oracle.
+    from tests.hp_reference import mp_weights
+    X = NS.disk2d(777, seed=777)
+    n, ell, m, delta = 80, 6, 7, 0.25
+    g = gpu_run(X, n, ell, m, delta)
+    ref = O.assemble(X, n, ell, m, delta)
+    assert np.array_equal(g["owner"], ref["owner"]) and np.array_equal(g["col"], ref["col"])
+    errs = []
+    for i in (23, 100, 400):
+        j = ref["owner"][i]
+        idx = ref["nbr"][j]
+        w_hp = mp_weights(X, idx, ell, m, X[i:i + 1], dps=40)[:, 0]
+        o = np.argsort(idx)
+        scale = np.abs(w_hp).max()
+        e_gpu = np.abs(g["val"][i * n:(i + 1) * n] - w_hp[o]).max() / scale
+        e_ora = np.abs(ref["val"][i * n:(i + 1) * n] - w_hp[o]).max() / scale
+        errs.append((e_gpu, e_ora))
+        assert e_gpu <= max(1e-9, 4.0 * e_ora), (i, e_gpu, e_ora)
+    print("forward errors (gpu, oracle):", errs)
 
 
 # ------------------------------------------------------------------ full-size 2D workload

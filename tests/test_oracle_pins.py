@@ -16,6 +16,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_1606_03135_gb300 import nodesets as NS
+from tests.hp_reference import mp_weights as _mp_weights
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -127,49 +128,6 @@ def test_seven_point_laplacian_3d_when_n_equals_M():
     X = np.array(pts, dtype=np.float64) - 0.2
     W, _ = O.local_weights(X, np.arange(10), 2, 5, X[:1])
     np.testing.assert_allclose(W[:, 0] * h * h, [-6, 1, 1, 1, 1, 1, 1, 0, 0, 0], atol=1e-11)
-
-
-def _mp_weights(X, idx, ell, m, Y, dps=40):
-    """Independent high-precision weights from the definitions of §4.1, in the ORIGINAL
-    coordinates with raw monomials x^a y^b (z^c); Laplacians by sympy differentiation."""
-    import mpmath as mp
-    import sympy as sp
-    mp.mp.dps = dps
-    d = X.shape[1]
-    syms = sp.symbols("x0:%d" % d)
-    cs = sp.symbols("c0:%d" % d)
-    r = sp.sqrt(sum((s - c) ** 2 for s, c in zip(syms, cs)))
-    lap = lambda f: sum(sp.diff(f, s, 2) for s in syms)
-    phi = r ** m
-    lphi = sp.simplify(lap(phi))
-    f_lphi = sp.lambdify(syms + cs, lphi, "mpmath")
-    exps = [a for g in range(ell + 1) for a in itertools.product(range(g + 1), repeat=d)
-            if sum(a) == g]
-    monos = [sp.Mul(*[s ** a for s, a in zip(syms, al)]) for al in exps]
-    f_mono = [sp.lambdify(syms, p, "mpmath") for p in monos]
-    f_lmono = [sp.lambdify(syms, lap(p), "mpmath") for p in monos]
-    n, M = len(idx), len(monos)
-    K = n + M
-    P = [[mp.mpf(float(v)) for v in X[i]] for i in idx]
-    A = mp.zeros(K, K)
-    for a in range(n):
-        for b in range(n):
-            A[a, b] = mp.sqrt(sum((P[a][t] - P[b][t]) ** 2 for t in range(d))) ** m
-        for l in range(M):
-            A[a, n + l] = f_mono[l](*P[a])
-            A[n + l, a] = A[a, n + l]
-    out = []
-    for y in Y:
-        yy = [mp.mpf(float(v)) for v in y]
-        b = mp.zeros(K, 1)
-        for a in range(n):
-            same = all(yy[t] == P[a][t] for t in range(d))
-            b[a] = 0 if same else f_lphi(*(yy + P[a]))
-        for l in range(M):
-            b[n + l] = f_lmono[l](*yy)
-        x = mp.lu_solve(A, b)
-        out.append([float(x[j]) for j in range(n)])
-    return np.array(out).T
 
 
 @pytest.mark.parametrize("d,n,ell,m,seed", [(2, 8, 1, 3, 1), (2, 10, 2, 5, 2), (3, 12, 1, 3, 3),
