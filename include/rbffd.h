@@ -136,6 +136,26 @@ int rbffd_export_stencils(rbffd_plan_t plan, int32_t* nbr, double* rho2, int32_t
  * produced it (§4.2.1), and is_center [N] (1 center, 2 fallback stencil, 0 otherwise). */
 int rbffd_export_lambda(rbffd_plan_t plan, double* lam_row, uint8_t* is_center);
 
+/* rbffd_stencils_noalloc -- the stencil step of rbffd_plan (kNN by (squared distance,
+ * index), stencil width, retention-ball size) for callers that cannot allocate device
+ * memory while they run: for example a solver that hands all device memory to its own pool
+ * before the run starts, or a loop with a fixed time budget that must not wait on the
+ * allocator.  The paper has no counterpart; this is a service of the library.
+ *   nodes    [N][d] FP64 device pointer; nbr [N][n] int32, rho2 [N] FP64, ball_len [N] int32
+ *            device pointers to caller-owned outputs (same contents as rbffd_export_stencils
+ *            of a plan built with the same arguments).
+ *   N        1 <= n <= N <= RBFFD_NOALLOC_MAX_NODES; larger N returns RBFFD_EINVAL and
+ *            writes nothing.  d, n, delta as for rbffd_plan.
+ * It allocates nothing: its working memory is one fixed array in the library's device
+ * memory (about 2 MB, held on every GPU that loads the library until the process exits).
+ * The first call on a device looks that array up for the current device; make that first
+ * call before any stream capture.  All calls share the array, so calls that overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the caller.  The
+ * call waits for `stream` to read the device status (RBFFD_EDUPLICATE for coincident nodes). */
+#define RBFFD_NOALLOC_MAX_NODES 32768
+int rbffd_stencils_noalloc(const double* nodes, int64_t N, int d, int n, double delta,
+                           int32_t* nbr, double* rho2, int32_t* ball_len, void* stream);
+
 /* rbffd_destroy -- free the plan and everything it owns (waits for its last stream). */
 void rbffd_destroy(rbffd_plan_t plan);
 

@@ -55,6 +55,8 @@ _SIGS = {
     "rbffd_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_export_stencils": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_export_lambda": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_stencils_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_destroy": (None, [C.c_void_p]),
     "rbffd_strerror": (C.c_char_p, [C.c_int]),
 }
@@ -129,6 +131,12 @@ def rbffd_export_stencils(plan, nbr, rho2, ball_len):
 
 def rbffd_export_lambda(plan, lam_row, is_center):
     return load().rbffd_export_lambda(plan, _p(lam_row), _p(is_center))
+
+
+def rbffd_stencils_noalloc(nodes, N, d, n, delta, nbr, rho2, ball_len, stream=None):
+    """Allocation-free stencil step on caller-owned device buffers (torch tensors)."""
+    return load().rbffd_stencils_noalloc(_p(nodes), N, d, n, float(delta), _p(nbr), _p(rho2),
+                                         _p(ball_len), stream)
 
 
 def rbffd_destroy(plan):
