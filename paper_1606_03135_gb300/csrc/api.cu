@@ -27,13 +27,13 @@ struct rbffd_plan_s {
     int* ball_len = nullptr;
     int* indeg = nullptr;
     long long* slot_off = nullptr;
-    signed char* alpha = nullptr;
+    short* basis = nullptr;  // monomial recurrence + Laplacian tables, M * (2 + 2d)
     DevCounters* ctr = nullptr;
     DevCounters* h_ctr = nullptr;  // pinned
     long long* h_slots = nullptr;  // pinned
     int max_ball = 0;
     long long total_slots = 0;
-    int qcap = 0, stride = 0, wpb = 1;
+    int qcap = 0, stride = 0;
     // traversal and results
     bool have_asm = false, assembled = false;
     int* state = nullptr;
@@ -111,6 +111,53 @@ int monomial_table(int d, int ell, signed char* out) {
     return M;
 }
 
+// Tables that let the kernels build the monomial basis by recurrence: psi_l is
+// psi_parent[l] times coordinate var[l]; the Laplacian of psi_l is the sum over axes a of
+// lap_coef[l][a] * psi_lap_child[l][a] (child = exponent minus 2 e_a, coef = e_a (e_a - 1)).
+// Layout: parent[M], var[M], lap_child[M][d], lap_coef[M][d] (int16).
+int basis_tables(int d, int ell, short* out) {
+    signed char ex[kMaxTerms * 3];
+    const int M = monomial_table(d, ell, ex);
+    auto index_of = [&](const int* e) {
+        for (int l = 0; l < M; ++l) {
+            bool same = true;
+            for (int a = 0; a < d; ++a) same = same && ex[l * d + a] == e[a];
+            if (same) return l;
+        }
+        return -1;
+    };
+    short* parent = out;
+    short* var = out + M;
+    short* lchild = out + 2 * M;
+    short* lcoef = out + 2 * M + M * d;
+    for (int l = 0; l < M; ++l) {
+        int e[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) e[a] = ex[l * d + a];
+        parent[l] = 0;
+        var[l] = 0;
+        for (int a = 0; a < d; ++a)
+            if (e[a] > 0) {
+                e[a] -= 1;
+                parent[l] = (short)index_of(e);
+                var[l] = (short)a;
+                e[a] += 1;
+                break;
+            }
+        for (int a = 0; a < d; ++a) {
+            if (e[a] >= 2) {
+                e[a] -= 2;
+                lchild[l * d + a] = (short)index_of(e);
+                lcoef[l * d + a] = (short)((e[a] + 2) * (e[a] + 1));
+                e[a] += 2;
+            } else {
+                lchild[l * d + a] = -1;
+                lcoef[l * d + a] = 0;
+            }
+        }
+    }
+    return M;
+}
+
 void free_assemble(rbffd_plan_s* p, cudaStream_t s) {
     release(&p->state, s); release(&p->pending, s); release(&p->owner, s);
     release(&p->queue, s); release(&p->fb_flag, s); release(&p->fb_list, s);
@@ -127,7 +174,7 @@ void free_plan(rbffd_plan_s* p) {
     if (s) cudaStreamSynchronize(s);
     free_assemble(p, s);
     release(&p->X, s); release(&p->nbr, s); release(&p->rho2, s); release(&p->ball_len, s);
-    release(&p->indeg, s); release(&p->slot_off, s); release(&p->alpha, s); release(&p->ctr, s);
+    release(&p->indeg, s); release(&p->slot_off, s); release(&p->basis, s); release(&p->ctr, s);
     cudaStreamSynchronize(s);
     if (p->h_ctr) cudaFreeHost(p->h_ctr);
     if (p->h_slots) cudaFreeHost(p->h_slots);
@@ -188,8 +235,9 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     const int Ni = (int)N;
     const int ncell_max = 2 * Ni + 64;
     const size_t sbytes = grid_scratch_bytes(Ni, d, ncell_max);
-    signed char h_alpha[kMaxTerms * 3];
-    monomial_table(d, ell, h_alpha);
+    short h_basis[kMaxTerms * 8];
+    basis_tables(d, ell, h_basis);
+    const size_t basis_count = (size_t)M * (2 + 2 * d);
     for (auto& e : p->ev)
         if ((rc = bad(cudaEventCreate(&e))) != RBFFD_OK) goto fail;
     if ((rc = bad(cudaMallocHost(reinterpret_cast<void**>(&p->h_ctr), sizeof(DevCounters)))) ||
@@ -198,7 +246,7 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     if ((rc = alloc(&p->X, (size_t)N * d, s)) || (rc = alloc(&p->nbr, (size_t)N * n, s)) ||
         (rc = alloc(&p->rho2, (size_t)N, s)) || (rc = alloc(&p->ball_len, (size_t)N, s)) ||
         (rc = alloc(&p->indeg, (size_t)N, s)) || (rc = alloc(&p->slot_off, (size_t)N + 1, s)) ||
-        (rc = alloc(&p->alpha, (size_t)M * d, s)) || (rc = alloc(&p->ctr, 1, s)))
+        (rc = alloc(&p->basis, basis_count, s)) || (rc = alloc(&p->ctr, 1, s)))
         goto fail;
     if ((rc = bad(cudaMallocAsync(&scratch, sbytes, s)))) goto fail;
     if ((rc = bad(cudaMemcpyAsync(p->X, nodes, (size_t)N * d * sizeof(double),
@@ -206,7 +254,8 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
                                                   : cudaMemcpyDeviceToDevice,
                                   s))))
         goto fail;
-    if ((rc = bad(cudaMemcpyAsync(p->alpha, h_alpha, (size_t)M * d, cudaMemcpyHostToDevice, s))) ||
+    if ((rc = bad(cudaMemcpyAsync(p->basis, h_basis, basis_count * sizeof(short),
+                                  cudaMemcpyHostToDevice, s))) ||
         (rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s))))
         goto fail;
     cudaEventRecord(p->ev[0], s);
@@ -231,11 +280,11 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     p->qcap = p->max_ball < 1 ? 1 : p->max_ball;
     {
         int stride = 0;
-        const size_t per_warp = solve_smem_per_warp(n, p->K, p->qcap, d, &stride);
+        const size_t per_cta = solve_smem_per_cta(n, p->K, p->qcap, d, &stride) +
+                               basis_smem_bytes(M, d);
         const size_t avail = (size_t)max_optin_smem() - 64;
         p->stride = stride;
-        if (per_warp > avail) { rc = RBFFD_EINVAL; goto fail; }
-        p->wpb = (2 * per_warp <= avail) ? 2 : 1;
+        if (per_cta > avail) { rc = RBFFD_EINVAL; goto fail; }
     }
     *out = p;
     return RBFFD_OK;
@@ -268,7 +317,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     }
     SolveArgs a{};
     a.X = p->X; a.nbr = p->nbr; a.rho2 = p->rho2; a.ball_len = p->ball_len;
-    a.slot_off = p->slot_off; a.alpha = p->alpha;
+    a.slot_off = p->slot_off; a.basis = p->basis;
     a.N = (int)p->N; a.n = p->n; a.M = p->M; a.K = p->K; a.m = p->m; a.ell = p->ell;
     a.qcap = p->qcap; a.stride = p->stride; a.mode = p->opts.stab_mode;
     a.coef = (double)(p->m * (p->m + p->d - 2));
@@ -278,7 +327,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.slot_w = p->slot_w; a.slot_lam = p->slot_lam; a.slot_pass = p->slot_pass; a.ctr = p->ctr;
     a.no_seed = p->opts.fault_inject == 1;
     if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
-    rc = launch_traversal(p->d, a, p->indeg, p->wpb, s, &p->launches, p->ev[2], p->ev[3]);
+    rc = launch_traversal(p->d, a, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
     if (rc) return rc;
     cudaEventRecord(p->ev[4], s);
     if (p->opts.stab_mode == RBFFD_STAB_FALLBACK) {

@@ -21,83 +21,102 @@
 // the paper's cost model (2/3) K^3 + 2 K^2 q flops.  Every FP64 warp instruction occupies
 // all 32 lanes of the narrow FP64 pipe whatever its active mask, so the updates are
 // flattened over (row, column) pairs to keep lanes busy.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "rbffd_internal.cuh"
 
 namespace rbffd {
 
-struct WarpSmem {
-    double* A;     // K rows x stride, [A P | B ; P^T 0 | B_psi]
-    double* xi;    // n x D scaled stencil coordinates
-    double* rdiag; // K reciprocal pivots
-    int* cols;     // qcap: ball position of each solved column
-    int* colof;    // n: column of each ball position or -1
+constexpr int kNT = 128;  // threads per stencil team: one warp per SM sub-partition
+
+// Per-CTA shared-memory views of one local system.
+struct StencilSmem {
+    double* A;      // K rows x stride: [A P | B ; P^T 0 | B_psi]
+    double* xi;     // n x D scaled stencil coordinates
+    double* rdiag;  // K reciprocal pivots
+    double* lam;    // qcap Lebesgue values of the solved columns
+    int* cols;      // qcap ball position of each solved column
+    int* colof;     // n column of each ball position, or -1
+    unsigned char* keep;  // qcap kept-for-coverage flags
 };
 
-size_t solve_smem_per_warp(int n, int K, int qcap, int D, int* stride_out) {
+// Monomial basis tables in shared memory (built on the host in graded order):
+//   psi_l = psi_parent[l] * xi_var[l]            (l >= 1; psi_0 = 1)
+//   Laplacian psi_l = sum_a lap_coef[l][a] * psi_lap_child[l][a]
+struct Basis {
+    const short* parent;
+    const short* var;
+    const short* lap_child;
+    const short* lap_coef;
+};
+
+size_t solve_smem_per_cta(int n, int K, int qcap, int D, int* stride_out) {
     int stride = K + qcap;
     if ((stride & 1) == 0) ++stride;  // odd row stride: column walks hit distinct banks
     if (stride_out) *stride_out = stride;
-    size_t b = (size_t)K * stride * 8 + (size_t)n * D * 8 + (size_t)K * 8 +
-               (size_t)(qcap + n) * 4;
+    size_t b = (size_t)K * stride * 8 + (size_t)n * D * 8 + (size_t)K * 8 + (size_t)qcap * 8 +
+               (size_t)(qcap + n) * 4 + (size_t)qcap;
     return (b + 15) & ~size_t(15);
 }
 
-__device__ __forceinline__ double ipow_rn(double x, int e) {
-    double p = 1.0;
-    for (int s = 0; s < e; ++s) p = __dmul_rn(p, x);
-    return p;
+size_t basis_smem_bytes(int M, int D) { return ((size_t)M * (2 + 2 * D) * sizeof(short) + 15) & ~size_t(15); }
+
+template <int D>
+__device__ __forceinline__ void carve(char* p, int n, int K, int qcap, int S, StencilSmem& sm) {
+    sm.A = reinterpret_cast<double*>(p);
+    p += (size_t)K * S * 8;
+    sm.xi = reinterpret_cast<double*>(p);
+    p += (size_t)n * D * 8;
+    sm.rdiag = reinterpret_cast<double*>(p);
+    p += (size_t)K * 8;
+    sm.lam = reinterpret_cast<double*>(p);
+    p += (size_t)qcap * 8;
+    sm.cols = reinterpret_cast<int*>(p);
+    p += (size_t)qcap * 4;
+    sm.colof = reinterpret_cast<int*>(p);
+    p += (size_t)n * 4;
+    sm.keep = reinterpret_cast<unsigned char*>(p);
 }
 
-// psi(x) = prod_a x_a^alpha_a (same multiplication order as the definition, no FMA)
-template <int D>
-__device__ __forceinline__ double mono_rn(const double* x, const signed char* al) {
-    double p = 1.0;
-    for (int a = 0; a < D; ++a) p = __dmul_rn(p, ipow_rn(x[a], al[a]));
-    return p;
+__device__ __forceinline__ Basis load_basis(char* smem, const short* g, int M, int D) {
+    short* s = reinterpret_cast<short*>(smem);
+    for (int e = threadIdx.x; e < M * (2 + 2 * D); e += blockDim.x) s[e] = g[e];
+    Basis b;
+    b.parent = s;
+    b.var = s + M;
+    b.lap_child = s + 2 * M;
+    b.lap_coef = s + 2 * M + M * D;
+    return b;
 }
 
-// Laplacian of psi: sum_a alpha_a (alpha_a - 1) x^(alpha - 2 e_a)
+// Assemble and solve the local system of stencil j for the q columns in sm.cols, with the
+// whole CTA.  Returns false (uniformly) on an exactly zero pivot.  On success the first n
+// rows of the right-hand-side block of sm.A hold the weights in scaled coordinates.
 template <int D>
-__device__ __forceinline__ double lap_mono_rn(const double* x, const signed char* al) {
-    double s = 0.0;
-    for (int a = 0; a < D; ++a) {
-        if (al[a] < 2) continue;
-        double p = (double)(al[a] * (al[a] - 1));
-        for (int b = 0; b < D; ++b) p = __dmul_rn(p, ipow_rn(x[b], b == a ? al[b] - 2 : al[b]));
-        s = __dadd_rn(s, p);
-    }
-    return s;
-}
-
-// Assemble and solve the local system of stencil j for the q columns in sm.cols.
-// Returns false on an exactly zero pivot.  On return (true) the first n rows of the
-// right-hand-side block of sm.A hold the scaled weights.
-template <int D>
-__device__ bool solve_local(const SolveArgs& a, const signed char* alpha, int j, int q,
-                            const WarpSmem& sm, int lane) {
+__device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
+                            const StencilSmem& sm) {
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = a.n, M = a.M, K = a.K, S = a.stride, m = a.m;
     const int Wd = K + q;
     double r2c = a.rho2[j];
     if (!(r2c > 0.0)) r2c = 1.0;
     const double rho = sqrt(r2c);
     const double* xc = a.X + (size_t)j * D;
-    for (int t = lane; t < n; t += 32) {
+    for (int t = tid; t < n; t += kNT) {
         const int id = a.nbr[(size_t)j * n + t];
         for (int c = 0; c < D; ++c)
             sm.xi[t * D + c] = __ddiv_rn(__dsub_rn(a.X[(size_t)id * D + c], xc[c]), rho);
     }
-    for (int e = lane; e < K * Wd; e += 32) {
+    for (int e = tid; e < K * Wd; e += kNT) {
         const int r = e / Wd, c = e - r * Wd;
         sm.A[r * S + c] = 0.0;
     }
-    __syncwarp();
+    __syncthreads();
     // A_ab = r^m and, for solved ball members, the phi-part of the right-hand side
     // m (m + D - 2) r^(m-2) (Laplacian of r^m in D dimensions), pair by pair
     {
-        int ra = 0, off = lane;
+        int ra = 0, off = tid;
         while (ra < n - 1 && off >= n - 1 - ra) { off -= n - 1 - ra; ++ra; }
         while (ra < n - 1) {
             const int rb = ra + 1 + off;
@@ -111,60 +130,80 @@ __device__ bool solve_local(const SolveArgs& a, const signed char* alpha, int j,
             const int ca = sm.colof[ra], cb = sm.colof[rb];
             if (cb >= 0) sm.A[ra * S + K + cb] = __dmul_rn(a.coef, pm2);
             if (ca >= 0) sm.A[rb * S + K + ca] = __dmul_rn(a.coef, pm2);
-            off += 32;
+            off += kNT;
             while (ra < n - 1 && off >= n - 1 - ra) { off -= n - 1 - ra; ++ra; }
         }
     }
-    // polynomial blocks P and P^T
-    for (int e = lane; e < n * M; e += 32) {
-        const int r = e / M, l = e - r * M;
-        const double v = mono_rn<D>(sm.xi + r * D, alpha + l * D);
-        sm.A[r * S + n + l] = v;
-        sm.A[(n + l) * S + r] = v;
+    // P: one stencil point per thread, each monomial = an earlier one times one coordinate
+    for (int r = tid; r < n; r += kNT) {
+        double* row = sm.A + r * S + n;
+        row[0] = 1.0;
+        sm.A[n * S + r] = 1.0;
+        for (int l = 1; l < M; ++l) {
+            const double v = row[bs.parent[l]] * sm.xi[r * D + bs.var[l]];
+            row[l] = v;
+            sm.A[(n + l) * S + r] = v;
+        }
     }
-    // psi-part of the right-hand sides: Laplacian of each monomial at each solved member
-    for (int e = lane; e < M * q; e += 32) {
+    __syncthreads();
+    // psi-part of the right-hand sides: Laplacian of each monomial at each solved member,
+    // from the monomial values already in that member's row of P
+    for (int e = tid; e < M * q; e += kNT) {
         const int l = e / q, c = e - l * q;
-        sm.A[(n + l) * S + K + c] = lap_mono_rn<D>(sm.xi + sm.cols[c] * D, alpha + l * D);
+        const double* prow = sm.A + sm.cols[c] * S + n;
+        double s = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const int ch = bs.lap_child[l * D + d];
+            if (ch >= 0) s = fma((double)bs.lap_coef[l * D + d], prow[ch], s);
+        }
+        sm.A[(n + l) * S + K + c] = s;
     }
-    __syncwarp();
+    __syncthreads();
 
-    // Gaussian elimination with partial pivoting on [A_hat | B_hat]
+    // Gaussian elimination with partial pivoting on [A_hat | B_hat]; the pivot search, row
+    // swap, reciprocal and multipliers are done by warp 0 alone (FP64 work counts per warp
+    // instruction, so the other warps must not repeat it)
     for (int p = 0; p < K; ++p) {
-        unsigned long long bv = 0ull;
-        int bi = 0x7fffffff;
-        for (int i = p + lane; i < K; i += 32) {
-            const unsigned long long v =
-                (unsigned long long)__double_as_longlong(sm.A[i * S + p]) & 0x7fffffffffffffffull;
-            if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-        }
-        if (bv == 0ull) return false;
-        if (bi != p) {
-            for (int c = p + lane; c < Wd; c += 32) {
-                const double t = sm.A[p * S + c];
-                sm.A[p * S + c] = sm.A[bi * S + c];
-                sm.A[bi * S + c] = t;
+        if (wid == 0) {
+            unsigned long long bv = 0ull;
+            int bi = 0x7fffffff;
+            for (int i = p + lane; i < K; i += 32) {
+                const unsigned long long v =
+                    (unsigned long long)__double_as_longlong(sm.A[i * S + p]) & 0x7fffffffffffffffull;
+                if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
             }
-            __syncwarp();
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (bv == 0ull) {
+                if (lane == 0) s_ok = 0;
+            } else {
+                if (bi != p) {
+                    for (int c = p + lane; c < Wd; c += 32) {
+                        const double t = sm.A[p * S + c];
+                        sm.A[p * S + c] = sm.A[bi * S + c];
+                        sm.A[bi * S + c] = t;
+                    }
+                    __syncwarp();
+                }
+                const double rcp = 1.0 / sm.A[p * S + p];
+                if (lane == 0) { sm.rdiag[p] = rcp; s_ok = 1; }
+                for (int i = p + 1 + lane; i < K; i += 32) sm.A[i * S + p] *= rcp;
+            }
         }
-        const double rcp = 1.0 / sm.A[p * S + p];
-        if (lane == 0) sm.rdiag[p] = rcp;
-        for (int i = p + 1 + lane; i < K; i += 32) sm.A[i * S + p] = sm.A[i * S + p] * rcp;
-        __syncwarp();
+        __syncthreads();
+        if (!s_ok) return false;
         const int wr = K - p - 1, wc = Wd - p - 1;
-        if (wr > 0 && wc > 0) {
-            const int total = wr * wc;
-            int ii = lane / wc, jj = lane - (lane / wc) * wc;
-            const int di = 32 / wc, dj = 32 - di * wc;
-            double* Ap = sm.A + p * S + p + 1;
+        const int total = wr * wc;
+        if (tid < total) {
+            int ii = tid / wc, jj = tid - (tid / wc) * wc;
+            const int di = kNT / wc, dj = kNT - di * wc;
+            const double* Ap = sm.A + p * S + p + 1;
             double* Ab = sm.A + (p + 1) * S;
 #pragma unroll 4
-            for (int e = lane; e < total; e += 32) {
+            for (int e = tid; e < total; e += kNT) {
                 double* row = Ab + ii * S;
                 row[p + 1 + jj] = fma(-row[p], Ap[jj], row[p + 1 + jj]);
                 ii += di;
@@ -172,20 +211,19 @@ __device__ bool solve_local(const SolveArgs& a, const signed char* alpha, int j,
                 if (jj >= wc) { jj -= wc; ++ii; }
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
     // back substitution, q columns at once
     for (int p = K - 1; p >= 0; --p) {
-        const double rcp = sm.rdiag[p];
-        for (int c = lane; c < q; c += 32) sm.A[p * S + K + c] *= rcp;
-        __syncwarp();
+        if (tid < q) sm.A[p * S + K + tid] *= sm.rdiag[p];
+        __syncthreads();
         const int total = p * q;
-        if (total > 0) {
-            int ii = lane / q, jj = lane - (lane / q) * q;
-            const int di = 32 / q, dj = 32 - di * q;
+        if (tid < total) {
+            int ii = tid / q, jj = tid - (tid / q) * q;
+            const int di = kNT / q, dj = kNT - di * q;
             const double* xp = sm.A + p * S + K;
 #pragma unroll 4
-            for (int e = lane; e < total; e += 32) {
+            for (int e = tid; e < total; e += kNT) {
                 double* row = sm.A + ii * S;
                 row[K + jj] = fma(-row[p], xp[jj], row[K + jj]);
                 ii += di;
@@ -193,9 +231,20 @@ __device__ bool solve_local(const SolveArgs& a, const signed char* alpha, int j,
                 if (jj >= q) { jj -= q; ++ii; }
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
     return true;
+}
+
+// Local L-Lebesgue value sum_r |w_r| of every solved column (one warp per column).
+__device__ __forceinline__ void lebesgue_values(const SolveArgs& a, int q, const StencilSmem& sm) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int c = wid; c < q; c += kNT / 32) {
+        double s = 0.0;
+        for (int r = lane; r < a.n; r += 32) s += fabs(sm.A[r * a.stride + a.K + c]);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sm.lam[c] = s;
+    }
 }
 
 // ------------------------------------------------------------------ traversal state machine
@@ -249,157 +298,133 @@ __global__ void k_traversal_seed(SolveArgs a, const int* __restrict__ indeg) {
     }
 }
 
+// One CTA per center.  Thread 0 claims the next queue slot and waits (bounded) for it to be
+// filled; the CTA then solves the center, tests and writes its columns, and resolves the
+// traversal state of its ball members.
 template <int D>
-__device__ __forceinline__ void carve(char* smem, int wib, size_t per_warp, int n, int K,
-                                      int qcap, int S, WarpSmem& sm) {
-    char* p = smem + per_warp * wib;
-    sm.A = reinterpret_cast<double*>(p);
-    p += (size_t)K * S * 8;
-    sm.xi = reinterpret_cast<double*>(p);
-    p += (size_t)n * D * 8;
-    sm.rdiag = reinterpret_cast<double*>(p);
-    p += (size_t)K * 8;
-    sm.cols = reinterpret_cast<int*>(p);
-    p += (size_t)qcap * 4;
-    sm.colof = reinterpret_cast<int*>(p);
-}
-
-template <int D>
-__global__ void __launch_bounds__(128) k_traversal(SolveArgs a, size_t per_warp, int alpha_bytes) {
+__global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
-    signed char* alpha = reinterpret_cast<signed char*>(smem);
-    for (int e = threadIdx.x; e < a.M * D; e += blockDim.x) alpha[e] = a.alpha[e];
+    __shared__ int s_j, s_q;
+    const Basis bs = load_basis(smem, a.basis, a.M, D);
+    StencilSmem sm;
+    carve<D>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
     __syncthreads();
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    WarpSmem sm;
-    carve<D>(smem + alpha_bytes, wib, per_warp, a.n, a.K, a.qcap, a.stride, sm);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = a.n, N = a.N;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
 
     for (;;) {
-        int slot = 0;
-        if (lane == 0) slot = atomicAdd(&a.ctr->q_head, 1);
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (slot >= N) break;
-        int j = -1;
-        if (lane == 0) {
-            const unsigned long long t0 = globaltimer_ns();
-            unsigned ns = 32;
-            for (;;) {
-                j = *((volatile int*)&a.queue[slot]);
-                if (j >= 0) break;
-                if (*((volatile int*)&a.ctr->done) >= N || *((volatile int*)&a.ctr->abort) != 0) {
-                    j = -1;
-                    break;
+        if (tid == 0) {
+            int j = -1;
+            const int slot = atomicAdd(&a.ctr->q_head, 1);
+            if (slot < N) {
+                const unsigned long long t0 = globaltimer_ns();
+                unsigned ns = 32;
+                for (;;) {
+                    j = *((volatile int*)&a.queue[slot]);
+                    if (j >= 0) break;
+                    if (*((volatile int*)&a.ctr->done) >= N || *((volatile int*)&a.ctr->abort) != 0) {
+                        j = -1;
+                        break;
+                    }
+                    if (globaltimer_ns() - t0 > a.timeout_ns) {
+                        set_error(a.ctr, RBFFD_ETIMEOUT);
+                        atomicExch(&a.ctr->abort, 1);
+                        j = -1;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    if (ns < 2048) ns <<= 1;
                 }
-                if (globaltimer_ns() - t0 > a.timeout_ns) {
-                    set_error(a.ctr, RBFFD_ETIMEOUT);
-                    atomicExch(&a.ctr->abort, 1);
-                    j = -1;
-                    break;
-                }
-                __nanosleep(ns);
-                if (ns < 2048) ns <<= 1;
             }
+            s_j = j;
         }
-        j = __shfl_sync(0xffffffffu, j, 0);
+        __syncthreads();
+        const int j = s_j;
         if (j < 0) break;
         __threadfence();
 
         // columns: the center and every later ball member not already kept by an earlier center
         const int L = a.ball_len[j];
-        int q = 0;
-        for (int t0 = 0; t0 < n; t0 += 32) {
-            const int t = t0 + lane;
-            bool inc = false;
-            if (t < L) {
-                if (t == 0) inc = true;
-                else {
-                    const int i = a.nbr[(size_t)j * n + t];
-                    inc = (i > j) && (__ldcg(&a.owner[i]) >= j);
+        if (wid == 0) {
+            int q = 0;
+            for (int t0 = 0; t0 < n; t0 += 32) {
+                const int t = t0 + lane;
+                bool inc = false;
+                if (t < L) {
+                    if (t == 0) inc = true;
+                    else {
+                        const int i = a.nbr[(size_t)j * n + t];
+                        inc = (i > j) && (__ldcg(&a.owner[i]) >= j);
+                    }
                 }
+                const unsigned bal = __ballot_sync(0xffffffffu, inc);
+                const int pos = q + __popc(bal & ((1u << lane) - 1u));
+                if (inc) sm.cols[pos] = t;
+                if (t < n) sm.colof[t] = inc ? pos : -1;
+                q += __popc(bal);
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, inc);
-            const int pos = q + __popc(bal & ((1u << lane) - 1u));
-            if (inc) sm.cols[pos] = t;
-            if (t < n) sm.colof[t] = inc ? pos : -1;
-            q += __popc(bal);
+            if (lane == 0) s_q = q;
         }
-        __syncwarp();
-        const bool ok = solve_local<D>(a, alpha, j, q, sm, lane);
-        if (!ok && lane == 0) {
-            atomicAdd(&a.ctr->n_singular, 1);
-            set_error(a.ctr, RBFFD_ESINGULAR);
+        __syncthreads();
+        const int q = s_q;
+        const bool ok = solve_local<D>(a, bs, j, q, sm);
+        if (ok) lebesgue_values(a, q, sm);
+        __syncthreads();
+        // Lebesgue test (§4.2.1) per column; q <= n <= kNT, so one thread per column
+        const long long base = a.slot_off[j];
+        bool failed = false;
+        if (tid < q) {
+            const double lam = ok ? sm.lam[tid] : nan;
+            const bool test_ok =
+                ok && __double_as_longlong(lam) <= __double_as_longlong(sm.lam[0]);
+            bool keep;
+            if (!ok) keep = (tid == 0);
+            else if (a.mode != RBFFD_STAB_SEQ) keep = true;
+            else keep = test_ok;
+            sm.keep[tid] = keep ? 1 : 0;
+            a.slot_lam[base + sm.cols[tid]] = lam;
+            a.slot_pass[base + sm.cols[tid]] = (tid == 0 || test_ok) ? 1 : 0;
+            failed = tid > 0 && !test_ok;
         }
-        // Lebesgue test per column (columns beyond 32 are handled in chunks of 32)
-        int rejected = 0;
-        unsigned keepmask[4] = {0u, 0u, 0u, 0u};
-        {
-            int done_cols = 0;
-            double lam0 = 0.0;
-            const int S = a.stride, K = a.K;
-            const long long base = a.slot_off[j];
-            double r2c = a.rho2[j];
-            if (!(r2c > 0.0)) r2c = 1.0;
-            const double inv_r2 = 1.0 / r2c;
-            while (done_cols < q) {
-                const int c = done_cols + lane;
-                double lam = 0.0;
-                if (ok && c < q) {
-                    double s = 0.0;
-                    for (int r = 0; r < n; ++r) s = __dadd_rn(s, fabs(sm.A[r * S + K + c]));
-                    lam = s;
-                }
-                if (done_cols == 0) lam0 = __shfl_sync(0xffffffffu, lam, 0);
-                bool pass = false;
-                if (c < q) {
-                    if (!ok) pass = (c == 0);
-                    else if (a.mode != RBFFD_STAB_SEQ) pass = true;
-                    else pass = __double_as_longlong(lam) <= __double_as_longlong(lam0);
-                    a.slot_lam[base + sm.cols[c]] = ok ? lam : __longlong_as_double(0x7ff8000000000000LL);
-                    const bool test_ok = ok && __double_as_longlong(lam) <= __double_as_longlong(lam0);
-                    a.slot_pass[base + sm.cols[c]] = (c == 0 || test_ok) ? 1 : 0;
-                    if (c > 0 && !test_ok) ++rejected;
-                }
-                const unsigned pm = __ballot_sync(0xffffffffu, pass);
-                keepmask[done_cols >> 5] = pm;
-                const int w = min(32, q - done_cols);
-                for (int e = lane; e < w * n; e += 32) {
-                    const int cc = e / n, r = e - cc * n;
-                    if (!((pm >> cc) & 1u)) continue;
-                    const int col = done_cols + cc;
-                    const double v = ok ? sm.A[r * S + K + col] * inv_r2
-                                        : __longlong_as_double(0x7ff8000000000000LL);
-                    a.slot_w[(base + sm.cols[col]) * n + r] = v;
-                }
-                done_cols += 32;
-            }
+        const int rejected = __syncthreads_count(failed);
+        double r2c = a.rho2[j];
+        if (!(r2c > 0.0)) r2c = 1.0;
+        const double inv_r2 = 1.0 / r2c;
+        for (int e = tid; e < q * n; e += kNT) {
+            const int c = e / n, r = e - c * n;
+            if (!sm.keep[c]) continue;
+            a.slot_w[(base + sm.cols[c]) * n + r] =
+                ok ? sm.A[r * a.stride + a.K + c] * inv_r2 : nan;
         }
-        for (int o = 16; o > 0; o >>= 1) rejected += __shfl_xor_sync(0xffffffffu, rejected, o);
         // ownership: the earliest center keeping a row owns it
-        for (int c = 1 + lane; c < q; c += 32) {
-            if ((keepmask[c >> 5] >> (c & 31)) & 1u) {
-                const int i = a.nbr[(size_t)j * n + sm.cols[c]];
-                atomicMin(&a.owner[i], j);
-            }
+        if (tid > 0 && tid < q && sm.keep[tid]) {
+            const int i = a.nbr[(size_t)j * n + sm.cols[tid]];
+            atomicMin(&a.owner[i], j);
         }
         __threadfence();
+        __syncthreads();
         // resolve: kept members become covered; every later ball member loses a dependency
-        for (int t = 1 + lane; t < L; t += 32) {
+        for (int t = 1 + tid; t < L; t += kNT) {
             const int i = a.nbr[(size_t)j * n + t];
             if (i <= j) continue;
             const int c = sm.colof[t];
-            const bool kept = c >= 0 && ((keepmask[c >> 5] >> (c & 31)) & 1u);
+            const bool kept = c >= 0 && sm.keep[c];
             if (kept && atomicCAS(&a.state[i], kUndecided, kCovered) == kUndecided) on_covered(a, i);
             __threadfence();
             release(a, i);
         }
-        if (lane == 0) {
+        if (tid == 0) {
+            if (!ok) {
+                atomicAdd(&a.ctr->n_singular, 1);
+                set_error(a.ctr, RBFFD_ESINGULAR);
+            }
             atomicAdd(&a.ctr->n_centers, 1ull);
             atomicAdd(&a.ctr->sum_cols, (unsigned long long)q);
             atomicAdd(&a.ctr->n_rejected, (unsigned long long)rejected);
             atomicAdd(&a.ctr->done, 1);
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -422,42 +447,39 @@ __global__ void k_fallback_collect(SolveArgs a) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(128) k_fallback_solve(SolveArgs a, size_t per_warp, int alpha_bytes) {
+__global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
-    signed char* alpha = reinterpret_cast<signed char*>(smem);
-    for (int e = threadIdx.x; e < a.M * D; e += blockDim.x) alpha[e] = a.alpha[e];
+    const Basis bs = load_basis(smem, a.basis, a.M, D);
+    StencilSmem sm;
+    carve<D>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
     __syncthreads();
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    WarpSmem sm;
-    carve<D>(smem + alpha_bytes, wib, per_warp, a.n, a.K, a.qcap, a.stride, sm);
+    const int tid = threadIdx.x;
     const int count = *((volatile int*)&a.ctr->fb_count);
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int w = blockIdx.x * (blockDim.x >> 5) + wib; w < count; w += nw) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int i = a.fb_list[w];
-        for (int t = lane; t < a.n; t += 32) sm.colof[t] = (t == 0) ? 0 : -1;
-        if (lane == 0) sm.cols[0] = 0;
-        __syncwarp();
-        const bool ok = solve_local<D>(a, alpha, i, 1, sm, lane);
-        if (!ok && lane == 0) {
-            atomicAdd(&a.ctr->n_singular, 1);
-            set_error(a.ctr, RBFFD_ESINGULAR);
-        }
-        double lam = 0.0;
-        if (ok)
-            for (int r = 0; r < a.n; ++r) lam = __dadd_rn(lam, fabs(sm.A[r * a.stride + a.K]));
+        for (int t = tid; t < a.n; t += kNT) sm.colof[t] = (t == 0) ? 0 : -1;
+        if (tid == 0) sm.cols[0] = 0;
+        __syncthreads();
+        const bool ok = solve_local<D>(a, bs, i, 1, sm);
+        if (ok) lebesgue_values(a, 1, sm);
+        __syncthreads();
         double r2c = a.rho2[i];
         if (!(r2c > 0.0)) r2c = 1.0;
         const double inv_r2 = 1.0 / r2c;
         const long long slot = a.slot_off[i];
-        for (int r = lane; r < a.n; r += 32)
-            a.slot_w[slot * a.n + r] = ok ? sm.A[r * a.stride + a.K] * inv_r2
-                                          : __longlong_as_double(0x7ff8000000000000LL);
-        if (lane == 0) {
-            a.slot_lam[slot] = ok ? lam : __longlong_as_double(0x7ff8000000000000LL);
+        for (int r = tid; r < a.n; r += kNT)
+            a.slot_w[slot * a.n + r] = ok ? sm.A[r * a.stride + a.K] * inv_r2 : nan;
+        if (tid == 0) {
+            a.slot_lam[slot] = ok ? sm.lam[0] : nan;
+            if (!ok) {
+                atomicAdd(&a.ctr->n_singular, 1);
+                set_error(a.ctr, RBFFD_ESINGULAR);
+            }
             atomicAdd(&a.ctr->n_fallback, 1ull);
             atomicAdd(&a.ctr->sum_cols, 1ull);
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -540,18 +562,17 @@ static int sm_count() {
 }
 
 template <int D>
-static int traversal(const SolveArgs& a, const int* indeg, int wpb, cudaStream_t s, int* launches,
+static int traversal(const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
                      cudaEvent_t ev0, cudaEvent_t ev1) {
     int stride = 0;
-    const size_t per_warp = solve_smem_per_warp(a.n, a.K, a.qcap, D, &stride);
-    const int alpha_bytes = (a.M * D + 15) & ~15;
-    const size_t smem = alpha_bytes + per_warp * wpb;
+    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, &stride);
+    const int basis_bytes = (int)basis_smem_bytes(a.M, D);
+    const size_t smem = basis_bytes + per_cta;
     if (RB_CUDA(cudaFuncSetAttribute(k_traversal<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem)))
         return RBFFD_EINVAL;
     int per_sm = 0;
-    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traversal<D>, wpb * 32,
-                                                              smem)) ||
+    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traversal<D>, kNT, smem)) ||
         per_sm < 1)
         return RBFFD_EINVAL;
     const int tb = 256, nb = (a.N + tb - 1) / tb;
@@ -559,23 +580,23 @@ static int traversal(const SolveArgs& a, const int* indeg, int wpb, cudaStream_t
                                        a.fb_flag);
     k_traversal_seed<<<nb, tb, 0, s>>>(a, indeg);
     *launches += 2;
-    int grid = per_sm * sm_count();
+    const int grid = min(per_sm * sm_count(), a.N);
     SolveArgs aa = a;
-    size_t pw = per_warp;
-    int ab = alpha_bytes;
-    void* args[] = {&aa, &pw, &ab};
+    size_t pc = per_cta;
+    int bb = basis_bytes;
+    void* args[] = {&aa, &pc, &bb};
     if (ev0) cudaEventRecord(ev0, s);
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_traversal<D>, dim3(grid),
-                                                dim3(wpb * 32), args, smem, s);
+                                                dim3(kNT), args, smem, s);
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
     return RB_CUDA(e);
 }
 
-int launch_traversal(int D, const SolveArgs& a, const int* indeg, int wpb, cudaStream_t s,
-                     int* launches, cudaEvent_t ev0, cudaEvent_t ev1) {
-    return D == 2 ? traversal<2>(a, indeg, wpb, s, launches, ev0, ev1)
-                  : traversal<3>(a, indeg, wpb, s, launches, ev0, ev1);
+int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
+                     cudaEvent_t ev0, cudaEvent_t ev1) {
+    return D == 2 ? traversal<2>(a, indeg, s, launches, ev0, ev1)
+                  : traversal<3>(a, indeg, s, launches, ev0, ev1);
 }
 
 template <int D>
@@ -583,16 +604,15 @@ static int fallback(const SolveArgs& a, cudaStream_t s, int* launches) {
     const int tb = 256, nb = (a.N + tb - 1) / tb;
     k_fallback_collect<<<nb, tb, 0, s>>>(a);
     int stride = 0;
-    const size_t per_warp = solve_smem_per_warp(a.n, a.K, a.qcap, D, &stride);
-    const int alpha_bytes = (a.M * D + 15) & ~15;
-    const int wpb = 2;
-    const size_t smem = alpha_bytes + per_warp * wpb;
+    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, &stride);
+    const int basis_bytes = (int)basis_smem_bytes(a.M, D);
+    const size_t smem = basis_bytes + per_cta;
     if (RB_CUDA(cudaFuncSetAttribute(k_fallback_solve<D>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return RBFFD_EINVAL;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback_solve<D>, wpb * 32, smem);
-    k_fallback_solve<D><<<max(per_sm, 1) * sm_count(), wpb * 32, smem, s>>>(a, per_warp, alpha_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback_solve<D>, kNT, smem);
+    k_fallback_solve<D><<<max(per_sm, 1) * sm_count(), kNT, smem, s>>>(a, per_cta, basis_bytes);
     *launches += 2;
     return RB_LAUNCHED(__func__);
 }

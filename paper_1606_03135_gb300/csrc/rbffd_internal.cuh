@@ -108,7 +108,7 @@ struct SolveArgs {
     const double* rho2;
     const int* ball_len;
     const long long* slot_off;
-    const signed char* alpha;  // [M][D] monomial exponents, graded order
+    const short* basis;        // monomial recurrence and Laplacian tables (see assemble.cu)
     int N, n, M, K, m, ell;
     int qcap;                  // columns room per stencil
     int stride;                // row stride of the local system in shared memory (odd)
@@ -130,9 +130,10 @@ struct SolveArgs {
     DevCounters* ctr;
 };
 
-size_t solve_smem_per_warp(int n, int K, int qcap, int D, int* stride_out);
-int launch_traversal(int D, const SolveArgs& a, const int* indeg, int warps_per_block,
-                     cudaStream_t s, int* launches, cudaEvent_t ev0, cudaEvent_t ev1);
+size_t solve_smem_per_cta(int n, int K, int qcap, int D, int* stride_out);
+size_t basis_smem_bytes(int M, int D);
+int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
+                     cudaEvent_t ev0, cudaEvent_t ev1);
 int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches);
 int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* val,
                     double* lam_row, unsigned char* is_center, cudaStream_t s, int* launches);
