@@ -40,10 +40,11 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def _workload():
+def _workload(name=None):
     from paper_1606_03135_gb300 import nodesets as NS
-    w = NS.WORKLOADS[WORKLOAD]
-    return NS.make(WORKLOAD), w
+    name = name or WORKLOAD
+    w = NS.WORKLOADS[name]
+    return NS.make(name), w
 
 
 class ClockSampler:
@@ -173,8 +174,9 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     from paper_1606_03135_gb300 import rbffd as R
     R.load()
-    X, w = _workload()
+    X, w = _workload(args.workload)
     N, n, ell, m, deltas = X.shape[0], w["n"], w["ell"], w["m"], w["deltas"]
+    d = X.shape[1]
     Xd = torch.from_numpy(X).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -271,7 +273,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "d": 2, "n": n, "ell": ell, "m": m,
+        "config": {"workload": args.workload or WORKLOAD, "N": N, "d": d, "n": n, "ell": ell, "m": m,
                    "deltas": list(deltas), "stab": "seq",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -296,6 +298,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=None,
+                    help="another named node-set workload (default: the 2D delta sweep)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

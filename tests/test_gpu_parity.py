@@ -218,3 +218,79 @@ def test_bounded_wait_runs_out_and_context_survives():
         assert e.value.code == R.ETIMEOUT
     assert time.time() - t0 < 30
     compare(X, 12, 2, 3, 0.5)  # the context is still usable
+
+
+# ------------------------------------------------------------------ 3D workload
+@pytest.mark.slow
+def test_ball3d_N20000_full_oracle_all_deltas():
+    # exact structure in 3D at a size the oracle finishes in seconds
+    X = NS.ball3d(20000, seed=3)
+    nbr, d2 = O.knn(X, 45)
+    for delta in (1.0, 0.4, 0.2):
+        ref = O.assemble(X, 45, 3, 7, delta, O.STAB_SEQ, nbr, d2)
+        ref["nbr"], ref["d2"] = nbr, d2
+        compare(X, 45, 3, 7, delta, ref=ref)
+
+
+def _lebesgue_accepts(X, nbr_j, ell, m, xi):
+    """Oracle's Lebesgue test of stencil nbr_j (center nbr_j[0]) at point xi."""
+    W, lam = O.local_weights(X, nbr_j, ell, m, np.stack([X[nbr_j[0]], xi]))
+    return lam[1] <= lam[0], abs(lam[0] - lam[1]) / lam[0]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("delta", [1.0, 0.4, 0.2])
+def test_ball3d_N100000_sampled(delta):
+    """Full-size 3D workload, in the launch configuration the benchmark uses.  The oracle
+    checks sampled stencils, sampled rows, and the properties that characterise the
+    traversal uniquely: a node is a center iff no earlier center keeps it; a kept row
+    belongs to the earliest center keeping it."""
+    X = NS.ball3d(100000, seed=3)
+    n, ell, m = 45, 3, 7
+    g = gpu_run(X, n, ell, m, delta)
+    N = X.shape[0]
+    rng = NS.permutation(17, N)
+    # kNN and balls on sampled nodes, by brute force
+    for k in rng[:300]:
+        diff = X[k][None, :] - X
+        s = diff[:, 0] * diff[:, 0]
+        s = s + diff[:, 1] * diff[:, 1]
+        s = s + diff[:, 2] * diff[:, 2]
+        order = np.lexsort((np.arange(N), s))[:n]
+        assert np.array_equal(g["nbr"][k], order)
+        assert g["rho2"][k] == s[order[-1]]
+        f = (1.0 - delta) * (1.0 - delta)
+        assert g["ball_len"][k] == int((s[order] <= f * s[order[-1]]).sum())
+    nbr, bl, owner, isc = g["nbr"], g["ball_len"], g["owner"], g["is_center"]
+    # in-neighbours: earlier nodes whose ball holds k
+    ins = [[] for _ in range(N)]
+    for j in range(N):
+        for t in range(1, bl[j]):
+            i = nbr[j, t]
+            if i > j:
+                ins[i].append(j)
+    # every row: owner is a center <= i whose ball holds i
+    assert np.all(owner <= np.arange(N))
+    assert np.all(isc[owner] == 1)
+    near = 0
+    for i in rng[:400]:
+        o = owner[i]
+        assert i == o or i in nbr[o, :bl[o]]
+        earlier = sorted(j for j in ins[i] if isc[j] == 1 and j < (o if o != i else i))
+        for j in earlier:  # no earlier center keeps i
+            acc, margin = _lebesgue_accepts(X, nbr[j], ell, m, X[i])
+            if margin <= 1e-9:
+                near += 1
+                continue
+            assert not acc, (i, j)
+        if o != i:
+            acc, margin = _lebesgue_accepts(X, nbr[o], ell, m, X[i])
+            assert acc or margin <= 1e-9
+        # the row's weights are the owner stencil's weights at x_i
+        W, _ = O.local_weights(X, nbr[o], ell, m, X[i:i + 1])
+        order = np.argsort(nbr[o])
+        a = g["val"][i * n:(i + 1) * n]
+        assert np.array_equal(g["col"][i * n:(i + 1) * n], nbr[o][order])
+        assert np.abs(a - W[order, 0]).max() <= TOL * np.abs(W).max()
+    assert near == 0
+    assert g["stats"]["status"] == 0
