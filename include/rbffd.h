@@ -45,6 +45,12 @@ extern "C" {
 #define RBFFD_STAB_FALLBACK 2 /* coverage as OFF; a node failing the test gets its row from
                                  its own delta = 1 stencil */
 
+/* Factorization of the local symmetric saddle-point system (§4.1, §4.3 "one matrix
+ * decomposition").  LDLT: symmetric indefinite LDL^T with Bunch-Kaufman pivoting,
+ * (1/3) K^3 flops; LU: partial-pivot LU, (2/3) K^3 flops.  Same weights up to rounding. */
+#define RBFFD_FACTOR_LDLT 0
+#define RBFFD_FACTOR_LU 1
+
 typedef struct {
     int stab_mode;      /* RBFFD_STAB_* */
     int nodes_on_host;  /* 1: `nodes` is a host pointer, copied to the device by rbffd_plan */
@@ -53,6 +59,7 @@ typedef struct {
                            errors; 0: fully asynchronous, errors surface in rbffd_stats */
     int fault_inject;   /* tests only: 1 = seed no work, so every traversal wait runs out and
                            rbffd_assemble returns RBFFD_ETIMEOUT after timeout_ms; 0 = off */
+    int factor;         /* RBFFD_FACTOR_LDLT (default) or RBFFD_FACTOR_LU */
 } rbffd_opts;
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */
@@ -78,8 +85,9 @@ typedef struct {
     int64_t n_singular;     /* stencils with an exactly zero pivot */
     int32_t status;         /* device status of the last assemble (RBFFD_OK or an error) */
     int32_t n, M, K, d;     /* stencil size, monomials, n + M, dimension */
-    double alg_flops;       /* paper's cost model for the result: sum over centers of
-                               (2/3) K^3 + 2 K^2 q_k  (§4.3), q_k = rows the center kept */
+    double alg_flops;       /* §4.3 cost model for the result: sum over factored stencils of
+                               c K^3 + 2 K^2 q_k, q_k = rows the stencil kept, c = 1/3 (LDLT)
+                               or 2/3 (LU) */
     int64_t n_launches;     /* kernels this plan has launched so far (cumulative) */
     float ms_stencils;      /* device time of the kNN/retention-ball phase of rbffd_plan */
     float ms_traversal;     /* device time of the traversal + local-solve kernel */

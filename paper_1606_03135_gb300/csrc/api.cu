@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "rbffd_internal.cuh"
@@ -29,8 +30,9 @@ struct rbffd_plan_s {
     long long* slot_off = nullptr;
     short* basis = nullptr;  // monomial recurrence + Laplacian tables, M * (2 + 2d)
     DevCounters* ctr = nullptr;
-    DevCounters* h_ctr = nullptr;  // pinned
-    long long* h_slots = nullptr;  // pinned
+    DevCounters h_ctr{};           // host copy of the device counters
+    void* plan_block = nullptr;    // one allocation for the stencil arrays
+    void* asm_block = nullptr;     // one allocation for the traversal and CSR arrays
     int max_ball = 0;
     long long total_slots = 0;
     int qcap = 0, stride = 0;
@@ -52,6 +54,7 @@ struct rbffd_plan_s {
     unsigned char* is_center = nullptr;
     cudaEvent_t ev[8] = {};
     int launches = 0;
+    bool counters_fresh = false;
 };
 
 namespace rbffd {
@@ -68,17 +71,57 @@ namespace {
 
 #define bad(e) RB_CUDA(e)
 
-template <typename T>
-int alloc(T** p, size_t count, cudaStream_t s) {
+// One stream-ordered memory pool per device, owned by the library, that keeps freed blocks
+// cached (release threshold = unlimited): repeated plans on a device reuse memory without
+// returning to the driver.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+int pool_for(int dev, cudaMemPool_t* out) {
+    if (dev < 0 || dev >= kMaxDevices) return RBFFD_ECUDA;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        int rc = bad(cudaMemPoolCreate(&pool, &props));
+        if (rc) return rc;
+        uint64_t thr = ~0ull;
+        if ((rc = bad(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr)))) {
+            cudaMemPoolDestroy(pool);
+            return rc;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return RBFFD_OK;
+}
+
+// Lays several arrays out in one allocation, each on a 256-byte boundary.
+struct Carver {
+    size_t bytes = 0;
+    template <typename T>
+    size_t add(size_t count) {
+        const size_t off = bytes;
+        bytes += (count * sizeof(T) + 255) & ~size_t(255);
+        return off;
+    }
+};
+
+int pool_alloc(void** p, size_t bytes, int dev, cudaStream_t s) {
     *p = nullptr;
-    if (count == 0) count = 1;
-    return bad(cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), s));
+    cudaMemPool_t pool;
+    int rc = pool_for(dev, &pool);
+    if (rc) return rc;
+    return bad(cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, s));
 }
 
 template <typename T>
-void release(T** p, cudaStream_t s) {
-    if (*p) cudaFreeAsync(*p, s);
-    *p = nullptr;
+T* at(void* base, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(base) + off);
 }
 
 long long binom(int a, int b) {
@@ -159,11 +202,8 @@ int basis_tables(int d, int ell, short* out) {
 }
 
 void free_assemble(rbffd_plan_s* p, cudaStream_t s) {
-    release(&p->state, s); release(&p->pending, s); release(&p->owner, s);
-    release(&p->queue, s); release(&p->fb_flag, s); release(&p->fb_list, s);
-    release(&p->slot_w, s); release(&p->slot_lam, s); release(&p->slot_pass, s);
-    release(&p->row_ptr, s); release(&p->col, s); release(&p->val, s);
-    release(&p->lam_row, s); release(&p->is_center, s);
+    if (p->asm_block) cudaFreeAsync(p->asm_block, s);
+    p->asm_block = nullptr;
     p->have_asm = false;
     p->assembled = false;
 }
@@ -171,16 +211,24 @@ void free_assemble(rbffd_plan_s* p, cudaStream_t s) {
 void free_plan(rbffd_plan_s* p) {
     if (!p) return;
     cudaStream_t s = p->last;
-    if (s) cudaStreamSynchronize(s);
     free_assemble(p, s);
-    release(&p->X, s); release(&p->nbr, s); release(&p->rho2, s); release(&p->ball_len, s);
-    release(&p->indeg, s); release(&p->slot_off, s); release(&p->basis, s); release(&p->ctr, s);
+    if (p->plan_block) cudaFreeAsync(p->plan_block, s);
     cudaStreamSynchronize(s);
-    if (p->h_ctr) cudaFreeHost(p->h_ctr);
-    if (p->h_slots) cudaFreeHost(p->h_slots);
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
     delete p;
+}
+
+// Copy the device counters of the last call to the host (waits for the plan's stream).
+int refresh_counters(rbffd_plan_s* p) {
+    if (p->counters_fresh) return RBFFD_OK;
+    int rc;
+    if ((rc = bad(cudaMemcpyAsync(&p->h_ctr, p->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                  p->last))) ||
+        (rc = bad(cudaStreamSynchronize(p->last))))
+        return rc;
+    p->counters_fresh = true;
+    return RBFFD_OK;
 }
 
 int max_optin_smem() {
@@ -218,9 +266,10 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
         return RBFFD_EINVAL;
     const int M = (int)binom(ell + d, d);
     if (M > n) return RBFFD_EINVAL;
-    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0};
+    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT};
     if (opts) o = *opts;
-    if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1)
+    if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
+        (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU))
         return RBFFD_EINVAL;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
 
@@ -240,15 +289,23 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     const size_t basis_count = (size_t)M * (2 + 2 * d);
     for (auto& e : p->ev)
         if ((rc = bad(cudaEventCreate(&e))) != RBFFD_OK) goto fail;
-    if ((rc = bad(cudaMallocHost(reinterpret_cast<void**>(&p->h_ctr), sizeof(DevCounters)))) ||
-        (rc = bad(cudaMallocHost(reinterpret_cast<void**>(&p->h_slots), sizeof(long long)))))
-        goto fail;
-    if ((rc = alloc(&p->X, (size_t)N * d, s)) || (rc = alloc(&p->nbr, (size_t)N * n, s)) ||
-        (rc = alloc(&p->rho2, (size_t)N, s)) || (rc = alloc(&p->ball_len, (size_t)N, s)) ||
-        (rc = alloc(&p->indeg, (size_t)N, s)) || (rc = alloc(&p->slot_off, (size_t)N + 1, s)) ||
-        (rc = alloc(&p->basis, basis_count, s)) || (rc = alloc(&p->ctr, 1, s)))
-        goto fail;
-    if ((rc = bad(cudaMallocAsync(&scratch, sbytes, s)))) goto fail;
+    {
+        Carver c;
+        const size_t oX = c.add<double>((size_t)N * d), oN = c.add<int>((size_t)N * n),
+                     oR = c.add<double>((size_t)N), oB = c.add<int>((size_t)N),
+                     oI = c.add<int>((size_t)N), oS = c.add<long long>((size_t)N + 1),
+                     oP = c.add<short>(basis_count), oC = c.add<DevCounters>(1);
+        if ((rc = pool_alloc(&p->plan_block, c.bytes, p->device, s))) goto fail;
+        p->X = at<double>(p->plan_block, oX);
+        p->nbr = at<int>(p->plan_block, oN);
+        p->rho2 = at<double>(p->plan_block, oR);
+        p->ball_len = at<int>(p->plan_block, oB);
+        p->indeg = at<int>(p->plan_block, oI);
+        p->slot_off = at<long long>(p->plan_block, oS);
+        p->basis = at<short>(p->plan_block, oP);
+        p->ctr = at<DevCounters>(p->plan_block, oC);
+    }
+    if ((rc = pool_alloc(&scratch, sbytes, p->device, s))) goto fail;
     if ((rc = bad(cudaMemcpyAsync(p->X, nodes, (size_t)N * d * sizeof(double),
                                   o.nodes_on_host ? cudaMemcpyHostToDevice
                                                   : cudaMemcpyDeviceToDevice,
@@ -266,17 +323,20 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     rc = launch_scan_i32_to_i64(p->ball_len, p->slot_off, Ni, s, &p->launches);
     if (rc) goto fail;
     cudaEventRecord(p->ev[1], s);
-    if ((rc = bad(cudaMemcpyAsync(p->h_ctr, p->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
-                                  s))) ||
-        (rc = bad(cudaMemcpyAsync(p->h_slots, p->slot_off + N, sizeof(long long),
-                                  cudaMemcpyDeviceToHost, s))))
-        goto fail;
     cudaFreeAsync(scratch, s);
     scratch = nullptr;
-    if ((rc = bad(cudaStreamSynchronize(s)))) goto fail;
-    if (p->h_ctr->status) { rc = p->h_ctr->status; goto fail; }
-    p->max_ball = p->h_ctr->max_ball;
-    p->total_slots = *p->h_slots;
+    {
+        long long slots = 0;  // pageable copies: each returns once the stream has reached it
+        if ((rc = bad(cudaMemcpyAsync(&p->h_ctr, p->ctr, sizeof(DevCounters),
+                                      cudaMemcpyDeviceToHost, s))) ||
+            (rc = bad(cudaMemcpyAsync(&slots, p->slot_off + N, sizeof(long long),
+                                      cudaMemcpyDeviceToHost, s))) ||
+            (rc = bad(cudaStreamSynchronize(s))))
+            goto fail;
+        p->total_slots = slots;
+    }
+    if (p->h_ctr.status) { rc = p->h_ctr.status; goto fail; }
+    p->max_ball = p->h_ctr.max_ball;
     p->qcap = p->max_ball < 1 ? 1 : p->max_ball;
     {
         int stride = 0;
@@ -301,18 +361,24 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     const size_t N = (size_t)p->N, n = (size_t)p->n;
     int rc = RBFFD_OK;
     if (!p->have_asm) {
-        if ((rc = alloc(&p->state, N, s)) || (rc = alloc(&p->pending, N, s)) ||
-            (rc = alloc(&p->owner, N, s)) || (rc = alloc(&p->queue, N, s)) ||
-            (rc = alloc(&p->fb_flag, N, s)) || (rc = alloc(&p->fb_list, N, s)) ||
-            (rc = alloc(&p->slot_w, (size_t)p->total_slots * n, s)) ||
-            (rc = alloc(&p->slot_lam, (size_t)p->total_slots, s)) ||
-            (rc = alloc(&p->slot_pass, (size_t)p->total_slots, s)) ||
-            (rc = alloc(&p->row_ptr, N + 1, s)) || (rc = alloc(&p->col, N * n, s)) ||
-            (rc = alloc(&p->val, N * n, s)) || (rc = alloc(&p->lam_row, N, s)) ||
-            (rc = alloc(&p->is_center, N, s))) {
-            free_assemble(p, s);
-            return rc;
-        }
+        const size_t S = (size_t)p->total_slots;
+        Carver c;
+        const size_t o_state = c.add<int>(N), o_pend = c.add<int>(N), o_own = c.add<int>(N),
+                     o_q = c.add<int>(N), o_fbf = c.add<unsigned char>(N),
+                     o_fbl = c.add<int>(N), o_sw = c.add<double>(S * n),
+                     o_sl = c.add<double>(S), o_sp = c.add<unsigned char>(S),
+                     o_rp = c.add<long long>(N + 1), o_col = c.add<int>(N * n),
+                     o_val = c.add<double>(N * n), o_lam = c.add<double>(N),
+                     o_isc = c.add<unsigned char>(N);
+        if ((rc = pool_alloc(&p->asm_block, c.bytes, p->device, s))) return rc;
+        void* b = p->asm_block;
+        p->state = at<int>(b, o_state); p->pending = at<int>(b, o_pend);
+        p->owner = at<int>(b, o_own); p->queue = at<int>(b, o_q);
+        p->fb_flag = at<unsigned char>(b, o_fbf); p->fb_list = at<int>(b, o_fbl);
+        p->slot_w = at<double>(b, o_sw); p->slot_lam = at<double>(b, o_sl);
+        p->slot_pass = at<unsigned char>(b, o_sp); p->row_ptr = at<long long>(b, o_rp);
+        p->col = at<int>(b, o_col); p->val = at<double>(b, o_val);
+        p->lam_row = at<double>(b, o_lam); p->is_center = at<unsigned char>(b, o_isc);
         p->have_asm = true;
     }
     SolveArgs a{};
@@ -326,6 +392,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.fb_flag = p->fb_flag; a.fb_list = p->fb_list;
     a.slot_w = p->slot_w; a.slot_lam = p->slot_lam; a.slot_pass = p->slot_pass; a.ctr = p->ctr;
     a.no_seed = p->opts.fault_inject == 1;
+    a.factor = p->opts.factor;
     if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
     rc = launch_traversal(p->d, a, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
     if (rc) return rc;
@@ -339,10 +406,8 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
                          &p->launches);
     if (rc) return rc;
     cudaEventRecord(p->ev[6], s);
-    if ((rc = bad(cudaMemcpyAsync(p->h_ctr, p->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
-                                  s))))
-        return rc;
     p->assembled = true;
+    p->counters_fresh = false;
     if (out) {
         out->n_rows = p->N;
         out->nnz = p->N * p->n;
@@ -351,8 +416,8 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
         out->val = p->val;
     }
     if (p->opts.sync) {
-        if ((rc = bad(cudaStreamSynchronize(s)))) return rc;
-        return p->h_ctr->status;
+        if ((rc = refresh_counters(p))) return rc;
+        return p->h_ctr.status;
     }
     return RBFFD_OK;
 }
@@ -366,10 +431,10 @@ int rbffd_apply(rbffd_plan_t p, const double* u, double* y, void* stream) {
 
 int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
     if (!p || !out) return RBFFD_EINVAL;
-    int rc = bad(cudaStreamSynchronize(p->last));
+    int rc = p->assembled ? refresh_counters(p) : bad(cudaStreamSynchronize(p->last));
     if (rc) return rc;
     memset(out, 0, sizeof(*out));
-    const DevCounters& c = *p->h_ctr;
+    const DevCounters& c = p->h_ctr;
     out->n_nodes = p->N;
     out->max_ball = p->max_ball;
     out->n = p->n; out->M = p->M; out->K = p->K; out->d = p->d;
@@ -384,7 +449,8 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
         out->n_singular = c.n_singular;
         out->status = c.status;
         const double K = p->K;
-        const double lu = 2.0 / 3.0 * K * K * K, col = 2.0 * K * K;
+        const double c3 = p->opts.factor == RBFFD_FACTOR_LU ? 2.0 / 3.0 : 1.0 / 3.0;
+        const double lu = c3 * K * K * K, col = 2.0 * K * K;
         out->alg_flops = (double)c.n_centers * lu + (double)(p->N - (int64_t)c.n_fallback) * col +
                          (double)c.n_fallback * (lu + col);
         if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) out->ms_traversal = ms;

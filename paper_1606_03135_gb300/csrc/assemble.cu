@@ -33,7 +33,14 @@ constexpr int kNT = 128;  // threads per stencil team: one warp per SM sub-parti
 struct StencilSmem {
     double* A;      // K rows x stride: [A P | B ; P^T 0 | B_psi]
     double* xi;     // n x D scaled stencil coordinates
-    double* rdiag;  // K reciprocal pivots
+    double* rdiag;  // K reciprocal pivots (LDL^T: 1x1 reciprocal or 2x2 inverse entry 00)
+    double* dinv1;  // K  LDL^T 2x2 inverse entry 01
+    double* dinv2;  // K  LDL^T 2x2 inverse entry 11
+    double* wv;     // K  unscaled pivot column(s) of the current LDL^T step
+    double* wv2;    // K
+    int* perm;      // K  original unknown held by each row (symmetric pivoting)
+    int* rowof;     // K  row holding each original unknown
+    unsigned char* pk;  // K  1: 1x1 pivot, 2: first row of a 2x2 pivot, 0: its second row
     double* lam;    // qcap Lebesgue values of the solved columns
     int* cols;      // qcap ball position of each solved column
     int* colof;     // n column of each ball position, or -1
@@ -54,8 +61,9 @@ size_t solve_smem_per_cta(int n, int K, int qcap, int D, int* stride_out) {
     int stride = K + qcap;
     if ((stride & 1) == 0) ++stride;  // odd row stride: column walks hit distinct banks
     if (stride_out) *stride_out = stride;
-    size_t b = (size_t)K * stride * 8 + (size_t)n * D * 8 + (size_t)K * 8 + (size_t)qcap * 8 +
-               (size_t)(qcap + n) * 4 + (size_t)qcap;
+    size_t b = (size_t)K * stride * 8 + (size_t)n * D * 8 + (size_t)K * 5 * 8 +
+               (size_t)qcap * 8 + (size_t)(qcap + n) * 4 + (size_t)K * 2 * 4 + (size_t)K +
+               (size_t)qcap;
     return (b + 15) & ~size_t(15);
 }
 
@@ -69,12 +77,26 @@ __device__ __forceinline__ void carve(char* p, int n, int K, int qcap, int S, St
     p += (size_t)n * D * 8;
     sm.rdiag = reinterpret_cast<double*>(p);
     p += (size_t)K * 8;
+    sm.dinv1 = reinterpret_cast<double*>(p);
+    p += (size_t)K * 8;
+    sm.dinv2 = reinterpret_cast<double*>(p);
+    p += (size_t)K * 8;
+    sm.wv = reinterpret_cast<double*>(p);
+    p += (size_t)K * 8;
+    sm.wv2 = reinterpret_cast<double*>(p);
+    p += (size_t)K * 8;
     sm.lam = reinterpret_cast<double*>(p);
     p += (size_t)qcap * 8;
     sm.cols = reinterpret_cast<int*>(p);
     p += (size_t)qcap * 4;
     sm.colof = reinterpret_cast<int*>(p);
     p += (size_t)n * 4;
+    sm.perm = reinterpret_cast<int*>(p);
+    p += (size_t)K * 4;
+    sm.rowof = reinterpret_cast<int*>(p);
+    p += (size_t)K * 4;
+    sm.pk = reinterpret_cast<unsigned char*>(p);
+    p += (size_t)K;
     sm.keep = reinterpret_cast<unsigned char*>(p);
 }
 
@@ -89,14 +111,12 @@ __device__ __forceinline__ Basis load_basis(char* smem, const short* g, int M, i
     return b;
 }
 
-// Assemble and solve the local system of stencil j for the q columns in sm.cols, with the
-// whole CTA.  Returns false (uniformly) on an exactly zero pivot.  On success the first n
-// rows of the right-hand-side block of sm.A hold the weights in scaled coordinates.
+// Assemble the local system of stencil j (§4.1) and its q right-hand sides (the columns in
+// sm.cols) in shared memory, with the whole CTA.
 template <int D>
-__device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
-                            const StencilSmem& sm) {
-    __shared__ int s_ok;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+__device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q,
+                               const StencilSmem& sm) {
+    const int tid = threadIdx.x;
     const int n = a.n, M = a.M, K = a.K, S = a.stride, m = a.m;
     const int Wd = K + q;
     double r2c = a.rho2[j];
@@ -115,23 +135,34 @@ __device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
     __syncthreads();
     // A_ab = r^m and, for solved ball members, the phi-part of the right-hand side
     // m (m + D - 2) r^(m-2) (Laplacian of r^m in D dimensions), pair by pair
-    {
-        int ra = 0, off = tid;
-        while (ra < n - 1 && off >= n - 1 - ra) { off -= n - 1 - ra; ++ra; }
-        while (ra < n - 1) {
-            const int rb = ra + 1 + off;
-            const double r2 = sqdist_rn<D>(sm.xi + ra * D, sm.xi + rb * D);
-            const double r = sqrt(r2);
-            double pm2 = r;
-            for (int s = 0; s < (m - 3) / 2; ++s) pm2 = __dmul_rn(pm2, r2);
-            const double pm = __dmul_rn(pm2, r2);
-            sm.A[ra * S + rb] = pm;
-            sm.A[rb * S + ra] = pm;
-            const int ca = sm.colof[ra], cb = sm.colof[rb];
-            if (cb >= 0) sm.A[ra * S + K + cb] = __dmul_rn(a.coef, pm2);
-            if (ca >= 0) sm.A[rb * S + K + ca] = __dmul_rn(a.coef, pm2);
-            off += kNT;
-            while (ra < n - 1 && off >= n - 1 - ra) { off -= n - 1 - ra; ++ra; }
+    // (pairs a < b; row a of the strict upper triangle has n-1-a entries, and rows a and
+    // n-2-a together have n, so the flattened index steps in O(1))
+    if (n > 1) {
+        const int rows = n - 1, L2 = n;
+        const int total = ((rows + 1) >> 1) * L2;
+        int pr = tid / L2, off = tid - (tid / L2) * L2;
+        const int di = kNT / L2, dj = kNT - di * L2;
+        for (int e = tid; e < total; e += kNT) {
+            const int len0 = rows - pr;
+            const bool first = off < len0;
+            const int ra = first ? pr : rows - 1 - pr;
+            const int t = first ? off : off - len0;
+            if (first || ra != pr) {
+                const int rb = ra + 1 + t;
+                const double r2 = sqdist_rn<D>(sm.xi + ra * D, sm.xi + rb * D);
+                const double r = sqrt(r2);
+                double pm2 = r;
+                for (int s = 0; s < (m - 3) / 2; ++s) pm2 = __dmul_rn(pm2, r2);
+                const double pm = __dmul_rn(pm2, r2);
+                sm.A[ra * S + rb] = pm;
+                sm.A[rb * S + ra] = pm;
+                const int ca = sm.colof[ra], cb = sm.colof[rb];
+                if (cb >= 0) sm.A[ra * S + K + cb] = __dmul_rn(a.coef, pm2);
+                if (ca >= 0) sm.A[rb * S + K + ca] = __dmul_rn(a.coef, pm2);
+            }
+            pr += di;
+            off += dj;
+            if (off >= L2) { off -= L2; ++pr; }
         }
     }
     // P: one stencil point per thread, each monomial = an earlier one times one coordinate
@@ -159,7 +190,27 @@ __device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
         sm.A[(n + l) * S + K + c] = s;
     }
     __syncthreads();
+}
 
+// A float close to the non-negative double with IEEE bits `b` (top 23 mantissa bits,
+// exponent clamped to the float range), built with integer operations only.
+__device__ __forceinline__ float approx_f32(unsigned long long b) {
+    const int e = (int)(b >> 52) - 1023;
+    if (b == 0ull) return 0.0f;
+    const int ef = e < -126 ? -126 : (e > 127 ? 127 : e);
+    const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
+    return __int_as_float((int)(((unsigned)(ef + 127) << 23) | mant));
+}
+
+// LU with partial pivoting of [A_hat | B_hat] (the paper's decomposition, §4.3 cost model
+// (2/3) K^3 + 2 K^2 q), then back substitution.  Returns false (uniformly) on an exactly zero
+// pivot; on success row r of the right-hand-side block holds unknown r.
+__device__ bool factor_solve_lu(const SolveArgs& a, int q, const StencilSmem& sm) {
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int K = a.K, S = a.stride;
+    const int Wd = K + q;
+    for (int r = tid; r < K; r += kNT) sm.rowof[r] = r;
     // Gaussian elimination with partial pivoting on [A_hat | B_hat]; the pivot search, row
     // swap, reciprocal and multipliers are done by warp 0 alone (FP64 work counts per warp
     // instruction, so the other warps must not repeat it)
@@ -236,12 +287,215 @@ __device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
     return true;
 }
 
+
+// Symmetric indefinite LDL^T factorization with Bunch-Kaufman partial pivoting (J. R. Bunch
+// and L. Kaufman, "Some stable methods for calculating inertia and solving symmetric linear
+// systems", Math. Comp. 31 (1977)) of the symmetric saddle-point matrix [A P; P^T 0], with
+// the right-hand sides carried along; (1/3) K^3 + 2 K^2 q flops.  Only the lower triangle is
+// referenced.  1x1 and 2x2 pivots; symmetric row/column swaps are tracked in sm.perm.
+// Pivot tests use alpha = (1 + sqrt(17)) / 8.  Returns false (uniformly) on an exactly
+// singular pivot column.  On success sm.rowof[u] is
+// the row of the right-hand-side block that holds unknown u.
+__device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& sm) {
+    __shared__ int s_ok, s_kind;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int K = a.K, S = a.stride;
+    double* A = sm.A;
+    for (int r = tid; r < K; r += kNT) sm.perm[r] = r;
+    __syncthreads();
+    int p = 0;
+    while (p < K) {
+        if (wid == 0) {
+            // lambda = max |A[i][p]|, i > p, lowest index on ties
+            unsigned long long lv = 0ull;
+            int r = 0x7fffffff;
+            for (int i = p + 1 + lane; i < K; i += 32) {
+                const unsigned long long v =
+                    (unsigned long long)__double_as_longlong(A[i * S + p]) & 0x7fffffffffffffffull;
+                if (v > lv || (v == lv && i < r)) { lv = v; r = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ov = __shfl_xor_sync(0xffffffffu, lv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, r, o);
+                if (ov > lv || (ov == lv && oi < r)) { lv = ov; r = oi; }
+            }
+            // the pivot choice only has to be a valid Bunch-Kaufman choice, so the tests run in
+            // FP32 on values rebuilt from the FP64 bit patterns (no FP64 instructions)
+            const unsigned long long pv =
+                (unsigned long long)__double_as_longlong(A[p * S + p]) & 0x7fffffffffffffffull;
+            const float lam = approx_f32(lv), app = approx_f32(pv);
+            const float af = 0.6403882f;
+            int kind = 1, swap_a = p, swap_b = p;
+            bool ok = true;
+            if (lv == 0ull) {
+                ok = pv != 0ull;  // column already eliminated: 1x1 pivot if nonzero
+            } else if (!(app >= af * lam)) {
+                // sigma = max |A_rj| over the active part of row/column r, j != r
+                unsigned long long sv = 0ull;
+                for (int jj = p + lane; jj < K; jj += 32) {
+                    if (jj == r) continue;
+                    const double v = jj < r ? A[r * S + jj] : A[jj * S + r];
+                    const unsigned long long b =
+                        (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+                    sv = b > sv ? b : sv;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, sv, o);
+                    sv = ov > sv ? ov : sv;
+                }
+                const float sig = approx_f32(sv);
+                const float arr = approx_f32(
+                    (unsigned long long)__double_as_longlong(A[r * S + r]) & 0x7fffffffffffffffull);
+                if (app * sig >= af * lam * lam) {
+                    kind = 1;
+                } else if (arr >= af * sig) {
+                    kind = 1; swap_a = p; swap_b = r;
+                } else {
+                    kind = 2; swap_a = p + 1; swap_b = r;
+                }
+            }
+            if (ok && swap_a != swap_b) {
+                // symmetric swap of unknowns swap_a < swap_b in lower-triangle storage
+                const int ua = swap_a, ub = swap_b;
+                const int n1 = ua, n2 = ub - ua - 1, n3 = K - ub - 1, nq = q;
+                const int tot = n1 + n2 + n3 + nq + 1;
+                for (int e = lane; e < tot; e += 32) {
+                    double *x, *y;
+                    if (e < n1) { x = A + ua * S + e; y = A + ub * S + e; }
+                    else if (e < n1 + n2) { const int i = ua + 1 + (e - n1); x = A + i * S + ua; y = A + ub * S + i; }
+                    else if (e < n1 + n2 + n3) { const int i = ub + 1 + (e - n1 - n2); x = A + i * S + ua; y = A + i * S + ub; }
+                    else if (e < n1 + n2 + n3 + nq) { const int c = K + (e - n1 - n2 - n3); x = A + ua * S + c; y = A + ub * S + c; }
+                    else { x = A + ua * S + ua; y = A + ub * S + ub; }
+                    const double t = *x; *x = *y; *y = t;
+                }
+                if (lane == 0) { const int t = sm.perm[ua]; sm.perm[ua] = sm.perm[ub]; sm.perm[ub] = t; }
+                __syncwarp();
+            }
+            if (ok) {
+                if (kind == 1) {
+                    const double rcp = 1.0 / A[p * S + p];
+                    if (lane == 0) { sm.rdiag[p] = rcp; sm.pk[p] = 1; }
+                    for (int i = p + 1 + lane; i < K; i += 32) {
+                        const double w = A[i * S + p];
+                        sm.wv[i] = w;
+                        A[i * S + p] = w * rcp;
+                    }
+                } else {
+                    const double d0 = A[p * S + p], d1 = A[(p + 1) * S + p], d2 = A[(p + 1) * S + p + 1];
+                    const double rdet = 1.0 / fma(d0, d2, -d1 * d1);
+                    const double i00 = d2 * rdet, i01 = -d1 * rdet, i11 = d0 * rdet;
+                    if (lane == 0) {
+                        sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.dinv2[p] = i11;
+                        sm.pk[p] = 2; sm.pk[p + 1] = 0;
+                        A[(p + 1) * S + p] = 0.0;  // L has no entry inside a 2x2 pivot block
+                    }
+                    for (int i = p + 2 + lane; i < K; i += 32) {
+                        const double w1 = A[i * S + p], w2 = A[i * S + p + 1];
+                        sm.wv[i] = w1;
+                        sm.wv2[i] = w2;
+                        A[i * S + p] = fma(w1, i00, w2 * i01);
+                        A[i * S + p + 1] = fma(w1, i01, w2 * i11);
+                    }
+                }
+            }
+            if (lane == 0) { s_ok = ok ? 1 : 0; s_kind = kind; }
+        }
+        __syncthreads();
+        if (!s_ok) return false;
+        const int kind = s_kind;
+        // trailing update of the lower triangle and of the right-hand sides: row i (> p0)
+        // has (i - p0) triangle entries followed by q right-hand-side entries
+        const int p0 = p + kind - 1;
+        const int rows = K - p0 - 1;
+        if (rows > 0) {
+            // Rows r and rows-1-r are paired into one virtual row of constant length
+            // rows + 1 + 2q, so the flattened index steps in O(1) like a rectangle.  The FP64
+            // work is branch-free: source operands are selected with integer arithmetic so
+            // every lane issues the same FMA (a divergent FP64 instruction costs the whole
+            // warp on the FP64 pipe).
+            const int L2 = rows + 1 + 2 * q;
+            const int total = ((rows + 1) >> 1) * L2;
+            if (tid < total) {
+                int pr = tid / L2, off = tid - (tid / L2) * L2;
+                const int di = kNT / L2, dj = kNT - di * L2;
+                for (int e = tid; e < total; e += kNT) {
+                    const int len0 = pr + 1 + q;
+                    const bool first = off < len0;
+                    const int r = first ? pr : rows - 1 - pr;
+                    const int t = first ? off : off - len0;
+                    if (first || r != pr) {  // an odd middle row pairs with itself: once only
+                        double* Ai = A + (p0 + 1 + r) * S;
+                        const bool tri = t <= r;
+                        const int col = tri ? p0 + 1 + t : K + t - (r + 1);
+                        const double* s1 = tri ? sm.wv + col : A + p * S + col;
+                        if (kind == 1) {
+                            Ai[col] = fma(-Ai[p], *s1, Ai[col]);
+                        } else {
+                            const double* s2 = tri ? sm.wv2 + col : A + (p + 1) * S + col;
+                            Ai[col] = fma(-Ai[p + 1], *s2, fma(-Ai[p], *s1, Ai[col]));
+                        }
+                    }
+                    pr += di;
+                    off += dj;
+                    if (off >= L2) { off -= L2; ++pr; }
+                }
+            }
+        }
+        __syncthreads();
+        p += kind;
+    }
+    // D solve: 1x1 rows scale by the reciprocal pivot, 2x2 blocks multiply by their inverse
+    for (int e = tid; e < K * q; e += kNT) {
+        const int i = e / q, c = e - (e / q) * q;
+        const int k = sm.pk[i];
+        double* Bi = A + i * S + K + c;
+        if (k == 1) {
+            *Bi *= sm.rdiag[i];
+        } else if (k == 2) {
+            double* Bn = Bi + S;
+            const double y0 = *Bi, y1 = *Bn;
+            *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
+            *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
+        }
+    }
+    __syncthreads();
+    // back substitution with L^T: once x_i is final, x_j -= L[i][j] x_i for j < i
+    for (int i = K - 1; i > 0; --i) {
+        const int total = i * q;
+        if (tid < total) {
+            int jj = tid / q, cc = tid - (tid / q) * q;
+            const int dj = kNT / q, dc = kNT - dj * q;
+            const double* Li = A + i * S;
+            const double* xi = Li + K;
+#pragma unroll 4
+            for (int e = tid; e < total; e += kNT) {
+                double* xj = A + jj * S + K;
+                xj[cc] = fma(-Li[jj], xi[cc], xj[cc]);
+                jj += dj;
+                cc += dc;
+                if (cc >= q) { cc -= q; ++jj; }
+            }
+        }
+        __syncthreads();
+    }
+    for (int r = tid; r < K; r += kNT) sm.rowof[sm.perm[r]] = r;
+    __syncthreads();
+    return true;
+}
+
+template <int D>
+__device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
+                            const StencilSmem& sm) {
+    assemble_local<D>(a, bs, j, q, sm);
+    return a.factor == RBFFD_FACTOR_LU ? factor_solve_lu(a, q, sm) : factor_solve_ldlt(a, q, sm);
+}
+
 // Local L-Lebesgue value sum_r |w_r| of every solved column (one warp per column).
 __device__ __forceinline__ void lebesgue_values(const SolveArgs& a, int q, const StencilSmem& sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = wid; c < q; c += kNT / 32) {
         double s = 0.0;
-        for (int r = lane; r < a.n; r += 32) s += fabs(sm.A[r * a.stride + a.K + c]);
+        for (int r = lane; r < a.n; r += 32) s += fabs(sm.A[sm.rowof[r] * a.stride + a.K + c]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) sm.lam[c] = s;
     }
@@ -395,7 +649,7 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
             const int c = e / n, r = e - c * n;
             if (!sm.keep[c]) continue;
             a.slot_w[(base + sm.cols[c]) * n + r] =
-                ok ? sm.A[r * a.stride + a.K + c] * inv_r2 : nan;
+                ok ? sm.A[sm.rowof[r] * a.stride + a.K + c] * inv_r2 : nan;
         }
         // ownership: the earliest center keeping a row owns it
         if (tid > 0 && tid < q && sm.keep[tid]) {
@@ -469,7 +723,7 @@ __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_
         const double inv_r2 = 1.0 / r2c;
         const long long slot = a.slot_off[i];
         for (int r = tid; r < a.n; r += kNT)
-            a.slot_w[slot * a.n + r] = ok ? sm.A[r * a.stride + a.K] * inv_r2 : nan;
+            a.slot_w[slot * a.n + r] = ok ? sm.A[sm.rowof[r] * a.stride + a.K] * inv_r2 : nan;
         if (tid == 0) {
             a.slot_lam[slot] = ok ? sm.lam[0] : nan;
             if (!ok) {

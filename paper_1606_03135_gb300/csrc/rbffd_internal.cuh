@@ -115,6 +115,7 @@ struct SolveArgs {
     int mode;                  // RBFFD_STAB_*
     double coef;               // m (m + D - 2)
     int no_seed;               // fault injection: push no initial center (waits run out)
+    int factor;                // RBFFD_FACTOR_LDLT or RBFFD_FACTOR_LU
     unsigned long long timeout_ns;
     // traversal state
     int* state;

@@ -17,11 +17,12 @@ from . import build as _build
 
 OK, EINVAL, EDUPLICATE, ENOMEM, ESINGULAR, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 STAB_SEQ, STAB_OFF, STAB_FALLBACK = 0, 1, 2
+FACTOR_LDLT, FACTOR_LU = 0, 1
 
 
 class rbffd_opts(C.Structure):
     _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
-                ("sync", C.c_int), ("fault_inject", C.c_int)]
+                ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int)]
 
 
 class rbffd_csr(C.Structure):
@@ -163,7 +164,7 @@ class Plan:
     the library inside ``rbffd_plan``)."""
 
     def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
-                 stream=None, fault_inject=0):
+                 stream=None, fault_inject=0, factor=FACTOR_LDLT):
         self._plan = None
         self._stream = stream
         if isinstance(nodes, np.ndarray):
@@ -177,7 +178,7 @@ class Plan:
             on_host = 0
         self.N, self.d = self._nodes.shape
         self.n, self.ell, self.m, self.delta, self.mode = n, ell, m, delta, mode
-        opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject)
+        opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor)
         rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
                               _stream_handle(stream))
         _check(rc, "rbffd_plan")

@@ -45,8 +45,8 @@ def check_rows(g, ref, n, rows=None):
     return worst
 
 
-def compare(X, n, ell, m, delta, mode=R.STAB_SEQ, ref=None):
-    g = gpu_run(X, n, ell, m, delta, mode)
+def compare(X, n, ell, m, delta, mode=R.STAB_SEQ, ref=None, **kw):
+    g = gpu_run(X, n, ell, m, delta, mode, **kw)
     if ref is None:
         ref = O.assemble(X, n, ell, m, delta, mode)
     assert np.array_equal(g["nbr"], ref["nbr"])
@@ -83,6 +83,17 @@ def test_disk2d_N2000_other_modes(mode):
     g, ref = compare(X, 12, 2, 3, 0.5, mode)
     if mode == R.STAB_FALLBACK:
         assert ref["stats"]["n_fallback"] > 0
+
+
+@pytest.mark.parametrize("make,n,ell,m,delta", [
+    (lambda: NS.disk2d(2000, seed=1), 12, 2, 3, 0.5),
+    (lambda: NS.jittered_grid(9, 3, seed=9), 45, 3, 7, 0.3),
+    (lambda: NS.square2d(10000, seed=5), 31, 4, 7, 0.3),
+])
+def test_lu_factorization_option(make, n, ell, m, delta):
+    # the partial-pivot LU (the paper's decomposition) and the default symmetric LDL^T give
+    # the same matrix up to rounding
+    compare(make(), n, ell, m, delta, factor=R.FACTOR_LU)
 
 
 @pytest.mark.parametrize("N,n,ell,m,delta", [
