@@ -340,7 +340,8 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     p->qcap = p->max_ball < 1 ? 1 : p->max_ball;
     {
         int stride = 0;
-        const size_t per_cta = solve_smem_per_cta(n, p->K, p->qcap, d, &stride) +
+        const size_t per_cta = solve_smem_per_cta(n, p->K, p->qcap, d,
+                                                  o.factor == RBFFD_FACTOR_LDLT, &stride) +
                                basis_smem_bytes(M, d);
         const size_t avail = (size_t)max_optin_smem() - 64;
         p->stride = stride;

@@ -29,9 +29,15 @@ namespace rbffd {
 
 constexpr int kNT = 128;  // threads per stencil team: one warp per SM sub-partition
 
-// Per-CTA shared-memory views of one local system.
+// Per-CTA shared-memory views of one local system.  Two layouts:
+//   full   (LU):     A is K x S row-major holding [A_hat | B_hat]; X = A + K, xs = S
+//   packed (LDL^T):  T holds the lower triangle of A_hat by rows (row i starts at i(i+1)/2);
+//                    X is the K x q right-hand-side block with row stride xs (odd)
 struct StencilSmem {
-    double* A;      // K rows x stride: [A P | B ; P^T 0 | B_psi]
+    double* A;
+    double* T;
+    double* X;
+    int xs;
     double* xi;     // n x D scaled stencil coordinates
     double* rdiag;  // K reciprocal pivots (LDL^T: 1x1 reciprocal or 2x2 inverse entry 00)
     double* dinv1;  // K  LDL^T 2x2 inverse entry 01
@@ -47,6 +53,8 @@ struct StencilSmem {
     unsigned char* keep;  // qcap kept-for-coverage flags
 };
 
+__host__ __device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
+
 // Monomial basis tables in shared memory (built on the host in graded order):
 //   psi_l = psi_parent[l] * xi_var[l]            (l >= 1; psi_0 = 1)
 //   Laplacian psi_l = sum_a lap_coef[l][a] * psi_lap_child[l][a]
@@ -57,22 +65,36 @@ struct Basis {
     const short* lap_coef;
 };
 
-size_t solve_smem_per_cta(int n, int K, int qcap, int D, int* stride_out) {
-    int stride = K + qcap;
+// Bytes of one CTA's local system; *stride_out is S (full) or xs (packed).
+size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride_out) {
+    int stride = packed ? qcap : K + qcap;
     if ((stride & 1) == 0) ++stride;  // odd row stride: column walks hit distinct banks
     if (stride_out) *stride_out = stride;
-    size_t b = (size_t)K * stride * 8 + (size_t)n * D * 8 + (size_t)K * 5 * 8 +
-               (size_t)qcap * 8 + (size_t)(qcap + n) * 4 + (size_t)K * 2 * 4 + (size_t)K +
-               (size_t)qcap;
+    const size_t mat = packed ? ((size_t)tri(K) + 1) / 2 * 2 + (size_t)K * stride
+                              : (size_t)K * stride;
+    size_t b = mat * 8 + (size_t)n * D * 8 + (size_t)K * 5 * 8 + (size_t)qcap * 8 +
+               (size_t)(qcap + n) * 4 + (size_t)K * 2 * 4 + (size_t)K + (size_t)qcap;
     return (b + 15) & ~size_t(15);
 }
 
 size_t basis_smem_bytes(int M, int D) { return ((size_t)M * (2 + 2 * D) * sizeof(short) + 15) & ~size_t(15); }
 
-template <int D>
+template <int D, bool PACKED>
 __device__ __forceinline__ void carve(char* p, int n, int K, int qcap, int S, StencilSmem& sm) {
-    sm.A = reinterpret_cast<double*>(p);
-    p += (size_t)K * S * 8;
+    if (PACKED) {
+        sm.A = nullptr;
+        sm.T = reinterpret_cast<double*>(p);
+        p += ((size_t)tri(K) + 1) / 2 * 2 * 8;
+        sm.X = reinterpret_cast<double*>(p);
+        sm.xs = S;
+        p += (size_t)K * S * 8;
+    } else {
+        sm.A = reinterpret_cast<double*>(p);
+        sm.T = nullptr;
+        sm.X = sm.A + K;
+        sm.xs = S;
+        p += (size_t)K * S * 8;
+    }
     sm.xi = reinterpret_cast<double*>(p);
     p += (size_t)n * D * 8;
     sm.rdiag = reinterpret_cast<double*>(p);
@@ -112,13 +134,15 @@ __device__ __forceinline__ Basis load_basis(char* smem, const short* g, int M, i
 }
 
 // Assemble the local system of stencil j (§4.1) and its q right-hand sides (the columns in
-// sm.cols) in shared memory, with the whole CTA.
-template <int D>
+// sm.cols) in shared memory, with the whole CTA.  Full layout: both triangles of A_hat and
+// B_hat beside it.  Packed layout: the lower triangle of A_hat and B_hat apart.
+template <int D, bool PACKED>
 __device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q,
                                const StencilSmem& sm) {
     const int tid = threadIdx.x;
-    const int n = a.n, M = a.M, K = a.K, S = a.stride, m = a.m;
-    const int Wd = K + q;
+    const int n = a.n, M = a.M, K = a.K, m = a.m;
+    double* X = sm.X;
+    const int xs = sm.xs;
     double r2c = a.rho2[j];
     if (!(r2c > 0.0)) r2c = 1.0;
     const double rho = sqrt(r2c);
@@ -128,9 +152,18 @@ __device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q
         for (int c = 0; c < D; ++c)
             sm.xi[t * D + c] = __ddiv_rn(__dsub_rn(a.X[(size_t)id * D + c], xc[c]), rho);
     }
-    for (int e = tid; e < K * Wd; e += kNT) {
-        const int r = e / Wd, c = e - r * Wd;
-        sm.A[r * S + c] = 0.0;
+    if (PACKED) {
+        for (int e = tid; e < tri(K); e += kNT) sm.T[e] = 0.0;
+        for (int e = tid; e < K * q; e += kNT) {
+            const int r = e / q, c = e - r * q;
+            X[r * xs + c] = 0.0;
+        }
+    } else {
+        const int Wd = K + q, S = xs;
+        for (int e = tid; e < K * Wd; e += kNT) {
+            const int r = e / Wd, c = e - r * Wd;
+            sm.A[r * S + c] = 0.0;
+        }
     }
     __syncthreads();
     // A_ab = r^m and, for solved ball members, the phi-part of the right-hand side
@@ -154,11 +187,15 @@ __device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q
                 double pm2 = r;
                 for (int s = 0; s < (m - 3) / 2; ++s) pm2 = __dmul_rn(pm2, r2);
                 const double pm = __dmul_rn(pm2, r2);
-                sm.A[ra * S + rb] = pm;
-                sm.A[rb * S + ra] = pm;
+                if (PACKED) {
+                    sm.T[tri(rb) + ra] = pm;
+                } else {
+                    sm.A[ra * xs + rb] = pm;
+                    sm.A[rb * xs + ra] = pm;
+                }
                 const int ca = sm.colof[ra], cb = sm.colof[rb];
-                if (cb >= 0) sm.A[ra * S + K + cb] = __dmul_rn(a.coef, pm2);
-                if (ca >= 0) sm.A[rb * S + K + ca] = __dmul_rn(a.coef, pm2);
+                if (cb >= 0) X[ra * xs + cb] = __dmul_rn(a.coef, pm2);
+                if (ca >= 0) X[rb * xs + ca] = __dmul_rn(a.coef, pm2);
             }
             pr += di;
             off += dj;
@@ -167,27 +204,36 @@ __device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q
     }
     // P: one stencil point per thread, each monomial = an earlier one times one coordinate
     for (int r = tid; r < n; r += kNT) {
-        double* row = sm.A + r * S + n;
-        row[0] = 1.0;
-        sm.A[n * S + r] = 1.0;
-        for (int l = 1; l < M; ++l) {
-            const double v = row[bs.parent[l]] * sm.xi[r * D + bs.var[l]];
-            row[l] = v;
-            sm.A[(n + l) * S + r] = v;
+        if (PACKED) {
+            sm.T[tri(n) + r] = 1.0;
+            for (int l = 1; l < M; ++l)
+                sm.T[tri(n + l) + r] = sm.T[tri(n + bs.parent[l]) + r] * sm.xi[r * D + bs.var[l]];
+        } else {
+            double* row = sm.A + r * xs + n;
+            row[0] = 1.0;
+            sm.A[n * xs + r] = 1.0;
+            for (int l = 1; l < M; ++l) {
+                const double v = row[bs.parent[l]] * sm.xi[r * D + bs.var[l]];
+                row[l] = v;
+                sm.A[(n + l) * xs + r] = v;
+            }
         }
     }
     __syncthreads();
     // psi-part of the right-hand sides: Laplacian of each monomial at each solved member,
-    // from the monomial values already in that member's row of P
+    // from the monomial values already computed for that member
     for (int e = tid; e < M * q; e += kNT) {
         const int l = e / q, c = e - l * q;
-        const double* prow = sm.A + sm.cols[c] * S + n;
+        const int t = sm.cols[c];
         double s = 0.0;
         for (int d = 0; d < D; ++d) {
             const int ch = bs.lap_child[l * D + d];
-            if (ch >= 0) s = fma((double)bs.lap_coef[l * D + d], prow[ch], s);
+            if (ch >= 0) {
+                const double pv = PACKED ? sm.T[tri(n + ch) + t] : sm.A[t * xs + n + ch];
+                s = fma((double)bs.lap_coef[l * D + d], pv, s);
+            }
         }
-        sm.A[(n + l) * S + K + c] = s;
+        X[(n + l) * xs + c] = s;
     }
     __syncthreads();
 }
@@ -202,25 +248,27 @@ __device__ __forceinline__ float approx_f32(unsigned long long b) {
     return __int_as_float((int)(((unsigned)(ef + 127) << 23) | mant));
 }
 
-// LU with partial pivoting of [A_hat | B_hat] (the paper's decomposition, §4.3 cost model
-// (2/3) K^3 + 2 K^2 q), then back substitution.  Returns false (uniformly) on an exactly zero
-// pivot; on success row r of the right-hand-side block holds unknown r.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// LU with partial pivoting of [A_hat | B_hat] in the full layout (the paper's decomposition,
+// §4.3 cost model (2/3) K^3 + 2 K^2 q), then back substitution.  Returns false (uniformly)
+// on an exactly zero pivot; on success row r of the right-hand-side block holds unknown r.
 __device__ bool factor_solve_lu(const SolveArgs& a, int q, const StencilSmem& sm) {
     __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int K = a.K, S = a.stride;
+    const int K = a.K, S = sm.xs;
     const int Wd = K + q;
     for (int r = tid; r < K; r += kNT) sm.rowof[r] = r;
-    // Gaussian elimination with partial pivoting on [A_hat | B_hat]; the pivot search, row
-    // swap, reciprocal and multipliers are done by warp 0 alone (FP64 work counts per warp
-    // instruction, so the other warps must not repeat it)
+    // the pivot search, row swap, reciprocal and multipliers are done by warp 0 alone (FP64
+    // work counts per warp instruction, so the other warps must not repeat it)
     for (int p = 0; p < K; ++p) {
         if (wid == 0) {
             unsigned long long bv = 0ull;
             int bi = 0x7fffffff;
             for (int i = p + lane; i < K; i += 32) {
-                const unsigned long long v =
-                    (unsigned long long)__double_as_longlong(sm.A[i * S + p]) & 0x7fffffffffffffffull;
+                const unsigned long long v = abs_bits(sm.A[i * S + p]);
                 if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
             }
             for (int o = 16; o > 0; o >>= 1) {
@@ -287,20 +335,19 @@ __device__ bool factor_solve_lu(const SolveArgs& a, int q, const StencilSmem& sm
     return true;
 }
 
-
 // Symmetric indefinite LDL^T factorization with Bunch-Kaufman partial pivoting (J. R. Bunch
 // and L. Kaufman, "Some stable methods for calculating inertia and solving symmetric linear
-// systems", Math. Comp. 31 (1977)) of the symmetric saddle-point matrix [A P; P^T 0], with
-// the right-hand sides carried along; (1/3) K^3 + 2 K^2 q flops.  Only the lower triangle is
-// referenced.  1x1 and 2x2 pivots; symmetric row/column swaps are tracked in sm.perm.
-// Pivot tests use alpha = (1 + sqrt(17)) / 8.  Returns false (uniformly) on an exactly
-// singular pivot column.  On success sm.rowof[u] is
+// systems", Math. Comp. 31 (1977)) of the symmetric saddle-point matrix [A P; P^T 0] in the
+// packed layout, with the right-hand sides carried along; (1/3) K^3 + 2 K^2 q flops.  1x1
+// and 2x2 pivots with alpha = (1 + sqrt(17)) / 8; symmetric swaps are tracked in sm.perm.
+// Returns false (uniformly) on an exactly singular pivot column.  On success sm.rowof[u] is
 // the row of the right-hand-side block that holds unknown u.
 __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& sm) {
     __shared__ int s_ok, s_kind;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int K = a.K, S = a.stride;
-    double* A = sm.A;
+    const int K = a.K, xs = sm.xs;
+    double* T = sm.T;
+    double* X = sm.X;
     for (int r = tid; r < K; r += kNT) sm.perm[r] = r;
     __syncthreads();
     int p = 0;
@@ -310,8 +357,7 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
             unsigned long long lv = 0ull;
             int r = 0x7fffffff;
             for (int i = p + 1 + lane; i < K; i += 32) {
-                const unsigned long long v =
-                    (unsigned long long)__double_as_longlong(A[i * S + p]) & 0x7fffffffffffffffull;
+                const unsigned long long v = abs_bits(T[tri(i) + p]);
                 if (v > lv || (v == lv && i < r)) { lv = v; r = i; }
             }
             for (int o = 16; o > 0; o >>= 1) {
@@ -321,8 +367,7 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
             }
             // the pivot choice only has to be a valid Bunch-Kaufman choice, so the tests run in
             // FP32 on values rebuilt from the FP64 bit patterns (no FP64 instructions)
-            const unsigned long long pv =
-                (unsigned long long)__double_as_longlong(A[p * S + p]) & 0x7fffffffffffffffull;
+            const unsigned long long pv = abs_bits(T[tri(p) + p]);
             const float lam = approx_f32(lv), app = approx_f32(pv);
             const float af = 0.6403882f;
             int kind = 1, swap_a = p, swap_b = p;
@@ -334,18 +379,14 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
                 unsigned long long sv = 0ull;
                 for (int jj = p + lane; jj < K; jj += 32) {
                     if (jj == r) continue;
-                    const double v = jj < r ? A[r * S + jj] : A[jj * S + r];
-                    const unsigned long long b =
-                        (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+                    const unsigned long long b = abs_bits(jj < r ? T[tri(r) + jj] : T[tri(jj) + r]);
                     sv = b > sv ? b : sv;
                 }
                 for (int o = 16; o > 0; o >>= 1) {
                     const unsigned long long ov = __shfl_xor_sync(0xffffffffu, sv, o);
                     sv = ov > sv ? ov : sv;
                 }
-                const float sig = approx_f32(sv);
-                const float arr = approx_f32(
-                    (unsigned long long)__double_as_longlong(A[r * S + r]) & 0x7fffffffffffffffull);
+                const float sig = approx_f32(sv), arr = approx_f32(abs_bits(T[tri(r) + r]));
                 if (app * sig >= af * lam * lam) {
                     kind = 1;
                 } else if (arr >= af * sig) {
@@ -355,17 +396,17 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
                 }
             }
             if (ok && swap_a != swap_b) {
-                // symmetric swap of unknowns swap_a < swap_b in lower-triangle storage
+                // symmetric swap of unknowns ua < ub in the packed lower triangle
                 const int ua = swap_a, ub = swap_b;
                 const int n1 = ua, n2 = ub - ua - 1, n3 = K - ub - 1, nq = q;
                 const int tot = n1 + n2 + n3 + nq + 1;
                 for (int e = lane; e < tot; e += 32) {
                     double *x, *y;
-                    if (e < n1) { x = A + ua * S + e; y = A + ub * S + e; }
-                    else if (e < n1 + n2) { const int i = ua + 1 + (e - n1); x = A + i * S + ua; y = A + ub * S + i; }
-                    else if (e < n1 + n2 + n3) { const int i = ub + 1 + (e - n1 - n2); x = A + i * S + ua; y = A + i * S + ub; }
-                    else if (e < n1 + n2 + n3 + nq) { const int c = K + (e - n1 - n2 - n3); x = A + ua * S + c; y = A + ub * S + c; }
-                    else { x = A + ua * S + ua; y = A + ub * S + ub; }
+                    if (e < n1) { x = T + tri(ua) + e; y = T + tri(ub) + e; }
+                    else if (e < n1 + n2) { const int i = ua + 1 + (e - n1); x = T + tri(i) + ua; y = T + tri(ub) + i; }
+                    else if (e < n1 + n2 + n3) { const int i = ub + 1 + (e - n1 - n2); x = T + tri(i) + ua; y = T + tri(i) + ub; }
+                    else if (e < n1 + n2 + n3 + nq) { const int c = e - n1 - n2 - n3; x = X + ua * xs + c; y = X + ub * xs + c; }
+                    else { x = T + tri(ua) + ua; y = T + tri(ub) + ub; }
                     const double t = *x; *x = *y; *y = t;
                 }
                 if (lane == 0) { const int t = sm.perm[ua]; sm.perm[ua] = sm.perm[ub]; sm.perm[ub] = t; }
@@ -373,28 +414,28 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
             }
             if (ok) {
                 if (kind == 1) {
-                    const double rcp = 1.0 / A[p * S + p];
+                    const double rcp = 1.0 / T[tri(p) + p];
                     if (lane == 0) { sm.rdiag[p] = rcp; sm.pk[p] = 1; }
                     for (int i = p + 1 + lane; i < K; i += 32) {
-                        const double w = A[i * S + p];
+                        const double w = T[tri(i) + p];
                         sm.wv[i] = w;
-                        A[i * S + p] = w * rcp;
+                        T[tri(i) + p] = w * rcp;
                     }
                 } else {
-                    const double d0 = A[p * S + p], d1 = A[(p + 1) * S + p], d2 = A[(p + 1) * S + p + 1];
+                    const double d0 = T[tri(p) + p], d1 = T[tri(p + 1) + p], d2 = T[tri(p + 1) + p + 1];
                     const double rdet = 1.0 / fma(d0, d2, -d1 * d1);
                     const double i00 = d2 * rdet, i01 = -d1 * rdet, i11 = d0 * rdet;
                     if (lane == 0) {
                         sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.dinv2[p] = i11;
                         sm.pk[p] = 2; sm.pk[p + 1] = 0;
-                        A[(p + 1) * S + p] = 0.0;  // L has no entry inside a 2x2 pivot block
+                        T[tri(p + 1) + p] = 0.0;  // L has no entry inside a 2x2 pivot block
                     }
                     for (int i = p + 2 + lane; i < K; i += 32) {
-                        const double w1 = A[i * S + p], w2 = A[i * S + p + 1];
+                        const double w1 = T[tri(i) + p], w2 = T[tri(i) + p + 1];
                         sm.wv[i] = w1;
                         sm.wv2[i] = w2;
-                        A[i * S + p] = fma(w1, i00, w2 * i01);
-                        A[i * S + p + 1] = fma(w1, i01, w2 * i11);
+                        T[tri(i) + p] = fma(w1, i00, w2 * i01);
+                        T[tri(i) + p + 1] = fma(w1, i01, w2 * i11);
                     }
                 }
             }
@@ -403,16 +444,15 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
         __syncthreads();
         if (!s_ok) return false;
         const int kind = s_kind;
-        // trailing update of the lower triangle and of the right-hand sides: row i (> p0)
-        // has (i - p0) triangle entries followed by q right-hand-side entries
+        // Trailing update of the lower triangle and of the right-hand sides: row i (> p0)
+        // has (i - p0) triangle entries followed by q right-hand-side entries.  Rows r and
+        // rows-1-r are paired into one virtual row of constant length rows + 1 + 2q, so the
+        // flattened index steps in O(1).  The FP64 work is branch-free: source operands are
+        // selected with integer arithmetic so every lane issues the same FMA (a divergent
+        // FP64 instruction costs the whole warp on the FP64 pipe).
         const int p0 = p + kind - 1;
         const int rows = K - p0 - 1;
         if (rows > 0) {
-            // Rows r and rows-1-r are paired into one virtual row of constant length
-            // rows + 1 + 2q, so the flattened index steps in O(1) like a rectangle.  The FP64
-            // work is branch-free: source operands are selected with integer arithmetic so
-            // every lane issues the same FMA (a divergent FP64 instruction costs the whole
-            // warp on the FP64 pipe).
             const int L2 = rows + 1 + 2 * q;
             const int total = ((rows + 1) >> 1) * L2;
             if (tid < total) {
@@ -424,15 +464,18 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
                     const int r = first ? pr : rows - 1 - pr;
                     const int t = first ? off : off - len0;
                     if (first || r != pr) {  // an odd middle row pairs with itself: once only
-                        double* Ai = A + (p0 + 1 + r) * S;
-                        const bool tri = t <= r;
-                        const int col = tri ? p0 + 1 + t : K + t - (r + 1);
-                        const double* s1 = tri ? sm.wv + col : A + p * S + col;
+                        const int i = p0 + 1 + r;
+                        double* Ti = T + tri(i);
+                        const bool trin = t <= r;
+                        const int jj = p0 + 1 + t;      // triangle column
+                        const int c = t - (r + 1);      // right-hand-side column
+                        double* dst = trin ? Ti + jj : X + i * xs + c;
+                        const double* s1 = trin ? sm.wv + jj : X + p * xs + c;
                         if (kind == 1) {
-                            Ai[col] = fma(-Ai[p], *s1, Ai[col]);
+                            *dst = fma(-Ti[p], *s1, *dst);
                         } else {
-                            const double* s2 = tri ? sm.wv2 + col : A + (p + 1) * S + col;
-                            Ai[col] = fma(-Ai[p + 1], *s2, fma(-Ai[p], *s1, Ai[col]));
+                            const double* s2 = trin ? sm.wv2 + jj : X + (p + 1) * xs + c;
+                            *dst = fma(-Ti[p + 1], *s2, fma(-Ti[p], *s1, *dst));
                         }
                     }
                     pr += di;
@@ -448,11 +491,11 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
     for (int e = tid; e < K * q; e += kNT) {
         const int i = e / q, c = e - (e / q) * q;
         const int k = sm.pk[i];
-        double* Bi = A + i * S + K + c;
+        double* Bi = X + i * xs + c;
         if (k == 1) {
             *Bi *= sm.rdiag[i];
         } else if (k == 2) {
-            double* Bn = Bi + S;
+            double* Bn = Bi + xs;
             const double y0 = *Bi, y1 = *Bn;
             *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
             *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
@@ -465,11 +508,11 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
         if (tid < total) {
             int jj = tid / q, cc = tid - (tid / q) * q;
             const int dj = kNT / q, dc = kNT - dj * q;
-            const double* Li = A + i * S;
-            const double* xi = Li + K;
+            const double* Li = T + tri(i);
+            const double* xi = X + i * xs;
 #pragma unroll 4
             for (int e = tid; e < total; e += kNT) {
-                double* xj = A + jj * S + K;
+                double* xj = X + jj * xs;
                 xj[cc] = fma(-Li[jj], xi[cc], xj[cc]);
                 jj += dj;
                 cc += dc;
@@ -483,11 +526,11 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
     return true;
 }
 
-template <int D>
+template <int D, bool PACKED>
 __device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
                             const StencilSmem& sm) {
-    assemble_local<D>(a, bs, j, q, sm);
-    return a.factor == RBFFD_FACTOR_LU ? factor_solve_lu(a, q, sm) : factor_solve_ldlt(a, q, sm);
+    assemble_local<D, PACKED>(a, bs, j, q, sm);
+    return PACKED ? factor_solve_ldlt(a, q, sm) : factor_solve_lu(a, q, sm);
 }
 
 // Local L-Lebesgue value sum_r |w_r| of every solved column (one warp per column).
@@ -495,7 +538,7 @@ __device__ __forceinline__ void lebesgue_values(const SolveArgs& a, int q, const
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = wid; c < q; c += kNT / 32) {
         double s = 0.0;
-        for (int r = lane; r < a.n; r += 32) s += fabs(sm.A[sm.rowof[r] * a.stride + a.K + c]);
+        for (int r = lane; r < a.n; r += 32) s += fabs(sm.X[sm.rowof[r] * sm.xs + c]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) sm.lam[c] = s;
     }
@@ -555,13 +598,13 @@ __global__ void k_traversal_seed(SolveArgs a, const int* __restrict__ indeg) {
 // One CTA per center.  Thread 0 claims the next queue slot and waits (bounded) for it to be
 // filled; the CTA then solves the center, tests and writes its columns, and resolves the
 // traversal state of its ball members.
-template <int D>
+template <int D, bool PACKED>
 __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_j, s_q;
     const Basis bs = load_basis(smem, a.basis, a.M, D);
     StencilSmem sm;
-    carve<D>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
+    carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int n = a.n, N = a.N;
@@ -622,7 +665,7 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
         }
         __syncthreads();
         const int q = s_q;
-        const bool ok = solve_local<D>(a, bs, j, q, sm);
+        const bool ok = solve_local<D, PACKED>(a, bs, j, q, sm);
         if (ok) lebesgue_values(a, q, sm);
         __syncthreads();
         // Lebesgue test (§4.2.1) per column; q <= n <= kNT, so one thread per column
@@ -649,7 +692,7 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
             const int c = e / n, r = e - c * n;
             if (!sm.keep[c]) continue;
             a.slot_w[(base + sm.cols[c]) * n + r] =
-                ok ? sm.A[sm.rowof[r] * a.stride + a.K + c] * inv_r2 : nan;
+                ok ? sm.X[sm.rowof[r] * sm.xs + c] * inv_r2 : nan;
         }
         // ownership: the earliest center keeping a row owns it
         if (tid > 0 && tid < q && sm.keep[tid]) {
@@ -700,12 +743,12 @@ __global__ void k_fallback_collect(SolveArgs a) {
     }
 }
 
-template <int D>
+template <int D, bool PACKED>
 __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
     const Basis bs = load_basis(smem, a.basis, a.M, D);
     StencilSmem sm;
-    carve<D>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
+    carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
     __syncthreads();
     const int tid = threadIdx.x;
     const int count = *((volatile int*)&a.ctr->fb_count);
@@ -715,7 +758,7 @@ __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_
         for (int t = tid; t < a.n; t += kNT) sm.colof[t] = (t == 0) ? 0 : -1;
         if (tid == 0) sm.cols[0] = 0;
         __syncthreads();
-        const bool ok = solve_local<D>(a, bs, i, 1, sm);
+        const bool ok = solve_local<D, PACKED>(a, bs, i, 1, sm);
         if (ok) lebesgue_values(a, 1, sm);
         __syncthreads();
         double r2c = a.rho2[i];
@@ -723,7 +766,7 @@ __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_
         const double inv_r2 = 1.0 / r2c;
         const long long slot = a.slot_off[i];
         for (int r = tid; r < a.n; r += kNT)
-            a.slot_w[slot * a.n + r] = ok ? sm.A[sm.rowof[r] * a.stride + a.K] * inv_r2 : nan;
+            a.slot_w[slot * a.n + r] = ok ? sm.X[sm.rowof[r] * sm.xs] * inv_r2 : nan;
         if (tid == 0) {
             a.slot_lam[slot] = ok ? sm.lam[0] : nan;
             if (!ok) {
@@ -815,18 +858,18 @@ static int sm_count() {
     return v > 0 ? v : 1;
 }
 
-template <int D>
+template <int D, bool PACKED>
 static int traversal(const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
                      cudaEvent_t ev0, cudaEvent_t ev1) {
     int stride = 0;
-    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, &stride);
+    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, PACKED, &stride);
     const int basis_bytes = (int)basis_smem_bytes(a.M, D);
     const size_t smem = basis_bytes + per_cta;
-    if (RB_CUDA(cudaFuncSetAttribute(k_traversal<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem)))
+    auto kern = k_traversal<D, PACKED>;
+    if (RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return RBFFD_EINVAL;
     int per_sm = 0;
-    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traversal<D>, kNT, smem)) ||
+    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, smem)) ||
         per_sm < 1)
         return RBFFD_EINVAL;
     const int tb = 256, nb = (a.N + tb - 1) / tb;
@@ -834,14 +877,15 @@ static int traversal(const SolveArgs& a, const int* indeg, cudaStream_t s, int* 
                                        a.fb_flag);
     k_traversal_seed<<<nb, tb, 0, s>>>(a, indeg);
     *launches += 2;
-    const int grid = min(per_sm * sm_count(), a.N);
+    int grid = min(per_sm * sm_count(), a.N);
+    if (a.max_ctas > 0) grid = min(grid, a.max_ctas);
     SolveArgs aa = a;
     size_t pc = per_cta;
     int bb = basis_bytes;
     void* args[] = {&aa, &pc, &bb};
     if (ev0) cudaEventRecord(ev0, s);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_traversal<D>, dim3(grid),
-                                                dim3(kNT), args, smem, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kNT), args,
+                                                smem, s);
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
     return RB_CUDA(e);
@@ -849,30 +893,36 @@ static int traversal(const SolveArgs& a, const int* indeg, cudaStream_t s, int* 
 
 int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
                      cudaEvent_t ev0, cudaEvent_t ev1) {
-    return D == 2 ? traversal<2>(a, indeg, s, launches, ev0, ev1)
-                  : traversal<3>(a, indeg, s, launches, ev0, ev1);
+    const bool packed = a.factor == RBFFD_FACTOR_LDLT;
+    if (D == 2)
+        return packed ? traversal<2, true>(a, indeg, s, launches, ev0, ev1)
+                      : traversal<2, false>(a, indeg, s, launches, ev0, ev1);
+    return packed ? traversal<3, true>(a, indeg, s, launches, ev0, ev1)
+                  : traversal<3, false>(a, indeg, s, launches, ev0, ev1);
 }
 
-template <int D>
+template <int D, bool PACKED>
 static int fallback(const SolveArgs& a, cudaStream_t s, int* launches) {
     const int tb = 256, nb = (a.N + tb - 1) / tb;
     k_fallback_collect<<<nb, tb, 0, s>>>(a);
     int stride = 0;
-    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, &stride);
+    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, PACKED, &stride);
     const int basis_bytes = (int)basis_smem_bytes(a.M, D);
     const size_t smem = basis_bytes + per_cta;
-    if (RB_CUDA(cudaFuncSetAttribute(k_fallback_solve<D>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    auto kern = k_fallback_solve<D, PACKED>;
+    if (RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
         return RBFFD_EINVAL;
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fallback_solve<D>, kNT, smem);
-    k_fallback_solve<D><<<max(per_sm, 1) * sm_count(), kNT, smem, s>>>(a, per_cta, basis_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, smem);
+    kern<<<max(per_sm, 1) * sm_count(), kNT, smem, s>>>(a, per_cta, basis_bytes);
     *launches += 2;
     return RB_LAUNCHED(__func__);
 }
 
 int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches) {
-    return D == 2 ? fallback<2>(a, s, launches) : fallback<3>(a, s, launches);
+    const bool packed = a.factor == RBFFD_FACTOR_LDLT;
+    if (D == 2) return packed ? fallback<2, true>(a, s, launches) : fallback<2, false>(a, s, launches);
+    return packed ? fallback<3, true>(a, s, launches) : fallback<3, false>(a, s, launches);
 }
 
 int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* val,

@@ -111,11 +111,12 @@ struct SolveArgs {
     const short* basis;        // monomial recurrence and Laplacian tables (see assemble.cu)
     int N, n, M, K, m, ell;
     int qcap;                  // columns room per stencil
-    int stride;                // row stride of the local system in shared memory (odd)
+    int stride;                // row stride of the full matrix (LU) or of the RHS block (LDL^T)
     int mode;                  // RBFFD_STAB_*
     double coef;               // m (m + D - 2)
     int no_seed;               // fault injection: push no initial center (waits run out)
-    int factor;                // RBFFD_FACTOR_LDLT or RBFFD_FACTOR_LU
+    int factor;                // RBFFD_FACTOR_LDLT (packed layout) or RBFFD_FACTOR_LU (full)
+    int max_ctas;              // cap on the persistent grid (0 = fill the GPU)
     unsigned long long timeout_ns;
     // traversal state
     int* state;
@@ -131,7 +132,7 @@ struct SolveArgs {
     DevCounters* ctr;
 };
 
-size_t solve_smem_per_cta(int n, int K, int qcap, int D, int* stride_out);
+size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride_out);
 size_t basis_smem_bytes(int M, int D);
 int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
                      cudaEvent_t ev0, cudaEvent_t ev1);
