@@ -238,6 +238,41 @@ __device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q
     __syncthreads();
 }
 
+// Reciprocal of an FP64 value computed on the integer pipe (GB300's FP64 pipe is ~1/64 of its
+// FP32 rate, and a scalar division issued by one warp occupies it as a full warp
+// instruction): a 24-bit FP32 seed refined by two Newton-Raphson steps t' = t + t (1 - m t)
+// on the mantissa m in 64-bit fixed point, then rounded to 53 bits.  Within 1 ulp of 1/x
+// for normal x; zero, subnormal and near-overflow inputs use the FP64 division.
+__device__ __forceinline__ double rcp_fixed(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sign = b >> 63;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long f = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0 || e >= 0x7fd) return 1.0 / x;
+    if (f == 0)  // a power of two: exact
+        return __longlong_as_double((long long)((sign << 63) | ((unsigned long long)(2046 - e) << 52)));
+    const unsigned long long M = f | (1ull << 52);  // m = M / 2^52 in [1, 2)
+    const float rf = __frcp_rn(__int_as_float(0x3F800000 | (int)(f >> 29)));
+    const unsigned rb = __float_as_uint(rf);
+    unsigned long long Y =  // Y = t * 2^64, t = 1/m in (1/2, 1]
+        rb >= 0x3F800000u ? ~0ull : (unsigned long long)((rb & 0x7FFFFFu) | 0x800000u) << 40;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const unsigned long long lo = M * Y, hi = __umul64hi(M, Y);   // P = M Y
+        const unsigned long long H = (1ull << 52) - hi - (lo != 0ull);  // 2^116 - P, high part
+        const unsigned long long L = 0ull - lo;
+        const long long Dv = (long long)((H << 12) | (L >> 52));  // 2^64 (1 - m t)
+        const unsigned long long C = Dv >= 0 ? __umul64hi(Y, (unsigned long long)Dv)
+                                              : 0ull - __umul64hi(Y, (unsigned long long)(-Dv));
+        Y += C;
+    }
+    unsigned long long m53 = (Y + (1ull << 10)) >> 11;
+    int ex = 1022 - (e - 1023);
+    if (m53 >> 53) { m53 >>= 1; ++ex; }
+    return __longlong_as_double(
+        (long long)((sign << 63) | ((unsigned long long)ex << 52) | (m53 & 0xFFFFFFFFFFFFFull)));
+}
+
 // A float close to the non-negative double with IEEE bits `b` (top 23 mantissa bits,
 // exponent clamped to the float range), built with integer operations only.
 __device__ __forceinline__ float approx_f32(unsigned long long b) {
@@ -287,7 +322,7 @@ __device__ bool factor_solve_lu(const SolveArgs& a, int q, const StencilSmem& sm
                     }
                     __syncwarp();
                 }
-                const double rcp = 1.0 / sm.A[p * S + p];
+                const double rcp = rcp_fixed(sm.A[p * S + p]);
                 if (lane == 0) { sm.rdiag[p] = rcp; s_ok = 1; }
                 for (int i = p + 1 + lane; i < K; i += 32) sm.A[i * S + p] *= rcp;
             }
@@ -414,7 +449,7 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
             }
             if (ok) {
                 if (kind == 1) {
-                    const double rcp = 1.0 / T[tri(p) + p];
+                    const double rcp = rcp_fixed(T[tri(p) + p]);
                     if (lane == 0) { sm.rdiag[p] = rcp; sm.pk[p] = 1; }
                     for (int i = p + 1 + lane; i < K; i += 32) {
                         const double w = T[tri(i) + p];
@@ -423,7 +458,7 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
                     }
                 } else {
                     const double d0 = T[tri(p) + p], d1 = T[tri(p + 1) + p], d2 = T[tri(p + 1) + p + 1];
-                    const double rdet = 1.0 / fma(d0, d2, -d1 * d1);
+                    const double rdet = rcp_fixed(fma(d0, d2, -d1 * d1));
                     const double i00 = d2 * rdet, i01 = -d1 * rdet, i11 = d0 * rdet;
                     if (lane == 0) {
                         sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.dinv2[p] = i11;
