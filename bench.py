@@ -291,6 +291,40 @@ def run_gpu(args):
     return 0
 
 
+def run_serve(args):
+    """The serving workload: a seeded mix of jobs (2D/3D, N log-uniform, ell 2..5, random
+    delta) replayed with Poisson arrivals at two offered loads of the measured single-stream
+    throughput; prints one JSON line with p50/p99 latency and rows/s per load."""
+    import torch
+    from paper_1606_03135_gb300 import serve as S
+    from paper_1606_03135_gb300 import rbffd as R
+    R.load()
+    torch.cuda.set_device(0)
+    count = args.jobs
+    jobs = S.serving_jobs(count=count)
+    warm = S.serving_jobs(count=4, seed=77, n_min=1000, n_max=5000)
+    S.Server(slots=1, keep_results=False).run(warm)
+    for j in jobs:
+        j.arrival = 0.0
+    _, single = S.Server(slots=1, keep_results=False).run(jobs)
+    rate1 = count / single["makespan_s"]
+    out = {"metric": "serving rows/s and p50/p99 latency (FP64)", "unit": "rows/s",
+           "value": None, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"serve{count}: d in {{2,3}}, N log-uniform [1k,200k], "
+                                  "ell 2..5, n=2M+1, delta U[0.2,1], Poisson arrivals",
+                      "slots": args.slots, "hbm_budget_gb": 40},
+           "single_stream": {"rows_per_s": single["rows_per_s"],
+                             "makespan_s": single["makespan_s"]},
+           "loads": {}}
+    for load in (0.5, 0.9):
+        S.poisson_arrivals(jobs, rate=load * rate1)
+        _, summ = S.Server(slots=args.slots, keep_results=False).run(jobs)
+        out["loads"][str(load)] = summ
+    out["value"] = out["loads"]["0.9"]["rows_per_s"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,10 +333,15 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=None,
-                    help="another named node-set workload (default: the 2D delta sweep)")
+                    help="another named node-set workload (default: the 2D delta sweep), "
+                         "or 'serve' for the serving trace")
+    ap.add_argument("--jobs", type=int, default=256, help="serving trace length")
+    ap.add_argument("--slots", type=int, default=4, help="serving slots (streams)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

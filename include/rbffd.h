@@ -60,6 +60,8 @@ typedef struct {
     int fault_inject;   /* tests only: 1 = seed no work, so every traversal wait runs out and
                            rbffd_assemble returns RBFFD_ETIMEOUT after timeout_ms; 0 = off */
     int factor;         /* RBFFD_FACTOR_LDLT (default) or RBFFD_FACTOR_LU */
+    int max_ctas;       /* cap on the persistent traversal grid, so that plans assembled
+                           concurrently on several streams share the GPU; 0 = fill the GPU */
 } rbffd_opts;
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */
@@ -93,6 +95,8 @@ typedef struct {
     float ms_traversal;     /* device time of the traversal + local-solve kernel */
     float ms_fallback;      /* device time of the FALLBACK re-solves (0 otherwise) */
     float ms_finalize;      /* device time of the CSR scatter */
+    int64_t plan_bytes;     /* device memory the plan holds after rbffd_plan */
+    int64_t assemble_bytes; /* device memory rbffd_assemble adds (exact, known after plan) */
 } rbffd_stats_t;
 
 /* rbffd_plan -- build the stencils of §4.1 for one node set.

@@ -32,6 +32,7 @@ struct rbffd_plan_s {
     DevCounters* ctr = nullptr;
     DevCounters h_ctr{};           // host copy of the device counters
     void* plan_block = nullptr;    // one allocation for the stencil arrays
+    size_t plan_bytes = 0, asm_bytes = 0;
     void* asm_block = nullptr;     // one allocation for the traversal and CSR arrays
     int max_ball = 0;
     long long total_slots = 0;
@@ -266,10 +267,10 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
         return RBFFD_EINVAL;
     const int M = (int)binom(ell + d, d);
     if (M > n) return RBFFD_EINVAL;
-    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT};
+    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0};
     if (opts) o = *opts;
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
-        (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU))
+        (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0)
         return RBFFD_EINVAL;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
 
@@ -296,6 +297,7 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
                      oI = c.add<int>((size_t)N), oS = c.add<long long>((size_t)N + 1),
                      oP = c.add<short>(basis_count), oC = c.add<DevCounters>(1);
         if ((rc = pool_alloc(&p->plan_block, c.bytes, p->device, s))) goto fail;
+        p->plan_bytes = c.bytes;
         p->X = at<double>(p->plan_block, oX);
         p->nbr = at<int>(p->plan_block, oN);
         p->rho2 = at<double>(p->plan_block, oR);
@@ -337,6 +339,16 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     }
     if (p->h_ctr.status) { rc = p->h_ctr.status; goto fail; }
     p->max_ball = p->h_ctr.max_ball;
+    {
+        // device bytes the traversal and CSR arrays will take (same layout as rbffd_assemble)
+        const size_t S = (size_t)p->total_slots, Nz = (size_t)N, nz = (size_t)n;
+        Carver c;
+        c.add<int>(Nz); c.add<int>(Nz); c.add<int>(Nz); c.add<int>(Nz);
+        c.add<unsigned char>(Nz); c.add<int>(Nz); c.add<double>(S * nz); c.add<double>(S);
+        c.add<unsigned char>(S); c.add<long long>(Nz + 1); c.add<int>(Nz * nz);
+        c.add<double>(Nz * nz); c.add<double>(Nz); c.add<unsigned char>(Nz);
+        p->asm_bytes = c.bytes;
+    }
     p->qcap = p->max_ball < 1 ? 1 : p->max_ball;
     {
         int stride = 0;
@@ -362,8 +374,8 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     const size_t N = (size_t)p->N, n = (size_t)p->n;
     int rc = RBFFD_OK;
     if (!p->have_asm) {
-        const size_t S = (size_t)p->total_slots;
         Carver c;
+        const size_t S = (size_t)p->total_slots;
         const size_t o_state = c.add<int>(N), o_pend = c.add<int>(N), o_own = c.add<int>(N),
                      o_q = c.add<int>(N), o_fbf = c.add<unsigned char>(N),
                      o_fbl = c.add<int>(N), o_sw = c.add<double>(S * n),
@@ -394,6 +406,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.slot_w = p->slot_w; a.slot_lam = p->slot_lam; a.slot_pass = p->slot_pass; a.ctr = p->ctr;
     a.no_seed = p->opts.fault_inject == 1;
     a.factor = p->opts.factor;
+    a.max_ctas = p->opts.max_ctas;
     if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
     rc = launch_traversal(p->d, a, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
     if (rc) return rc;
@@ -440,6 +453,8 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
     out->max_ball = p->max_ball;
     out->n = p->n; out->M = p->M; out->K = p->K; out->d = p->d;
     out->n_launches = p->launches;
+    out->plan_bytes = (int64_t)p->plan_bytes;
+    out->assemble_bytes = (int64_t)p->asm_bytes;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]) == cudaSuccess) out->ms_stencils = ms;
     if (p->assembled) {

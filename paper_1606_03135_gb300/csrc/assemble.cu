@@ -7,7 +7,7 @@
 // earliest center keeping it.  Whether center j keeps node i depends only on stencil j and
 // x_i, so node k's fate is final as soon as every earlier node whose ball contains k (its
 // in-neighbours, counted in `indeg`) is final.  A persistent kernel runs this: a node whose
-// in-neighbours are all final and none kept it is pushed to a work queue as a center; a warp
+// in-neighbours are all final and none kept it is pushed to a work queue as a center; a CTA
 // pops it, factors its local system once, solves the right-hand sides of its still-open
 // ball members, and then (i) marks the members it keeps as covered and (ii) releases one
 // dependency of each later ball member.  Every device-side wait is bounded by a timeout and
@@ -914,16 +914,15 @@ static int traversal(const SolveArgs& a, const int* indeg, cudaStream_t s, int* 
     *launches += 2;
     int grid = min(per_sm * sm_count(), a.N);
     if (a.max_ctas > 0) grid = min(grid, a.max_ctas);
-    SolveArgs aa = a;
-    size_t pc = per_cta;
-    int bb = basis_bytes;
-    void* args[] = {&aa, &pc, &bb};
+    // A plain launch suffices: a worker only waits for queue entries that workers already
+    // running will push (the smallest unresolved node is always ready once every center
+    // that holds a claimed entry is solved), so progress needs no co-residency, and plans
+    // on other streams can run beside this grid.
     if (ev0) cudaEventRecord(ev0, s);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kNT), args,
-                                                smem, s);
+    kern<<<grid, kNT, smem, s>>>(a, per_cta, basis_bytes);
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
-    return RB_CUDA(e);
+    return RB_LAUNCHED(__func__);
 }
 
 int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,

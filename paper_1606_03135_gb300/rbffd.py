@@ -22,7 +22,8 @@ FACTOR_LDLT, FACTOR_LU = 0, 1
 
 class rbffd_opts(C.Structure):
     _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
-                ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int)]
+                ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int),
+                ("max_ctas", C.c_int)]
 
 
 class rbffd_csr(C.Structure):
@@ -37,7 +38,8 @@ class rbffd_stats_t(C.Structure):
                 ("M", C.c_int32), ("K", C.c_int32), ("d", C.c_int32), ("alg_flops", C.c_double),
                 ("n_launches", C.c_int64), ("ms_stencils", C.c_float),
                 ("ms_traversal", C.c_float), ("ms_fallback", C.c_float),
-                ("ms_finalize", C.c_float)]
+                ("ms_finalize", C.c_float), ("plan_bytes", C.c_int64),
+                ("assemble_bytes", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -164,7 +166,7 @@ class Plan:
     the library inside ``rbffd_plan``)."""
 
     def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
-                 stream=None, fault_inject=0, factor=FACTOR_LDLT):
+                 stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0):
         self._plan = None
         self._stream = stream
         if isinstance(nodes, np.ndarray):
@@ -178,7 +180,8 @@ class Plan:
             on_host = 0
         self.N, self.d = self._nodes.shape
         self.n, self.ell, self.m, self.delta, self.mode = n, ell, m, delta, mode
-        opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor)
+        opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor,
+                          max_ctas)
         rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
                               _stream_handle(stream))
         _check(rc, "rbffd_plan")
