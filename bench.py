@@ -291,6 +291,61 @@ def run_gpu(args):
     return 0
 
 
+def run_mixed(args):
+    """The mixed-degree workload: one plan + assemble per step on the clustered cube with
+    per-node degree 2..5 (n = 2M + 1), delta = 0.3, FALLBACK stabilization."""
+    import torch
+    from paper_1606_03135_gb300 import nodesets as NS
+    from paper_1606_03135_gb300 import rbffd as R
+    R.load()
+    torch.cuda.set_device(0)
+    name = args.workload
+    w = NS.MIXED_WORKLOADS[name]
+    X = w["gen"](**w["kw"])
+    n_node, ell_node, m_node = NS.mixed_degree_params(X, w["ells"])
+    Xd = torch.from_numpy(X).cuda()
+    delta = w["deltas"][0]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        p = R.Plan(Xd, n_node, ell_node, m_node, delta, mode=R.STAB_FALLBACK)
+        p.assemble()
+        st = p.stats()
+        p.close()
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sts = []
+    for s_ in range(args.steps):
+        ev[s_][0].record(stream)
+        sts.append(step())
+        ev[s_][1].record(stream)
+    torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    N = X.shape[0]
+    st = sts[-1]
+    trav = sum(x["ms_traversal"] + x["ms_fallback"] for x in sts)
+    alg = sum(x["alg_flops"] for x in sts)
+    line = {"metric": METRIC, "value": N * args.steps / (total_ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": name, "N": N, "d": 3, "ells": list(w["ells"]),
+                       "n_max": int(n_node.max()), "delta": delta, "stab": "fallback"},
+            "roofline": {"bound": "alu", "achieved": alg / (trav / 1e3) / 1e12,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": alg / (trav / 1e3) / 1e12 / FP64_PEAK_TFLOPS},
+            "stats": {k: st[k] for k in ("n_centers", "n_fallback", "n_rejected", "sum_cols",
+                                         "max_ball", "nnz", "ms_stencils", "ms_traversal",
+                                         "ms_fallback", "ms_finalize")}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serve(args):
     """The serving workload: a seeded mix of jobs (2D/3D, N log-uniform, ell 2..5, random
     delta) replayed with Poisson arrivals at two offered loads of the measured single-stream
@@ -342,6 +397,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload and args.workload.startswith("cube3d_") and "mixed" in args.workload:
+        return run_mixed(args)
     return run_gpu(args)
 
 

@@ -67,7 +67,9 @@ typedef struct {
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */
 
 /* CSR of L.  Device pointers owned by the plan; valid until the next rbffd_assemble on
- * the same plan or rbffd_destroy.  Each row has n entries, columns ascending. */
+ * the same plan or rbffd_destroy.  Each row has n entries (the size of the stencil that
+ * produced it, for rbffd_plan_mixed), columns ascending.  nnz is -1 when it is not known yet
+ * (per-node stencils assembled with opts.sync = 0: read it from rbffd_stats). */
 typedef struct {
     int64_t n_rows;
     int64_t nnz;
@@ -95,6 +97,7 @@ typedef struct {
     float ms_traversal;     /* device time of the traversal + local-solve kernel */
     float ms_fallback;      /* device time of the FALLBACK re-solves (0 otherwise) */
     float ms_finalize;      /* device time of the CSR scatter */
+    int64_t nnz;            /* entries of L (N n for uniform stencils) */
     int64_t plan_bytes;     /* device memory the plan holds after rbffd_plan */
     int64_t assemble_bytes; /* device memory rbffd_assemble adds (exact, known after plan) */
 } rbffd_stats_t;
@@ -117,6 +120,17 @@ typedef struct {
 int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
                const rbffd_opts* opts, void* stream, rbffd_plan_t* out);
 
+/* rbffd_plan_mixed -- as rbffd_plan, for node sets whose nodes carry their own stencil size
+ * n_node[k], polynomial degree ell_node[k] and PHS exponent m_node[k] (host arrays of N
+ * int32, copied; same limits as rbffd_plan's scalars, M_k <= n_k).  Node k's stencil is x_k
+ * and its n_k - 1 nearest neighbours, its width and retention ball follow from that
+ * stencil, and a row of L takes the stencil that produced it, so rows have the length n of
+ * that stencil (row_ptr gives them; nnz is known once rbffd_assemble has completed).  The
+ * paper uses one n and ell everywhere (§4.1); this extends the traversal unchanged. */
+int rbffd_plan_mixed(const double* nodes, int64_t N, int d, const int32_t* n_node,
+                     const int32_t* ell_node, const int32_t* m_node, double delta,
+                     const rbffd_opts* opts, void* stream, rbffd_plan_t* out);
+
 /* rbffd_assemble -- the traversal of §4.1 with the stabilization of §4.2.1: greedy center
  * selection, one factorization per center, multi-right-hand-side solves, Lebesgue test
  * and scatter into CSR (owned by the plan, described through *out, which may be NULL).
@@ -134,13 +148,14 @@ int rbffd_apply(rbffd_plan_t plan, const double* u, double* y, void* stream);
 int rbffd_stats(rbffd_plan_t plan, rbffd_stats_t* out);
 
 /* rbffd_export -- copy L and the stencil ownership to host memory (tests, serving).
- * row_ptr [N+1], col [N*n], val [N*n], owner [N] (stencil that produced each row;
+ * row_ptr [N+1], col [nnz], val [nnz], owner [N] (stencil that produced each row;
  * a FALLBACK row names itself).  Any pointer may be NULL to skip it.  Synchronous. */
 int rbffd_export(rbffd_plan_t plan, int64_t* row_ptr, int32_t* col, double* val,
                  int32_t* owner);
 
 /* rbffd_export_stencils -- copy the kNN stencils to host memory: nbr [N][n] (nbr[k][0] ==
- * k, ordered by (squared distance, index)), rho2 [N] (squared stencil width), ball_len [N]
+ * k, ordered by (squared distance, index); n is the largest stencil size of the plan), rho2
+ * [N] (squared stencil width), ball_len [N]
  * (retention-ball size; the ball is the prefix nbr[k][0..ball_len)).  NULL skips. */
 int rbffd_export_stencils(rbffd_plan_t plan, int32_t* nbr, double* rho2, int32_t* ball_len);
 

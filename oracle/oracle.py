@@ -65,6 +65,9 @@ def lib():
             L.ora_assemble.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_double, C.c_int, P, P, P, P, P, P, P, P,
                                        C.POINTER(Stats)]
+            L.ora_assemble_mixed.argtypes = [P, C.c_int64, C.c_int, P, P, P, C.c_int,
+                                             C.c_double, C.c_int, P, P, P, P, P, P, P, P,
+                                             C.POINTER(Stats)]
             _lib = L
     return _lib
 
@@ -154,6 +157,36 @@ def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None):
                               _ptr(is_center), _ptr(lam_row), C.byref(st)), "assemble")
     return dict(row_ptr=row_ptr, col=col, val=val, owner=owner, is_center=is_center,
                 lam_row=lam_row, stats=st.as_dict(), nbr=nbr, d2=d2)
+
+
+def assemble_mixed(X, n_node, ell_node, m_node, delta, mode=STAB_SEQ, nbr=None, d2=None):
+    """The traversal with per-node stencil size, degree and PHS exponent.  Returns the same
+    dict as assemble(); CSR rows have the length of the stencil that produced them."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    N, d = X.shape
+    n_node = np.ascontiguousarray(n_node, dtype=np.int32)
+    ell_node = np.ascontiguousarray(ell_node, dtype=np.int32)
+    m_node = np.ascontiguousarray(m_node, dtype=np.int32)
+    n_max = int(n_node.max())
+    if nbr is None or d2 is None:
+        nbr, d2 = knn(X, n_max)
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    col = np.zeros(N * n_max, dtype=np.int32)
+    val = np.zeros(N * n_max, dtype=np.float64)
+    owner = np.zeros(N, dtype=np.int32)
+    is_center = np.zeros(N, dtype=np.uint8)
+    lam_row = np.zeros(N, dtype=np.float64)
+    st = Stats()
+    _check(lib().ora_assemble_mixed(_ptr(X), N, d, _ptr(n_node), _ptr(ell_node), _ptr(m_node),
+                                    n_max, float(delta), mode,
+                                    _ptr(np.ascontiguousarray(nbr, dtype=np.int32)),
+                                    _ptr(np.ascontiguousarray(d2, dtype=np.float64)),
+                                    _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(owner),
+                                    _ptr(is_center), _ptr(lam_row), C.byref(st)),
+           "assemble_mixed")
+    nnz = int(row_ptr[-1])
+    return dict(row_ptr=row_ptr, col=col[:nnz], val=val[:nnz], owner=owner,
+                is_center=is_center, lam_row=lam_row, stats=st.as_dict(), nbr=nbr, d2=d2)
 
 
 def csr_matvec(row_ptr, col, val, u):

@@ -405,3 +405,128 @@ done:
     free(ball); free(covered); free(redo); free(Y); free(W); free(lam); free(cols);
     return rc;
 }
+
+/* ---------------------------------------------------------------- mixed stencils */
+
+/* The same traversal for node sets whose nodes carry their own stencil size n_k,
+ * polynomial degree ell_k and PHS exponent m_k (e.g. a higher degree in part of the
+ * domain).  nbr/d2 are the kNN lists of length n_max = max n_k (ora_knn); node k's stencil
+ * is the first n_k entries of its list, its width rho_k the distance of the n_k-th.  A row
+ * takes the stencil that produced it, so rows have the length n of that stencil; they are
+ * stored by row_ptr (N+1), col/val hold up to N*n_max entries. */
+int ora_assemble_mixed(const double* X, int64_t N, int d, const int32_t* n_node,
+                       const int32_t* ell_node, const int32_t* m_node, int n_max, double delta,
+                       int mode, const int32_t* nbr, const double* d2, int64_t* row_ptr,
+                       int32_t* col, double* val, int32_t* owner, uint8_t* is_center,
+                       double* lam_row, ora_stats* st) {
+    if (N < 1 || n_max < 1 || n_max > N || (d != 2 && d != 3) || !(delta > 0.0 && delta <= 1.0) ||
+        mode < 0 || mode > 2)
+        return ORA_EINVAL;
+    for (int64_t k = 0; k < N; ++k) {
+        if (n_node[k] < 1 || n_node[k] > n_max || m_node[k] < 3 || (m_node[k] % 2) == 0 ||
+            ell_node[k] < 0 || ora_poly_terms(d, ell_node[k], NULL) > n_node[k])
+            return ORA_EINVAL;
+    }
+    ora_stats s0;
+    memset(&s0, 0, sizeof(s0));
+    s0.min_abs_margin = INFINITY;
+    const double f = (1.0 - delta) * (1.0 - delta);
+    int32_t* ball = (int32_t*)malloc(sizeof(int32_t) * N);
+    int32_t* src = (int32_t*)malloc(sizeof(int32_t) * N);   /* stencil of each row */
+    int32_t* rcol = (int32_t*)malloc(sizeof(int32_t) * N * n_max);
+    double* rval = (double*)malloc(sizeof(double) * N * n_max);
+    uint8_t* covered = (uint8_t*)calloc((size_t)N, 1);
+    uint8_t* redo = (uint8_t*)calloc((size_t)N, 1);
+    double* Y = (double*)malloc(sizeof(double) * n_max * d);
+    double* W = (double*)malloc(sizeof(double) * n_max * n_max);
+    double* lam = (double*)malloc(sizeof(double) * n_max);
+    int* cols = (int*)malloc(sizeof(int) * n_max);
+    int rc = ORA_OK;
+    if (!ball || !src || !rcol || !rval || !covered || !redo || !Y || !W || !lam || !cols) {
+        rc = ORA_ENOMEM;
+        goto done;
+    }
+    for (int64_t k = 0; k < N; ++k) {  /* retention balls with each node's own width */
+        const int nk = n_node[k];
+        const double r2 = f * d2[k * n_max + nk - 1];
+        int len = 0;
+        for (int t = 0; t < nk; ++t)
+            if (d2[k * n_max + t] <= r2) len = t + 1;
+        ball[k] = len;
+        owner[k] = -1;
+        is_center[k] = 0;
+    }
+    for (int64_t k = 0; k < N; ++k) {
+        if (covered[k]) continue;
+        const int32_t* I = nbr + k * n_max;
+        const int nk = n_node[k];
+        int q = 0;
+        for (int t = 0; t < ball[k]; ++t)
+            if (!covered[I[t]]) cols[q++] = t;
+        for (int e = 0; e < q; ++e)
+            for (int a = 0; a < d; ++a) Y[e * d + a] = X[(int64_t)I[cols[e]] * d + a];
+        rc = ora_local_weights(X, d, I, nk, ell_node[k], m_node[k], ORA_OP_LAPLACIAN, Y, q, W, lam);
+        if (rc != ORA_OK) goto done;
+        is_center[k] = 1;
+        s0.n_centers++;
+        s0.sum_cols += q;
+        for (int e = 0; e < q; ++e) {
+            int64_t i = I[cols[e]];
+            int pass = 1;
+            if (e > 0) {
+                double margin = (lam[0] - lam[e]) / lam[0];
+                pass = lam[e] <= lam[0];
+                s0.n_decisions++;
+                if (!pass) s0.n_rejected++;
+                if (fabs(margin) < s0.min_abs_margin) s0.min_abs_margin = fabs(margin);
+                if (fabs(margin) <= 1e-9) s0.n_near_tie++;
+            }
+            if (mode == ORA_STAB_SEQ && !pass) continue;
+            covered[i] = 1;
+            owner[i] = (int32_t)k;
+            s0.sum_q++;
+            if (lam_row) lam_row[i] = lam[e];
+            if (mode == ORA_STAB_FALLBACK && !pass) { redo[i] = 1; continue; }
+            src[i] = (int32_t)k;
+            for (int j = 0; j < nk; ++j) {
+                rcol[i * n_max + j] = I[j];
+                rval[i * n_max + j] = W[(int64_t)j * q + e];
+            }
+        }
+    }
+    if (mode == ORA_STAB_FALLBACK) {
+        for (int64_t i = 0; i < N; ++i) {
+            if (!redo[i]) continue;
+            const int32_t* I = nbr + i * n_max;
+            const int ni = n_node[i];
+            rc = ora_local_weights(X, d, I, ni, ell_node[i], m_node[i], ORA_OP_LAPLACIAN,
+                                   X + i * d, 1, W, lam);
+            if (rc != ORA_OK) goto done;
+            owner[i] = (int32_t)i;
+            is_center[i] = 2;
+            s0.n_fallback++;
+            s0.sum_cols++;
+            if (lam_row) lam_row[i] = lam[0];
+            src[i] = (int32_t)i;
+            for (int j = 0; j < ni; ++j) {
+                rcol[i * n_max + j] = I[j];
+                rval[i * n_max + j] = W[j];
+            }
+        }
+    }
+    row_ptr[0] = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        const int len = n_node[src[i]];
+        row_ptr[i + 1] = row_ptr[i] + len;
+        for (int j = 0; j < len; ++j) {
+            col[row_ptr[i] + j] = rcol[i * n_max + j];
+            val[row_ptr[i] + j] = rval[i * n_max + j];
+        }
+        sort_row(col + row_ptr[i], val + row_ptr[i], len);
+    }
+done:
+    if (st) *st = s0;
+    free(ball); free(src); free(rcol); free(rval); free(covered); free(redo);
+    free(Y); free(W); free(lam); free(cols);
+    return rc;
+}

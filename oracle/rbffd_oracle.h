@@ -70,6 +70,15 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
                  double* val, int32_t* owner, uint8_t* is_center, double* lam_row,
                  ora_stats* stats);
 
+/* Mixed stencils: node k has its own n_k <= n_max, ell_k and m_k.  nbr/d2 from ora_knn with
+ * n = n_max; node k's stencil is the first n_k entries.  Rows take the length of the stencil
+ * that produced them: row_ptr[N+1], col/val with room for N*n_max entries. */
+int ora_assemble_mixed(const double* X, int64_t N, int d, const int32_t* n_node,
+                       const int32_t* ell_node, const int32_t* m_node, int n_max, double delta,
+                       int mode, const int32_t* nbr, const double* d2, int64_t* row_ptr,
+                       int32_t* col, double* val, int32_t* owner, uint8_t* is_center,
+                       double* lam_row, ora_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,15 @@ struct rbffd_plan_s {
     int* ball_len = nullptr;
     int* indeg = nullptr;
     long long* slot_off = nullptr;
-    short* basis = nullptr;  // monomial recurrence + Laplacian tables, M * (2 + 2d)
+    short* basis = nullptr;  // monomial recurrence + Laplacian tables of the degrees in use
+    int basis_count = 0;
+    int boff[kMaxEll + 1] = {};
+    int Mof[kMaxEll + 1] = {};
+    bool mixed = false;      // per-node n, ell, m (rbffd_plan_mixed)
+    int* node_n = nullptr;
+    signed char* node_ell = nullptr;
+    signed char* node_m = nullptr;
+    long long nnz = 0;
     DevCounters* ctr = nullptr;
     DevCounters h_ctr{};           // host copy of the device counters
     void* plan_block = nullptr;    // one allocation for the stencil arrays
@@ -36,7 +44,7 @@ struct rbffd_plan_s {
     void* asm_block = nullptr;     // one allocation for the traversal and CSR arrays
     int max_ball = 0;
     long long total_slots = 0;
-    int qcap = 0, stride = 0;
+    int qcap = 0, stride = 0, grid = 0, fb_grid = 0;
     // traversal and results
     bool have_asm = false, assembled = false;
     int* state = nullptr;
@@ -222,12 +230,17 @@ void free_plan(rbffd_plan_s* p) {
 
 // Copy the device counters of the last call to the host (waits for the plan's stream).
 int refresh_counters(rbffd_plan_s* p) {
-    if (p->counters_fresh) return RBFFD_OK;
-    int rc;
+    int rc;  // always copied: a captured assembly may have been replayed since the last call
+    long long nnz = (long long)p->N * p->n;
     if ((rc = bad(cudaMemcpyAsync(&p->h_ctr, p->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
-                                  p->last))) ||
-        (rc = bad(cudaStreamSynchronize(p->last))))
+                                  p->last))))
         return rc;
+    if (p->mixed && p->assembled &&
+        (rc = bad(cudaMemcpyAsync(&nnz, p->row_ptr + p->N, sizeof(long long),
+                                  cudaMemcpyDeviceToHost, p->last))))
+        return rc;
+    if ((rc = bad(cudaStreamSynchronize(p->last)))) return rc;
+    p->nnz = nnz;
     p->counters_fresh = true;
     return RBFFD_OK;
 }
@@ -257,16 +270,39 @@ const char* rbffd_strerror(int code) {
     }
 }
 
-int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
-               const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
+}  // extern "C"
+
+namespace {
+
+// Shared by rbffd_plan (uniform n, ell, m: n_node == NULL) and rbffd_plan_mixed (per-node
+// host arrays; n is then the largest stencil size).
+int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
+              const int32_t* n_node, const int32_t* ell_node, const int32_t* m_node,
+              double delta, const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
     if (!out) return RBFFD_EINVAL;
     *out = nullptr;
     if (!nodes || (d != 2 && d != 3) || n < 1 || n > kMaxStencil || N < n || N > 0x7ffffffeLL ||
         ell < 0 || ell > kMaxEll || m < 3 || m > 15 || (m % 2) == 0 || !(delta > 0.0) ||
         !(delta <= 1.0))
         return RBFFD_EINVAL;
-    const int M = (int)binom(ell + d, d);
-    if (M > n) return RBFFD_EINVAL;
+    const bool mixed = n_node != nullptr;
+    int ell_lo = ell, ell_hi = ell, K_max = n + (int)binom(ell + d, d);
+    if ((int)binom(ell + d, d) > n) return RBFFD_EINVAL;
+    if (mixed) {
+        ell_lo = kMaxEll;
+        ell_hi = 0;
+        K_max = 0;
+        for (int64_t k = 0; k < N; ++k) {
+            const int nk = n_node[k], lk = ell_node[k], mk = m_node[k];
+            if (nk < 1 || nk > n || lk < 0 || lk > kMaxEll || mk < 3 || mk > 15 || (mk % 2) == 0)
+                return RBFFD_EINVAL;
+            const int Mk = (int)binom(lk + d, d);
+            if (Mk > nk) return RBFFD_EINVAL;
+            ell_lo = lk < ell_lo ? lk : ell_lo;
+            ell_hi = lk > ell_hi ? lk : ell_hi;
+            K_max = nk + Mk > K_max ? nk + Mk : K_max;
+        }
+    }
     rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0};
     if (opts) o = *opts;
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
@@ -277,17 +313,27 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
     rbffd_plan_s* p = new (std::nothrow) rbffd_plan_s();
     if (!p) return RBFFD_ENOMEM;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    p->N = N; p->d = d; p->n = n; p->ell = ell; p->m = m; p->M = M; p->K = n + M;
-    p->delta = delta; p->opts = o; p->last = s;
+    p->N = N; p->d = d; p->n = n; p->ell = ell; p->m = m; p->M = K_max - n; p->K = K_max;
+    p->delta = delta; p->opts = o; p->last = s; p->mixed = mixed;
     cudaGetDevice(&p->device);
     int rc = RBFFD_OK;
     void* scratch = nullptr;
     const int Ni = (int)N;
     const int ncell_max = 2 * Ni + 64;
     const size_t sbytes = grid_scratch_bytes(Ni, d, ncell_max);
-    short h_basis[kMaxTerms * 8];
-    basis_tables(d, ell, h_basis);
-    const size_t basis_count = (size_t)M * (2 + 2 * d);
+    // basis tables of every degree in [ell_lo, ell_hi], one after the other
+    short h_basis[(kMaxEll + 1) * kMaxTerms * 8];
+    size_t basis_count = 0;
+    for (int l = 0; l <= kMaxEll; ++l) {
+        p->Mof[l] = (int)binom(l + d, d);
+        p->boff[l] = 0;
+    }
+    for (int l = ell_lo; l <= ell_hi; ++l) {
+        p->boff[l] = (int)basis_count;
+        basis_tables(d, l, h_basis + basis_count);
+        basis_count += (size_t)p->Mof[l] * (2 + 2 * d);
+    }
+    p->basis_count = (int)basis_count;
     for (auto& e : p->ev)
         if ((rc = bad(cudaEventCreate(&e))) != RBFFD_OK) goto fail;
     {
@@ -295,7 +341,10 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
         const size_t oX = c.add<double>((size_t)N * d), oN = c.add<int>((size_t)N * n),
                      oR = c.add<double>((size_t)N), oB = c.add<int>((size_t)N),
                      oI = c.add<int>((size_t)N), oS = c.add<long long>((size_t)N + 1),
-                     oP = c.add<short>(basis_count), oC = c.add<DevCounters>(1);
+                     oP = c.add<short>(basis_count), oC = c.add<DevCounters>(1),
+                     oNn = c.add<int>(mixed ? (size_t)N : 0),
+                     oNl = c.add<signed char>(mixed ? (size_t)N : 0),
+                     oNm = c.add<signed char>(mixed ? (size_t)N : 0);
         if ((rc = pool_alloc(&p->plan_block, c.bytes, p->device, s))) goto fail;
         p->plan_bytes = c.bytes;
         p->X = at<double>(p->plan_block, oX);
@@ -306,6 +355,22 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
         p->slot_off = at<long long>(p->plan_block, oS);
         p->basis = at<short>(p->plan_block, oP);
         p->ctr = at<DevCounters>(p->plan_block, oC);
+        if (mixed) {
+            p->node_n = at<int>(p->plan_block, oNn);
+            p->node_ell = at<signed char>(p->plan_block, oNl);
+            p->node_m = at<signed char>(p->plan_block, oNm);
+        }
+    }
+    if (mixed) {  // per-node parameters to the device (small: staged through host vectors)
+        signed char* tmp = new (std::nothrow) signed char[2 * (size_t)N];
+        if (!tmp) { rc = RBFFD_ENOMEM; goto fail; }
+        for (int64_t k = 0; k < N; ++k) { tmp[k] = (signed char)ell_node[k]; tmp[N + k] = (signed char)m_node[k]; }
+        rc = bad(cudaMemcpyAsync(p->node_n, n_node, (size_t)N * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (!rc) rc = bad(cudaMemcpyAsync(p->node_ell, tmp, (size_t)N, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = bad(cudaMemcpyAsync(p->node_m, tmp + N, (size_t)N, cudaMemcpyHostToDevice, s));
+        if (!rc) rc = bad(cudaStreamSynchronize(s));  // the staging buffer is freed next
+        delete[] tmp;
+        if (rc) goto fail;
     }
     if ((rc = pool_alloc(&scratch, sbytes, p->device, s))) goto fail;
     if ((rc = bad(cudaMemcpyAsync(p->X, nodes, (size_t)N * d * sizeof(double),
@@ -319,8 +384,8 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
         goto fail;
     cudaEventRecord(p->ev[0], s);
     rc = launch_grid_and_knn(d, p->X, Ni, n, (1.0 - delta) * (1.0 - delta), scratch, sbytes,
-                             ncell_max, p->nbr, p->rho2, p->ball_len, p->indeg, p->ctr, s,
-                             &p->launches);
+                             ncell_max, p->nbr, p->rho2, p->ball_len, p->indeg, p->node_n,
+                             p->ctr, s, &p->launches);
     if (rc) goto fail;
     rc = launch_scan_i32_to_i64(p->ball_len, p->slot_off, Ni, s, &p->launches);
     if (rc) goto fail;
@@ -354,10 +419,13 @@ int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, dou
         int stride = 0;
         const size_t per_cta = solve_smem_per_cta(n, p->K, p->qcap, d,
                                                   o.factor == RBFFD_FACTOR_LDLT, &stride) +
-                               basis_smem_bytes(M, d);
+                               basis_smem_bytes((int)basis_count);
         const size_t avail = (size_t)max_optin_smem() - 64;
         p->stride = stride;
         if (per_cta > avail) { rc = RBFFD_EINVAL; goto fail; }
+        rc = prepare_solve_kernels(d, o.factor == RBFFD_FACTOR_LDLT, n, p->K, p->qcap,
+                                   (int)basis_count, &p->grid, &p->fb_grid);
+        if (rc) goto fail;
     }
     *out = p;
     return RBFFD_OK;
@@ -365,6 +433,27 @@ fail:
     if (scratch) cudaFreeAsync(scratch, s);
     free_plan(p);
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
+               const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
+    return plan_impl(nodes, N, d, n, ell, m, nullptr, nullptr, nullptr, delta, opts, stream, out);
+}
+
+int rbffd_plan_mixed(const double* nodes, int64_t N, int d, const int32_t* n_node,
+                     const int32_t* ell_node, const int32_t* m_node, double delta,
+                     const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
+    if (!out) return RBFFD_EINVAL;
+    *out = nullptr;
+    if (!n_node || !ell_node || !m_node || N < 1) return RBFFD_EINVAL;
+    int n_max = 0;
+    for (int64_t k = 0; k < N; ++k) n_max = n_node[k] > n_max ? n_node[k] : n_max;
+    return plan_impl(nodes, N, d, n_max, 0, 3, n_node, ell_node, m_node, delta, opts, stream,
+                     out);
 }
 
 int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
@@ -396,7 +485,9 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     }
     SolveArgs a{};
     a.X = p->X; a.nbr = p->nbr; a.rho2 = p->rho2; a.ball_len = p->ball_len;
-    a.slot_off = p->slot_off; a.basis = p->basis;
+    a.slot_off = p->slot_off; a.basis = p->basis; a.basis_count = p->basis_count;
+    for (int l = 0; l <= kMaxEll; ++l) { a.boff[l] = p->boff[l]; a.Mof[l] = p->Mof[l]; }
+    a.node_n = p->node_n; a.node_ell = p->node_ell; a.node_m = p->node_m;
     a.N = (int)p->N; a.n = p->n; a.M = p->M; a.K = p->K; a.m = p->m; a.ell = p->ell;
     a.qcap = p->qcap; a.stride = p->stride; a.mode = p->opts.stab_mode;
     a.coef = (double)(p->m * (p->m + p->d - 2));
@@ -407,6 +498,8 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.no_seed = p->opts.fault_inject == 1;
     a.factor = p->opts.factor;
     a.max_ctas = p->opts.max_ctas;
+    a.grid = p->grid;
+    a.fb_grid = p->fb_grid;
     if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
     rc = launch_traversal(p->d, a, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
     if (rc) return rc;
@@ -422,18 +515,17 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     cudaEventRecord(p->ev[6], s);
     p->assembled = true;
     p->counters_fresh = false;
+    if (p->opts.sync) {
+        if ((rc = refresh_counters(p))) return rc;
+    }
     if (out) {
         out->n_rows = p->N;
-        out->nnz = p->N * p->n;
+        out->nnz = p->opts.sync || !p->mixed ? (p->mixed ? p->nnz : p->N * p->n) : -1;
         out->row_ptr = reinterpret_cast<const int64_t*>(p->row_ptr);
         out->col = p->col;
         out->val = p->val;
     }
-    if (p->opts.sync) {
-        if ((rc = refresh_counters(p))) return rc;
-        return p->h_ctr.status;
-    }
-    return RBFFD_OK;
+    return p->opts.sync ? p->h_ctr.status : RBFFD_OK;
 }
 
 int rbffd_apply(rbffd_plan_t p, const double* u, double* y, void* stream) {
@@ -465,10 +557,8 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
         out->n_singular = c.n_singular;
         out->status = c.status;
         const double K = p->K;
-        const double c3 = p->opts.factor == RBFFD_FACTOR_LU ? 2.0 / 3.0 : 1.0 / 3.0;
-        const double lu = c3 * K * K * K, col = 2.0 * K * K;
-        out->alg_flops = (double)c.n_centers * lu + (double)(p->N - (int64_t)c.n_fallback) * col +
-                         (double)c.n_fallback * (lu + col);
+        out->alg_flops = c.alg_flops;
+        out->nnz = p->nnz;
         if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) out->ms_traversal = ms;
         if (cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) out->ms_fallback = ms;
         if (cudaEventElapsedTime(&ms, p->ev[5], p->ev[6]) == cudaSuccess) out->ms_finalize = ms;
@@ -484,8 +574,11 @@ int rbffd_export(rbffd_plan_t p, int64_t* row_ptr, int32_t* col, double* val, in
     const size_t N = (size_t)p->N, n = (size_t)p->n;
     int rc = RBFFD_OK;
     if (row_ptr && (rc = bad(cudaMemcpyAsync(row_ptr, p->row_ptr, (N + 1) * 8, cudaMemcpyDeviceToHost, s)))) return rc;
-    if (col && (rc = bad(cudaMemcpyAsync(col, p->col, N * n * 4, cudaMemcpyDeviceToHost, s)))) return rc;
-    if (val && (rc = bad(cudaMemcpyAsync(val, p->val, N * n * 8, cudaMemcpyDeviceToHost, s)))) return rc;
+    if ((rc = refresh_counters(p))) return rc;
+    const size_t nnz = (size_t)p->nnz;
+    (void)n;
+    if (col && (rc = bad(cudaMemcpyAsync(col, p->col, nnz * 4, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (val && (rc = bad(cudaMemcpyAsync(val, p->val, nnz * 8, cudaMemcpyDeviceToHost, s)))) return rc;
     if (owner && (rc = bad(cudaMemcpyAsync(owner, p->owner, N * 4, cudaMemcpyDeviceToHost, s)))) return rc;
     return bad(cudaStreamSynchronize(s));
 }

@@ -65,6 +65,31 @@ struct Basis {
     const short* lap_coef;
 };
 
+// The parameters of one stencil: size n, monomials M, system size K = n + M, PHS exponent m,
+// right-hand-side factor m (m + D - 2) and the basis tables of its degree.
+struct Shape {
+    int n, M, K, m;
+    double coef;
+    Basis bs;
+};
+
+template <int D>
+__device__ __forceinline__ Shape shape_of(const SolveArgs& a, const short* sbasis, int j) {
+    const int ell = a.node_ell ? (int)a.node_ell[j] : a.ell;
+    Shape s;
+    s.n = a.node_n ? a.node_n[j] : a.n;
+    s.M = a.Mof[ell];
+    s.K = s.n + s.M;
+    s.m = a.node_m ? (int)a.node_m[j] : a.m;
+    s.coef = (double)(s.m * (s.m + D - 2));
+    const short* b = sbasis + a.boff[ell];
+    s.bs.parent = b;
+    s.bs.var = b + s.M;
+    s.bs.lap_child = b + 2 * s.M;
+    s.bs.lap_coef = b + 2 * s.M + s.M * D;
+    return s;
+}
+
 // Bytes of one CTA's local system; *stride_out is S (full) or xs (packed).
 size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride_out) {
     int stride = packed ? qcap : K + qcap;
@@ -77,7 +102,7 @@ size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride
     return (b + 15) & ~size_t(15);
 }
 
-size_t basis_smem_bytes(int M, int D) { return ((size_t)M * (2 + 2 * D) * sizeof(short) + 15) & ~size_t(15); }
+size_t basis_smem_bytes(int count) { return ((size_t)count * sizeof(short) + 15) & ~size_t(15); }
 
 template <int D, bool PACKED>
 __device__ __forceinline__ void carve(char* p, int n, int K, int qcap, int S, StencilSmem& sm) {
@@ -122,25 +147,21 @@ __device__ __forceinline__ void carve(char* p, int n, int K, int qcap, int S, St
     sm.keep = reinterpret_cast<unsigned char*>(p);
 }
 
-__device__ __forceinline__ Basis load_basis(char* smem, const short* g, int M, int D) {
+__device__ __forceinline__ const short* load_basis(char* smem, const short* g, int count) {
     short* s = reinterpret_cast<short*>(smem);
-    for (int e = threadIdx.x; e < M * (2 + 2 * D); e += blockDim.x) s[e] = g[e];
-    Basis b;
-    b.parent = s;
-    b.var = s + M;
-    b.lap_child = s + 2 * M;
-    b.lap_coef = s + 2 * M + M * D;
-    return b;
+    for (int e = threadIdx.x; e < count; e += blockDim.x) s[e] = g[e];
+    return s;
 }
 
 // Assemble the local system of stencil j (§4.1) and its q right-hand sides (the columns in
 // sm.cols) in shared memory, with the whole CTA.  Full layout: both triangles of A_hat and
 // B_hat beside it.  Packed layout: the lower triangle of A_hat and B_hat apart.
 template <int D, bool PACKED>
-__device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q,
+__device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q,
                                const StencilSmem& sm) {
     const int tid = threadIdx.x;
-    const int n = a.n, M = a.M, K = a.K, m = a.m;
+    const int n = sh.n, M = sh.M, K = sh.K, m = sh.m;
+    const Basis& bs = sh.bs;
     double* X = sm.X;
     const int xs = sm.xs;
     double r2c = a.rho2[j];
@@ -148,7 +169,7 @@ __device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q
     const double rho = sqrt(r2c);
     const double* xc = a.X + (size_t)j * D;
     for (int t = tid; t < n; t += kNT) {
-        const int id = a.nbr[(size_t)j * n + t];
+        const int id = a.nbr[(size_t)j * a.n + t];
         for (int c = 0; c < D; ++c)
             sm.xi[t * D + c] = __ddiv_rn(__dsub_rn(a.X[(size_t)id * D + c], xc[c]), rho);
     }
@@ -194,8 +215,8 @@ __device__ void assemble_local(const SolveArgs& a, const Basis& bs, int j, int q
                     sm.A[rb * xs + ra] = pm;
                 }
                 const int ca = sm.colof[ra], cb = sm.colof[rb];
-                if (cb >= 0) X[ra * xs + cb] = __dmul_rn(a.coef, pm2);
-                if (ca >= 0) X[rb * xs + ca] = __dmul_rn(a.coef, pm2);
+                if (cb >= 0) X[ra * xs + cb] = __dmul_rn(sh.coef, pm2);
+                if (ca >= 0) X[rb * xs + ca] = __dmul_rn(sh.coef, pm2);
             }
             pr += di;
             off += dj;
@@ -290,10 +311,10 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 // LU with partial pivoting of [A_hat | B_hat] in the full layout (the paper's decomposition,
 // §4.3 cost model (2/3) K^3 + 2 K^2 q), then back substitution.  Returns false (uniformly)
 // on an exactly zero pivot; on success row r of the right-hand-side block holds unknown r.
-__device__ bool factor_solve_lu(const SolveArgs& a, int q, const StencilSmem& sm) {
+__device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
     __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int K = a.K, S = sm.xs;
+    const int S = sm.xs;
     const int Wd = K + q;
     for (int r = tid; r < K; r += kNT) sm.rowof[r] = r;
     // the pivot search, row swap, reciprocal and multipliers are done by warp 0 alone (FP64
@@ -377,10 +398,10 @@ __device__ bool factor_solve_lu(const SolveArgs& a, int q, const StencilSmem& sm
 // and 2x2 pivots with alpha = (1 + sqrt(17)) / 8; symmetric swaps are tracked in sm.perm.
 // Returns false (uniformly) on an exactly singular pivot column.  On success sm.rowof[u] is
 // the row of the right-hand-side block that holds unknown u.
-__device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& sm) {
+__device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
     __shared__ int s_ok, s_kind;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int K = a.K, xs = sm.xs;
+    const int xs = sm.xs;
     double* T = sm.T;
     double* X = sm.X;
     for (int r = tid; r < K; r += kNT) sm.perm[r] = r;
@@ -562,18 +583,18 @@ __device__ bool factor_solve_ldlt(const SolveArgs& a, int q, const StencilSmem& 
 }
 
 template <int D, bool PACKED>
-__device__ bool solve_local(const SolveArgs& a, const Basis& bs, int j, int q,
+__device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
                             const StencilSmem& sm) {
-    assemble_local<D, PACKED>(a, bs, j, q, sm);
-    return PACKED ? factor_solve_ldlt(a, q, sm) : factor_solve_lu(a, q, sm);
+    assemble_local<D, PACKED>(a, sh, j, q, sm);
+    return PACKED ? factor_solve_ldlt(sh.K, q, sm) : factor_solve_lu(sh.K, q, sm);
 }
 
 // Local L-Lebesgue value sum_r |w_r| of every solved column (one warp per column).
-__device__ __forceinline__ void lebesgue_values(const SolveArgs& a, int q, const StencilSmem& sm) {
+__device__ __forceinline__ void lebesgue_values(int n, int q, const StencilSmem& sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = wid; c < q; c += kNT / 32) {
         double s = 0.0;
-        for (int r = lane; r < a.n; r += 32) s += fabs(sm.X[sm.rowof[r] * sm.xs + c]);
+        for (int r = lane; r < n; r += 32) s += fabs(sm.X[sm.rowof[r] * sm.xs + c]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) sm.lam[c] = s;
     }
@@ -637,13 +658,14 @@ template <int D, bool PACKED>
 __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_j, s_q;
-    const Basis bs = load_basis(smem, a.basis, a.M, D);
+    const short* sbasis = load_basis(smem, a.basis, a.basis_count);
     StencilSmem sm;
     carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int n = a.n, N = a.N;
+    const int ns = a.n, N = a.N;  // ns: row stride of nbr and of a weight slot
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    const double c3 = PACKED ? 1.0 / 3.0 : 2.0 / 3.0;
 
     for (;;) {
         if (tid == 0) {
@@ -651,7 +673,7 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
             const int slot = atomicAdd(&a.ctr->q_head, 1);
             if (slot < N) {
                 const unsigned long long t0 = globaltimer_ns();
-                unsigned ns = 32;
+                unsigned nsl = 32;
                 for (;;) {
                     j = *((volatile int*)&a.queue[slot]);
                     if (j >= 0) break;
@@ -665,8 +687,8 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
                         j = -1;
                         break;
                     }
-                    __nanosleep(ns);
-                    if (ns < 2048) ns <<= 1;
+                    __nanosleep(nsl);
+                    if (nsl < 2048) nsl <<= 1;
                 }
             }
             s_j = j;
@@ -675,6 +697,8 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
         const int j = s_j;
         if (j < 0) break;
         __threadfence();
+        const Shape sh = shape_of<D>(a, sbasis, j);
+        const int n = sh.n;
 
         // columns: the center and every later ball member not already kept by an earlier center
         const int L = a.ball_len[j];
@@ -686,7 +710,7 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
                 if (t < L) {
                     if (t == 0) inc = true;
                     else {
-                        const int i = a.nbr[(size_t)j * n + t];
+                        const int i = a.nbr[(size_t)j * ns + t];
                         inc = (i > j) && (__ldcg(&a.owner[i]) >= j);
                     }
                 }
@@ -700,12 +724,12 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
         }
         __syncthreads();
         const int q = s_q;
-        const bool ok = solve_local<D, PACKED>(a, bs, j, q, sm);
-        if (ok) lebesgue_values(a, q, sm);
+        const bool ok = solve_local<D, PACKED>(a, sh, j, q, sm);
+        if (ok) lebesgue_values(n, q, sm);
         __syncthreads();
         // Lebesgue test (§4.2.1) per column; q <= n <= kNT, so one thread per column
         const long long base = a.slot_off[j];
-        bool failed = false;
+        bool failed = false, own = false;
         if (tid < q) {
             const double lam = ok ? sm.lam[tid] : nan;
             const bool test_ok =
@@ -718,27 +742,29 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
             a.slot_lam[base + sm.cols[tid]] = lam;
             a.slot_pass[base + sm.cols[tid]] = (tid == 0 || test_ok) ? 1 : 0;
             failed = tid > 0 && !test_ok;
+            own = keep && (a.mode != RBFFD_STAB_FALLBACK || tid == 0 || test_ok);
         }
         const int rejected = __syncthreads_count(failed);
+        const int owned = __syncthreads_count(own);
         double r2c = a.rho2[j];
         if (!(r2c > 0.0)) r2c = 1.0;
         const double inv_r2 = 1.0 / r2c;
         for (int e = tid; e < q * n; e += kNT) {
             const int c = e / n, r = e - c * n;
             if (!sm.keep[c]) continue;
-            a.slot_w[(base + sm.cols[c]) * n + r] =
+            a.slot_w[(base + sm.cols[c]) * ns + r] =
                 ok ? sm.X[sm.rowof[r] * sm.xs + c] * inv_r2 : nan;
         }
         // ownership: the earliest center keeping a row owns it
         if (tid > 0 && tid < q && sm.keep[tid]) {
-            const int i = a.nbr[(size_t)j * n + sm.cols[tid]];
+            const int i = a.nbr[(size_t)j * ns + sm.cols[tid]];
             atomicMin(&a.owner[i], j);
         }
         __threadfence();
         __syncthreads();
         // resolve: kept members become covered; every later ball member loses a dependency
         for (int t = 1 + tid; t < L; t += kNT) {
-            const int i = a.nbr[(size_t)j * n + t];
+            const int i = a.nbr[(size_t)j * ns + t];
             if (i <= j) continue;
             const int c = sm.colof[t];
             const bool kept = c >= 0 && sm.keep[c];
@@ -751,6 +777,8 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
                 atomicAdd(&a.ctr->n_singular, 1);
                 set_error(a.ctr, RBFFD_ESINGULAR);
             }
+            const double K = sh.K;
+            atomicAdd(&a.ctr->alg_flops, c3 * K * K * K + 2.0 * K * K * owned);
             atomicAdd(&a.ctr->n_centers, 1ull);
             atomicAdd(&a.ctr->sum_cols, (unsigned long long)q);
             atomicAdd(&a.ctr->n_rejected, (unsigned long long)rejected);
@@ -781,26 +809,28 @@ __global__ void k_fallback_collect(SolveArgs a) {
 template <int D, bool PACKED>
 __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
-    const Basis bs = load_basis(smem, a.basis, a.M, D);
+    const short* sbasis = load_basis(smem, a.basis, a.basis_count);
     StencilSmem sm;
     carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
     __syncthreads();
     const int tid = threadIdx.x;
     const int count = *((volatile int*)&a.ctr->fb_count);
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    const double c3 = PACKED ? 1.0 / 3.0 : 2.0 / 3.0;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int i = a.fb_list[w];
-        for (int t = tid; t < a.n; t += kNT) sm.colof[t] = (t == 0) ? 0 : -1;
+        const Shape sh = shape_of<D>(a, sbasis, i);
+        for (int t = tid; t < sh.n; t += kNT) sm.colof[t] = (t == 0) ? 0 : -1;
         if (tid == 0) sm.cols[0] = 0;
         __syncthreads();
-        const bool ok = solve_local<D, PACKED>(a, bs, i, 1, sm);
-        if (ok) lebesgue_values(a, 1, sm);
+        const bool ok = solve_local<D, PACKED>(a, sh, i, 1, sm);
+        if (ok) lebesgue_values(sh.n, 1, sm);
         __syncthreads();
         double r2c = a.rho2[i];
         if (!(r2c > 0.0)) r2c = 1.0;
         const double inv_r2 = 1.0 / r2c;
         const long long slot = a.slot_off[i];
-        for (int r = tid; r < a.n; r += kNT)
+        for (int r = tid; r < sh.n; r += kNT)
             a.slot_w[slot * a.n + r] = ok ? sm.X[sm.rowof[r] * sm.xs] * inv_r2 : nan;
         if (tid == 0) {
             a.slot_lam[slot] = ok ? sm.lam[0] : nan;
@@ -808,6 +838,8 @@ __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_
                 atomicAdd(&a.ctr->n_singular, 1);
                 set_error(a.ctr, RBFFD_ESINGULAR);
             }
+            const double K = sh.K;
+            atomicAdd(&a.ctr->alg_flops, c3 * K * K * K + 2.0 * K * K);
             atomicAdd(&a.ctr->n_fallback, 1ull);
             atomicAdd(&a.ctr->sum_cols, 1ull);
         }
@@ -815,16 +847,27 @@ __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_
     }
 }
 
+// Per-node stencils only: the length of every row (the size of the stencil that produced
+// it), into `len`, for the row-pointer scan.
+__global__ void k_row_len(SolveArgs a, int* __restrict__ len) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
+        const int s = a.fb_flag[i] ? i : a.owner[i];
+        len[i] = (s == kNoOwner) ? 0 : a.node_n[s];
+    }
+}
+
 // CSR: row i takes the weights of the column computed for it by its owner stencil (or its
-// own fallback stencil), with the columns sorted ascending.
+// own fallback stencil), with the columns sorted ascending.  Uniform stencils: row i starts
+// at i n; per-node stencils: row_ptr was scanned from the row lengths.
 __global__ void __launch_bounds__(256) k_finalize(SolveArgs a, long long* __restrict__ row_ptr,
                                                   int* __restrict__ col, double* __restrict__ val,
                                                   double* __restrict__ lam_row,
                                                   unsigned char* __restrict__ is_center) {
     extern __shared__ int fin_smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const int n = a.n;
-    int* cs = fin_smem + wib * n;
+    const int ns = a.n;
+    const bool uniform = a.node_n == nullptr;
+    int* cs = fin_smem + wib * ns;
     for (int i = blockIdx.x * wpb + wib; i < a.N; i += gridDim.x * wpb) {
         const bool fb = a.fb_flag[i] != 0;
         const int s = fb ? i : a.owner[i];
@@ -832,13 +875,14 @@ __global__ void __launch_bounds__(256) k_finalize(SolveArgs a, long long* __rest
             if (lane == 0) set_error(a.ctr, RBFFD_ECUDA);
             continue;
         }
+        const int n = uniform ? ns : a.node_n[s];
         int t = 0;
         if (s != i) {
             const int L = a.ball_len[s];
             int found = -1;
             for (int u0 = 1; u0 < L; u0 += 32) {
                 const int u = u0 + lane;
-                const bool hit = u < L && a.nbr[(size_t)s * n + u] == i;
+                const bool hit = u < L && a.nbr[(size_t)s * ns + u] == i;
                 const unsigned b = __ballot_sync(0xffffffffu, hit);
                 if (b && found < 0) found = u0 + __ffs(b) - 1;
             }
@@ -849,21 +893,24 @@ __global__ void __launch_bounds__(256) k_finalize(SolveArgs a, long long* __rest
             }
         }
         const long long slot = a.slot_off[s] + t;
-        for (int r = lane; r < n; r += 32) cs[r] = a.nbr[(size_t)s * n + r];
+        const long long rp = uniform ? (long long)i * ns : row_ptr[i];
+        for (int r = lane; r < n; r += 32) cs[r] = a.nbr[(size_t)s * ns + r];
         __syncwarp();
         for (int r = lane; r < n; r += 32) {
             const int c = cs[r];
             int rank = 0;
             for (int u = 0; u < n; ++u) rank += cs[u] < c;
-            col[(size_t)i * n + rank] = c;
-            val[(size_t)i * n + rank] = a.slot_w[slot * n + r];
+            col[rp + rank] = c;
+            val[rp + rank] = a.slot_w[slot * ns + r];
         }
         if (lane == 0) {
             if (fb) a.owner[i] = i;  // a fallback row names its own stencil
-            row_ptr[i] = (long long)i * n;
+            if (uniform) {
+                row_ptr[i] = rp;
+                if (i == a.N - 1) row_ptr[a.N] = (long long)a.N * ns;
+            }
             lam_row[i] = a.slot_lam[slot];
             is_center[i] = fb ? 2 : (s == i ? 1 : 0);
-            if (i == a.N - 1) row_ptr[a.N] = (long long)a.N * n;
         }
         __syncwarp();
     }
@@ -893,26 +940,65 @@ static int sm_count() {
     return v > 0 ? v : 1;
 }
 
+// The dynamic shared-memory limit is a per-kernel setting shared by every host thread, so it
+// is always raised to the device maximum (never lowered to one plan's need): plans assembled
+// concurrently on other streams cannot undercut each other's launches.
+static cudaError_t allow_max_smem(const void* kern) {
+    int dev = 0, mx = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                mx - (int)fa.sharedSizeBytes);
+}
+
+// Host-side preparation, done once per plan (not per assembly, so that rbffd_assemble only
+// enqueues stream work and can be captured in a CUDA graph): raise the kernels' shared-memory
+// limit and size the persistent grid from the occupancy.
+template <int D, bool PACKED>
+static int prepare(int n, int K, int qcap, int basis_count, int* grid, int* fb_grid) {
+    int stride = 0;
+    const size_t smem =
+        basis_smem_bytes(basis_count) + solve_smem_per_cta(n, K, qcap, D, PACKED, &stride);
+    auto kt = k_traversal<D, PACKED>;
+    auto kf = k_fallback_solve<D, PACKED>;
+    if (RB_CUDA(allow_max_smem((const void*)kt)) || RB_CUDA(allow_max_smem((const void*)kf)))
+        return RBFFD_EINVAL;
+    int per_sm = 0, per_sm_f = 0;
+    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kt, kNT, smem)) ||
+        RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, kf, kNT, smem)) ||
+        per_sm < 1 || per_sm_f < 1)
+        return RBFFD_EINVAL;
+    *grid = per_sm * sm_count();
+    *fb_grid = per_sm_f * sm_count();
+    return RBFFD_OK;
+}
+
+int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count, int* grid,
+                          int* fb_grid) {
+    if (D == 2)
+        return packed ? prepare<2, true>(n, K, qcap, basis_count, grid, fb_grid)
+                      : prepare<2, false>(n, K, qcap, basis_count, grid, fb_grid);
+    return packed ? prepare<3, true>(n, K, qcap, basis_count, grid, fb_grid)
+                  : prepare<3, false>(n, K, qcap, basis_count, grid, fb_grid);
+}
+
 template <int D, bool PACKED>
 static int traversal(const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
                      cudaEvent_t ev0, cudaEvent_t ev1) {
     int stride = 0;
     const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, PACKED, &stride);
-    const int basis_bytes = (int)basis_smem_bytes(a.M, D);
+    const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
     const size_t smem = basis_bytes + per_cta;
     auto kern = k_traversal<D, PACKED>;
-    if (RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-        return RBFFD_EINVAL;
-    int per_sm = 0;
-    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, smem)) ||
-        per_sm < 1)
-        return RBFFD_EINVAL;
     const int tb = 256, nb = (a.N + tb - 1) / tb;
     k_traversal_init<<<nb, tb, 0, s>>>(a.N, indeg, a.state, a.pending, a.owner, a.queue,
                                        a.fb_flag);
     k_traversal_seed<<<nb, tb, 0, s>>>(a, indeg);
     *launches += 2;
-    int grid = min(per_sm * sm_count(), a.N);
+    int grid = min(a.grid, a.N);
     if (a.max_ctas > 0) grid = min(grid, a.max_ctas);
     // A plain launch suffices: a worker only waits for queue entries that workers already
     // running will push (the smallest unresolved node is always ready once every center
@@ -941,14 +1027,10 @@ static int fallback(const SolveArgs& a, cudaStream_t s, int* launches) {
     k_fallback_collect<<<nb, tb, 0, s>>>(a);
     int stride = 0;
     const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, PACKED, &stride);
-    const int basis_bytes = (int)basis_smem_bytes(a.M, D);
+    const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
     const size_t smem = basis_bytes + per_cta;
     auto kern = k_fallback_solve<D, PACKED>;
-    if (RB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-        return RBFFD_EINVAL;
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, smem);
-    kern<<<max(per_sm, 1) * sm_count(), kNT, smem, s>>>(a, per_cta, basis_bytes);
+    kern<<<a.fb_grid, kNT, smem, s>>>(a, per_cta, basis_bytes);
     *launches += 2;
     return RB_LAUNCHED(__func__);
 }
@@ -961,6 +1043,13 @@ int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches) {
 
 int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* val,
                     double* lam_row, unsigned char* is_center, cudaStream_t s, int* launches) {
+    if (a.node_n) {  // rows of different lengths: scan their lengths into row_ptr first
+        const int tb = 256, nb = (a.N + tb - 1) / tb;
+        k_row_len<<<nb, tb, 0, s>>>(a, a.fb_list);
+        ++*launches;
+        int rc = launch_scan_i32_to_i64(a.fb_list, row_ptr, a.N, s, launches);
+        if (rc) return rc;
+    }
     const int wpb = 8;
     const int blocks = (a.N + wpb - 1) / wpb;
     k_finalize<<<blocks, wpb * 32, wpb * a.n * sizeof(int), s>>>(a, row_ptr, col, val, lam_row,

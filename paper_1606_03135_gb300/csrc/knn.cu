@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
                                              const double* __restrict__ sorted_X,
                                              int* __restrict__ nbr, double* __restrict__ rho2,
                                              int* __restrict__ ball_len, int* __restrict__ indeg,
-                                             DevCounters* ctr) {
+                                             const int* __restrict__ node_n, DevCounters* ctr) {
     extern __shared__ unsigned long long knn_smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -290,8 +290,9 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
             if (cnt == n || all) break;
             ++r;
         }
-        // write the stencil, its width and retention ball
-        const double r2k = __longlong_as_double((long long)lk[cur * n + n - 1]);
+        // write the stencil (the first nq of the n nearest), its width and retention ball
+        const int nq = node_n ? node_n[q] : n;
+        const double r2k = __longlong_as_double((long long)lk[cur * n + nq - 1]);
         const double rball = __dmul_rn(omd2, r2k);
         int blen = 0;
         for (int t0 = 0; t0 < n; t0 += 32) {
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
                 int id = li[cur * n + t];
                 double dd = __longlong_as_double((long long)lk[cur * n + t]);
                 nbr[(size_t)q * n + t] = id;
-                inb = dd <= rball;
+                inb = t < nq && dd <= rball;
                 if (t >= 1 && dd == 0.0) set_error(ctr, RBFFD_EDUPLICATE);
             }
             blen += __popc(__ballot_sync(0xffffffffu, inb));
@@ -335,7 +336,7 @@ size_t grid_scratch_bytes(int N, int D, int ncell_max) {
 template <int D>
 static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratch,
                         int ncell_max, int* nbr, double* rho2, int* ball_len, int* indeg,
-                        DevCounters* ctr, cudaStream_t s, int* launches) {
+                        const int* node_n, DevCounters* ctr, cudaStream_t s, int* launches) {
     char* p = static_cast<char*>(scratch);
     auto take = [&](size_t bytes) {
         char* r = p;
@@ -365,20 +366,21 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     size_t smem = (size_t)wpb * (2 * n + 32) * (sizeof(unsigned long long) + sizeof(int));
     int blocks = (N + wpb - 1) / wpb;
     k_knn<D><<<blocks, wpb * 32, smem, s>>>(X, N, n, omd2, gp, start, sorted_idx, sorted_X, nbr,
-                                            rho2, ball_len, indeg, ctr);
+                                            rho2, ball_len, indeg, node_n, ctr);
     *launches += 5;
     return RB_LAUNCHED(__func__);
 }
 
 int launch_grid_and_knn(int D, const double* X, int N, int n, double omd2, void* scratch,
                         size_t scratch_bytes, int ncell_max, int* nbr, double* rho2, int* ball_len,
-                        int* indeg, DevCounters* ctr, cudaStream_t s, int* launches) {
+                        int* indeg, const int* node_n, DevCounters* ctr, cudaStream_t s,
+                        int* launches) {
     if (scratch_bytes < grid_scratch_bytes(N, D, ncell_max)) return RBFFD_EINVAL;
     if (D == 2)
-        return grid_and_knn<2>(X, N, n, omd2, scratch, ncell_max, nbr, rho2, ball_len, indeg, ctr,
-                               s, launches);
-    return grid_and_knn<3>(X, N, n, omd2, scratch, ncell_max, nbr, rho2, ball_len, indeg, ctr, s,
-                           launches);
+        return grid_and_knn<2>(X, N, n, omd2, scratch, ncell_max, nbr, rho2, ball_len, indeg,
+                               node_n, ctr, s, launches);
+    return grid_and_knn<3>(X, N, n, omd2, scratch, ncell_max, nbr, rho2, ball_len, indeg, node_n,
+                           ctr, s, launches);
 }
 
 }  // namespace rbffd

@@ -72,7 +72,7 @@ extern "C" int rbffd_stencils_noalloc(const double* nodes, int64_t N, int d, int
     if ((rc = RB_CUDA(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), s)))) return rc;
     int launches = 0;
     rc = launch_grid_and_knn(d, nodes, Ni, n, (1.0 - delta) * (1.0 - delta), base, grid_bytes,
-                             ncell_max, nbr, rho2, ball_len, indeg, ctr, s, &launches);
+                             ncell_max, nbr, rho2, ball_len, indeg, nullptr, ctr, s, &launches);
     if (rc) return rc;
     int status = 0;
     if ((rc = RB_CUDA(cudaMemcpyAsync(&status, &ctr->status, sizeof(int),

@@ -53,7 +53,8 @@ struct DevCounters {
     unsigned long long n_rejected;
     unsigned long long sum_cols;
     unsigned long long n_fallback;
-    unsigned long long pad[22];
+    double alg_flops;        // sum over factored stencils of c K^3 + 2 K^2 (rows they own)
+    unsigned long long pad[21];
 };
 
 // Map a CUDA status to an RBFFD code; with RBFFD_DEBUG set in the environment the failing
@@ -94,9 +95,12 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // ------------------------------------------------------------------ host-side launchers
 struct PlanDev;  // defined in api.cu
 
+// Exact kNN with n neighbours per node; with node_n (device, may be NULL) node q's stencil,
+// width and ball use only its first node_n[q] neighbours.
 int launch_grid_and_knn(int D, const double* X, int N, int n, double omd2, void* scratch_grid,
                         size_t scratch_bytes, int ncell_max, int* nbr, double* rho2, int* ball_len,
-                        int* indeg, DevCounters* ctr, cudaStream_t s, int* launches);
+                        int* indeg, const int* node_n, DevCounters* ctr, cudaStream_t s,
+                        int* launches);
 size_t grid_scratch_bytes(int N, int D, int ncell_max);
 
 int launch_scan_i32_to_i64(const int* in, long long* out, int count, cudaStream_t s,
@@ -109,6 +113,14 @@ struct SolveArgs {
     const int* ball_len;
     const long long* slot_off;
     const short* basis;        // monomial recurrence and Laplacian tables (see assemble.cu)
+    int basis_count;           // shorts in `basis` (tables of every degree in use)
+    int boff[kMaxEll + 1];     // offset of degree ell's tables in `basis`
+    int Mof[kMaxEll + 1];      // number of monomials of degree <= ell
+    // Per-node stencil parameters (NULL: every node uses n, ell, m).  n is also the row stride
+    // of nbr and of a weight slot (the largest stencil size); M and K are the largest.
+    const int* node_n;
+    const signed char* node_ell;
+    const signed char* node_m;
     int N, n, M, K, m, ell;
     int qcap;                  // columns room per stencil
     int stride;                // row stride of the full matrix (LU) or of the RHS block (LDL^T)
@@ -117,6 +129,8 @@ struct SolveArgs {
     int no_seed;               // fault injection: push no initial center (waits run out)
     int factor;                // RBFFD_FACTOR_LDLT (packed layout) or RBFFD_FACTOR_LU (full)
     int max_ctas;              // cap on the persistent grid (0 = fill the GPU)
+    int grid;                  // persistent grid from the occupancy (set at plan time)
+    int fb_grid;               // grid of the fallback solves
     unsigned long long timeout_ns;
     // traversal state
     int* state;
@@ -133,7 +147,9 @@ struct SolveArgs {
 };
 
 size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride_out);
-size_t basis_smem_bytes(int M, int D);
+size_t basis_smem_bytes(int count);
+int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count, int* grid,
+                          int* fb_grid);
 int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
                      cudaEvent_t ev0, cudaEvent_t ev1);
 int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches);

@@ -176,6 +176,22 @@ def jittered_grid(side: int, d: int, amp: float = 0.2, seed: int = 7,
     return np.ascontiguousarray(P)
 
 
+def mixed_degree_params(X: np.ndarray, ells=(2, 3, 4, 5)):
+    """Per-node stencil parameters for a node set split into len(ells) slabs along x (by the
+    first coordinate's range): slab s uses degree ells[s], n = 2 M + 1 with M = C(ell+d, d)
+    monomials, and PHS exponent m = 5 for ell = 2, else 7.  Returns int32 arrays (n, ell, m)."""
+    N, d = X.shape
+    x = X[:, 0]
+    lo, hi = float(x.min()), float(x.max())
+    slab = np.minimum(((x - lo) / max(hi - lo, 1e-300) * len(ells)).astype(np.int64),
+                      len(ells) - 1)
+    ell = np.asarray(ells, dtype=np.int32)[slab]
+    M = np.array([math.comb(int(l) + d, d) for l in ell], dtype=np.int32)
+    n = (2 * M + 1).astype(np.int32)
+    m = np.where(ell == 2, 5, 7).astype(np.int32)
+    return n, ell, m
+
+
 #: The workloads, by name: (generator, kwargs, d, n, ell, m, deltas).
 WORKLOADS = {
     "disk2d_N2000_l2_n12_r3": dict(gen=disk2d, kw=dict(N=2000, seed=1), d=2, n=12, ell=2, m=3,
@@ -184,6 +200,13 @@ WORKLOADS = {
                                       m=7, deltas=(1.0, 0.5, 0.3)),
     "ball3d_N100000_l3_n45_r7": dict(gen=ball3d, kw=dict(N=100000, seed=3), d=3, n=45, ell=3,
                                      m=7, deltas=(1.0, 0.4, 0.2)),
+}
+
+
+#: Mixed-degree workload: clustered unit cube, degree 2..5 by x-slab, FALLBACK stabilization.
+MIXED_WORKLOADS = {
+    "cube3d_N500000_mixed_l2to5": dict(gen=cube3d_clustered, kw=dict(N=500000, seed=4), d=3,
+                                       ells=(2, 3, 4, 5), deltas=(0.3,), mode="fallback"),
 }
 
 

@@ -38,7 +38,7 @@ class rbffd_stats_t(C.Structure):
                 ("M", C.c_int32), ("K", C.c_int32), ("d", C.c_int32), ("alg_flops", C.c_double),
                 ("n_launches", C.c_int64), ("ms_stencils", C.c_float),
                 ("ms_traversal", C.c_float), ("ms_fallback", C.c_float),
-                ("ms_finalize", C.c_float), ("plan_bytes", C.c_int64),
+                ("ms_finalize", C.c_float), ("nnz", C.c_int64), ("plan_bytes", C.c_int64),
                 ("assemble_bytes", C.c_int64)]
 
     def as_dict(self):
@@ -52,6 +52,9 @@ _SIGS = {
     "rbffd_plan": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
                              C.c_double, C.POINTER(rbffd_opts), C.c_void_p,
                              C.POINTER(C.c_void_p)]),
+    "rbffd_plan_mixed": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_double, C.POINTER(rbffd_opts), C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
     "rbffd_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(rbffd_csr)]),
     "rbffd_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_stats": (C.c_int, [C.c_void_p, C.POINTER(rbffd_stats_t)]),
@@ -105,6 +108,14 @@ def rbffd_plan(nodes_ptr, N, d, n, ell, m, delta, opts=None, stream=None):
     out = C.c_void_p()
     rc = load().rbffd_plan(nodes_ptr, N, d, n, ell, m, float(delta),
                            C.byref(opts) if opts is not None else None, stream, C.byref(out))
+    return rc, out
+
+
+def rbffd_plan_mixed(nodes_ptr, N, d, n_node, ell_node, m_node, delta, opts=None, stream=None):
+    out = C.c_void_p()
+    rc = load().rbffd_plan_mixed(nodes_ptr, N, d, _p(n_node), _p(ell_node), _p(m_node),
+                                 float(delta), C.byref(opts) if opts is not None else None,
+                                 stream, C.byref(out))
     return rc, out
 
 
@@ -179,18 +190,43 @@ class Plan:
             self._nodes = nodes.contiguous()
             on_host = 0
         self.N, self.d = self._nodes.shape
-        self.n, self.ell, self.m, self.delta, self.mode = n, ell, m, delta, mode
+        self.ell, self.m, self.delta, self.mode = ell, m, delta, mode
+        self.sync = bool(sync)
         opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor,
                           max_ctas)
-        rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
-                              _stream_handle(stream))
-        _check(rc, "rbffd_plan")
+        if np.ndim(n) == 0:  # one stencil size, degree and exponent for every node
+            self.n = int(n)
+            rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
+                                  _stream_handle(stream))
+            _check(rc, "rbffd_plan")
+        else:                # per-node arrays
+            self._node_params = [np.ascontiguousarray(v, dtype=np.int32) for v in (n, ell, m)]
+            self.n = int(self._node_params[0].max())
+            rc, plan = rbffd_plan_mixed(_p(self._nodes), self.N, self.d, *self._node_params,
+                                        delta, opts, _stream_handle(stream))
+            _check(rc, "rbffd_plan_mixed")
         self._plan = plan
 
     def assemble(self):
         rc, csr = rbffd_assemble(self._plan, _stream_handle(self._stream))
         _check(rc, "rbffd_assemble")
         return csr
+
+    def capture_assemble(self, stream=None):
+        """Record one rbffd_assemble into a CUDA graph (torch.cuda.CUDAGraph); each replay()
+        forms L again on the device with no host work.  The plan must be asynchronous
+        (sync=False) and assembled once before capture, so the graph allocates nothing."""
+        import torch
+        if self.sync:
+            raise ValueError("capture needs a plan created with sync=False")
+        g = torch.cuda.CUDAGraph()
+        s = stream if stream is not None else torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.graph(g, stream=s):
+            rc, _ = rbffd_assemble(self._plan, C.c_void_p(s.cuda_stream))
+        _check(rc, "rbffd_assemble (capture)")
+        self._stream = s
+        return g
 
     def apply(self, u, y):
         _check(rbffd_apply(self._plan, _p(u), _p(y), _stream_handle(self._stream)),
@@ -202,10 +238,11 @@ class Plan:
         return st.as_dict()
 
     def export(self):
-        N, n = self.N, self.n
+        N = self.N
+        nnz = self.stats()["nnz"]
         row_ptr = np.zeros(N + 1, np.int64)
-        col = np.zeros(N * n, np.int32)
-        val = np.zeros(N * n, np.float64)
+        col = np.zeros(nnz, np.int32)
+        val = np.zeros(nnz, np.float64)
         owner = np.zeros(N, np.int32)
         _check(rbffd_export(self._plan, row_ptr, col, val, owner), "rbffd_export")
         return row_ptr, col, val, owner

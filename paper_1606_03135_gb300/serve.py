@@ -182,6 +182,7 @@ class Server:
             "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_latency_s": float(np.percentile(lat, 99)) if lat.size else None,
             "peak_reserved_bytes": self.budget.peak, "slots": self.slots,
+            "errors": [f"job {r.rid} (N={r.rows}): {r.error}" for r in out if r.error][:5],
         }
         return out, summary
 

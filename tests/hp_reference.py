@@ -52,3 +52,37 @@ def mp_weights(X, idx, ell, m, Y, dps=40):
     return np.array(out).T
 
 
+
+
+def lapack_weights(X, idx, ell, m, y):
+    """Laplacian weights of stencil X[idx] (center idx[0]) at point y from an independent
+    FP64 solve: the local system of §4.1 built with numpy in scaled local coordinates and
+    solved by LAPACK (numpy.linalg.solve).  Used to measure how far two correct FP64 solvers
+    drift apart on an ill-conditioned stencil."""
+    d = X.shape[1]
+    c = X[idx[0]]
+    rho = np.sqrt(((X[idx] - c) ** 2).sum(1).max())
+    xi = (X[idx] - c) / rho
+    eta = (y - c) / rho
+    ex = [a for g in range(ell + 1) for a in itertools.product(range(g + 1), repeat=d)
+          if sum(a) == g]
+    n, M = len(idx), len(ex)
+    K = n + M
+    R = np.sqrt(((xi[:, None] - xi[None]) ** 2).sum(-1))
+    A = np.zeros((K, K))
+    A[:n, :n] = R ** m
+    P = np.stack([np.prod(xi ** np.array(e), axis=1) for e in ex], 1)
+    A[:n, n:] = P
+    A[n:, :n] = P.T
+    b = np.zeros(K)
+    rr = np.sqrt(((xi - eta) ** 2).sum(-1))
+    b[:n] = m * (m + d - 2) * rr ** (m - 2)
+    for l, e in enumerate(ex):
+        v = 0.0
+        for a in range(d):
+            if e[a] >= 2:
+                ee = list(e)
+                ee[a] -= 2
+                v += e[a] * (e[a] - 1) * np.prod(eta ** np.array(ee))
+        b[n + l] = v
+    return np.linalg.solve(A, b)[:n] / rho ** 2

@@ -330,3 +330,53 @@ def test_laplacian_converges_3d():
         errs.append(_interior_error(X, r, f, lapf, 0.25))
     order = math.log2(errs[0] / errs[1])
     assert order > 1.5, (errs, order)  # ell = 3: expected order about 2
+
+
+# ------------------------------------------------------------------ mixed stencils
+def test_mixed_oracle_with_uniform_parameters_is_the_uniform_oracle():
+    X = NS.disk2d(700, seed=17)
+    N = X.shape[0]
+    for delta, mode in ((0.5, O.STAB_SEQ), (0.3, O.STAB_FALLBACK), (1.0, O.STAB_SEQ)):
+        a = O.assemble(X, 12, 2, 3, delta, mode)
+        b = O.assemble_mixed(X, np.full(N, 12), np.full(N, 2), np.full(N, 3), delta, mode)
+        for key in ("row_ptr", "col", "val", "owner", "is_center", "lam_row"):
+            assert np.array_equal(a[key], b[key]), key
+
+
+def test_mixed_traversal_satisfies_its_characterisation():
+    X = NS.cube3d_clustered(900, seed=4)
+    N = X.shape[0]
+    ell = np.where(X[:, 0] < 0.5, 2, 3).astype(np.int32)
+    n_node = np.array([2 * math.comb(int(l) + 3, 3) + 1 for l in ell], dtype=np.int32)
+    m_node = np.where(ell == 2, 5, 7).astype(np.int32)
+    delta = 0.4
+    r = O.assemble_mixed(X, n_node, ell, m_node, delta)
+    nbr, d2 = r["nbr"], r["d2"]
+    f = (1 - delta) * (1 - delta)
+    bl = [int((d2[k, :n_node[k]] <= f * d2[k, n_node[k] - 1]).sum()) for k in range(N)]
+    centers = np.flatnonzero(r["is_center"] == 1)
+    acc = {}
+    for j in centers:
+        idx = nbr[j, :n_node[j]]
+        W, lam = O.local_weights(X, idx, int(ell[j]), int(m_node[j]), X[idx[:bl[j]]])
+        acc[j] = (W, lam <= lam[0])
+    first = np.full(N, -1)
+    for j in centers:
+        for t in range(bl[j]):
+            i = nbr[j, t]
+            if i >= j and acc[j][1][t] and first[i] < 0:
+                first[i] = j
+    for k in range(N):
+        earlier = [j for j in centers if j < k and k in nbr[j, :bl[j]]
+                   and acc[j][1][int(np.flatnonzero(nbr[j, :bl[j]] == k)[0])]]
+        assert (r["is_center"][k] == 1) == (len(earlier) == 0)
+    for i in range(N):
+        j = first[i]
+        assert r["owner"][i] == j
+        t = int(np.flatnonzero(nbr[j, :n_node[j]] == i)[0])
+        cols = nbr[j, :n_node[j]]
+        o = np.argsort(cols)
+        sl = slice(r["row_ptr"][i], r["row_ptr"][i + 1])
+        assert r["row_ptr"][i + 1] - r["row_ptr"][i] == n_node[j]
+        assert np.array_equal(r["col"][sl], cols[o])
+        assert np.array_equal(r["val"][sl], acc[j][0][o, t])
