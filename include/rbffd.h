@@ -62,6 +62,9 @@ typedef struct {
     int factor;         /* RBFFD_FACTOR_LDLT (default) or RBFFD_FACTOR_LU */
     int max_ctas;       /* cap on the persistent traversal grid, so that plans assembled
                            concurrently on several streams share the GPU; 0 = fill the GPU */
+    int team;           /* threads per stencil team: 0 = chosen from the shared-memory
+                           footprint (128 when several stencils fit an SM, else 512), or
+                           128 / 512 to force one (used by the schedule autotuner) */
 } rbffd_opts;
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */

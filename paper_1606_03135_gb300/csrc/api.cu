@@ -44,7 +44,8 @@ struct rbffd_plan_s {
     void* asm_block = nullptr;     // one allocation for the traversal and CSR arrays
     int max_ball = 0;
     long long total_slots = 0;
-    int qcap = 0, stride = 0, grid = 0, fb_grid = 0;
+    int qcap = 0, stride = 0;
+    LaunchPlan lp;
     // traversal and results
     bool have_asm = false, assembled = false;
     int* state = nullptr;
@@ -303,10 +304,11 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
             K_max = nk + Mk > K_max ? nk + Mk : K_max;
         }
     }
-    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0};
+    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0};
     if (opts) o = *opts;
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
-        (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0)
+        (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0 ||
+        (o.team != 0 && o.team != 128 && o.team != 512))
         return RBFFD_EINVAL;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
 
@@ -423,8 +425,27 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         const size_t avail = (size_t)max_optin_smem() - 64;
         p->stride = stride;
         if (per_cta > avail) { rc = RBFFD_EINVAL; goto fail; }
+        // fallback classes: one per degree in use (per-node stencils) or one for all nodes
+        if (!mixed) {
+            p->lp.n_fb = 1;
+            p->lp.fb[0].cls = -1;
+            p->lp.fb[0].n = n;
+            p->lp.fb[0].K = p->K;
+        } else {
+            int nmax_of[kMaxEll + 1] = {};
+            for (int64_t k = 0; k < N; ++k)
+                nmax_of[ell_node[k]] = n_node[k] > nmax_of[ell_node[k]] ? n_node[k] : nmax_of[ell_node[k]];
+            for (int l = 0; l <= kMaxEll; ++l)
+                if (nmax_of[l] > 0) {
+                    FallbackClass& f = p->lp.fb[p->lp.n_fb++];
+                    f.cls = l;
+                    f.n = nmax_of[l];
+                    f.K = nmax_of[l] + p->Mof[l];
+                }
+        }
+        p->lp.force_nt = o.team;
         rc = prepare_solve_kernels(d, o.factor == RBFFD_FACTOR_LDLT, n, p->K, p->qcap,
-                                   (int)basis_count, &p->grid, &p->fb_grid);
+                                   (int)basis_count, &p->lp);
         if (rc) goto fail;
     }
     *out = p;
@@ -498,14 +519,13 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.no_seed = p->opts.fault_inject == 1;
     a.factor = p->opts.factor;
     a.max_ctas = p->opts.max_ctas;
-    a.grid = p->grid;
-    a.fb_grid = p->fb_grid;
+
     if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
-    rc = launch_traversal(p->d, a, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
+    rc = launch_traversal(p->d, a, p->lp, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
     if (rc) return rc;
     cudaEventRecord(p->ev[4], s);
     if (p->opts.stab_mode == RBFFD_STAB_FALLBACK) {
-        rc = launch_fallback(p->d, a, s, &p->launches);
+        rc = launch_fallback(p->d, a, p->lp, s, &p->launches);
         if (rc) return rc;
     }
     cudaEventRecord(p->ev[5], s);

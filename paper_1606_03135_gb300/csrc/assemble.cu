@@ -27,7 +27,10 @@
 
 namespace rbffd {
 
-constexpr int kNT = 128;  // threads per stencil team: one warp per SM sub-partition
+constexpr int kNT = 128;     // smallest stencil team: one warp per SM sub-partition
+constexpr int kMaxNT = 512;  // largest team (big systems, when few fit in shared memory)
+// Device code is compiled for a team size NT of 128 (small systems, many per SM) or 512
+// (large systems, one or a few per SM); the host picks the instantiation per launch.
 
 // Per-CTA shared-memory views of one local system.  Two layouts:
 //   full   (LU):     A is K x S row-major holding [A_hat | B_hat]; X = A + K, xs = S
@@ -156,7 +159,7 @@ __device__ __forceinline__ const short* load_basis(char* smem, const short* g, i
 // Assemble the local system of stencil j (§4.1) and its q right-hand sides (the columns in
 // sm.cols) in shared memory, with the whole CTA.  Full layout: both triangles of A_hat and
 // B_hat beside it.  Packed layout: the lower triangle of A_hat and B_hat apart.
-template <int D, bool PACKED>
+template <int D, bool PACKED, int NT>
 __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q,
                                const StencilSmem& sm) {
     const int tid = threadIdx.x;
@@ -168,20 +171,20 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
     if (!(r2c > 0.0)) r2c = 1.0;
     const double rho = sqrt(r2c);
     const double* xc = a.X + (size_t)j * D;
-    for (int t = tid; t < n; t += kNT) {
+    for (int t = tid; t < n; t += NT) {
         const int id = a.nbr[(size_t)j * a.n + t];
         for (int c = 0; c < D; ++c)
             sm.xi[t * D + c] = __ddiv_rn(__dsub_rn(a.X[(size_t)id * D + c], xc[c]), rho);
     }
     if (PACKED) {
-        for (int e = tid; e < tri(K); e += kNT) sm.T[e] = 0.0;
-        for (int e = tid; e < K * q; e += kNT) {
+        for (int e = tid; e < tri(K); e += NT) sm.T[e] = 0.0;
+        for (int e = tid; e < K * q; e += NT) {
             const int r = e / q, c = e - r * q;
             X[r * xs + c] = 0.0;
         }
     } else {
         const int Wd = K + q, S = xs;
-        for (int e = tid; e < K * Wd; e += kNT) {
+        for (int e = tid; e < K * Wd; e += NT) {
             const int r = e / Wd, c = e - r * Wd;
             sm.A[r * S + c] = 0.0;
         }
@@ -195,8 +198,8 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
         const int rows = n - 1, L2 = n;
         const int total = ((rows + 1) >> 1) * L2;
         int pr = tid / L2, off = tid - (tid / L2) * L2;
-        const int di = kNT / L2, dj = kNT - di * L2;
-        for (int e = tid; e < total; e += kNT) {
+        const int di = NT / L2, dj = NT - di * L2;
+        for (int e = tid; e < total; e += NT) {
             const int len0 = rows - pr;
             const bool first = off < len0;
             const int ra = first ? pr : rows - 1 - pr;
@@ -224,7 +227,7 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
         }
     }
     // P: one stencil point per thread, each monomial = an earlier one times one coordinate
-    for (int r = tid; r < n; r += kNT) {
+    for (int r = tid; r < n; r += NT) {
         if (PACKED) {
             sm.T[tri(n) + r] = 1.0;
             for (int l = 1; l < M; ++l)
@@ -243,7 +246,7 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
     __syncthreads();
     // psi-part of the right-hand sides: Laplacian of each monomial at each solved member,
     // from the monomial values already computed for that member
-    for (int e = tid; e < M * q; e += kNT) {
+    for (int e = tid; e < M * q; e += NT) {
         const int l = e / q, c = e - l * q;
         const int t = sm.cols[c];
         double s = 0.0;
@@ -311,12 +314,13 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 // LU with partial pivoting of [A_hat | B_hat] in the full layout (the paper's decomposition,
 // §4.3 cost model (2/3) K^3 + 2 K^2 q), then back substitution.  Returns false (uniformly)
 // on an exactly zero pivot; on success row r of the right-hand-side block holds unknown r.
+template <int NT>
 __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
     __shared__ int s_ok;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int S = sm.xs;
     const int Wd = K + q;
-    for (int r = tid; r < K; r += kNT) sm.rowof[r] = r;
+    for (int r = tid; r < K; r += NT) sm.rowof[r] = r;
     // the pivot search, row swap, reciprocal and multipliers are done by warp 0 alone (FP64
     // work counts per warp instruction, so the other warps must not repeat it)
     for (int p = 0; p < K; ++p) {
@@ -354,11 +358,11 @@ __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
         const int total = wr * wc;
         if (tid < total) {
             int ii = tid / wc, jj = tid - (tid / wc) * wc;
-            const int di = kNT / wc, dj = kNT - di * wc;
+            const int di = NT / wc, dj = NT - di * wc;
             const double* Ap = sm.A + p * S + p + 1;
             double* Ab = sm.A + (p + 1) * S;
 #pragma unroll 4
-            for (int e = tid; e < total; e += kNT) {
+            for (int e = tid; e < total; e += NT) {
                 double* row = Ab + ii * S;
                 row[p + 1 + jj] = fma(-row[p], Ap[jj], row[p + 1 + jj]);
                 ii += di;
@@ -375,10 +379,10 @@ __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
         const int total = p * q;
         if (tid < total) {
             int ii = tid / q, jj = tid - (tid / q) * q;
-            const int di = kNT / q, dj = kNT - di * q;
+            const int di = NT / q, dj = NT - di * q;
             const double* xp = sm.A + p * S + K;
 #pragma unroll 4
-            for (int e = tid; e < total; e += kNT) {
+            for (int e = tid; e < total; e += NT) {
                 double* row = sm.A + ii * S;
                 row[K + jj] = fma(-row[p], xp[jj], row[K + jj]);
                 ii += di;
@@ -398,13 +402,14 @@ __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
 // and 2x2 pivots with alpha = (1 + sqrt(17)) / 8; symmetric swaps are tracked in sm.perm.
 // Returns false (uniformly) on an exactly singular pivot column.  On success sm.rowof[u] is
 // the row of the right-hand-side block that holds unknown u.
+template <int NT>
 __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
     __shared__ int s_ok, s_kind;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int xs = sm.xs;
     double* T = sm.T;
     double* X = sm.X;
-    for (int r = tid; r < K; r += kNT) sm.perm[r] = r;
+    for (int r = tid; r < K; r += NT) sm.perm[r] = r;
     __syncthreads();
     int p = 0;
     while (p < K) {
@@ -513,8 +518,8 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
             const int total = ((rows + 1) >> 1) * L2;
             if (tid < total) {
                 int pr = tid / L2, off = tid - (tid / L2) * L2;
-                const int di = kNT / L2, dj = kNT - di * L2;
-                for (int e = tid; e < total; e += kNT) {
+                const int di = NT / L2, dj = NT - di * L2;
+                for (int e = tid; e < total; e += NT) {
                     const int len0 = pr + 1 + q;
                     const bool first = off < len0;
                     const int r = first ? pr : rows - 1 - pr;
@@ -544,7 +549,7 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
         p += kind;
     }
     // D solve: 1x1 rows scale by the reciprocal pivot, 2x2 blocks multiply by their inverse
-    for (int e = tid; e < K * q; e += kNT) {
+    for (int e = tid; e < K * q; e += NT) {
         const int i = e / q, c = e - (e / q) * q;
         const int k = sm.pk[i];
         double* Bi = X + i * xs + c;
@@ -563,11 +568,11 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
         const int total = i * q;
         if (tid < total) {
             int jj = tid / q, cc = tid - (tid / q) * q;
-            const int dj = kNT / q, dc = kNT - dj * q;
+            const int dj = NT / q, dc = NT - dj * q;
             const double* Li = T + tri(i);
             const double* xi = X + i * xs;
 #pragma unroll 4
-            for (int e = tid; e < total; e += kNT) {
+            for (int e = tid; e < total; e += NT) {
                 double* xj = X + jj * xs;
                 xj[cc] = fma(-Li[jj], xi[cc], xj[cc]);
                 jj += dj;
@@ -577,22 +582,23 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
         }
         __syncthreads();
     }
-    for (int r = tid; r < K; r += kNT) sm.rowof[sm.perm[r]] = r;
+    for (int r = tid; r < K; r += NT) sm.rowof[sm.perm[r]] = r;
     __syncthreads();
     return true;
 }
 
-template <int D, bool PACKED>
+template <int D, bool PACKED, int NT>
 __device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
                             const StencilSmem& sm) {
-    assemble_local<D, PACKED>(a, sh, j, q, sm);
-    return PACKED ? factor_solve_ldlt(sh.K, q, sm) : factor_solve_lu(sh.K, q, sm);
+    assemble_local<D, PACKED, NT>(a, sh, j, q, sm);
+    return PACKED ? factor_solve_ldlt<NT>(sh.K, q, sm) : factor_solve_lu<NT>(sh.K, q, sm);
 }
 
 // Local L-Lebesgue value sum_r |w_r| of every solved column (one warp per column).
+template <int NT>
 __device__ __forceinline__ void lebesgue_values(int n, int q, const StencilSmem& sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int c = wid; c < q; c += kNT / 32) {
+    for (int c = wid; c < q; c += (NT / 32)) {
         double s = 0.0;
         for (int r = lane; r < n; r += 32) s += fabs(sm.X[sm.rowof[r] * sm.xs + c]);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -654,8 +660,10 @@ __global__ void k_traversal_seed(SolveArgs a, const int* __restrict__ indeg) {
 // One CTA per center.  Thread 0 claims the next queue slot and waits (bounded) for it to be
 // filled; the CTA then solves the center, tests and writes its columns, and resolves the
 // traversal state of its ball members.
-template <int D, bool PACKED>
-__global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
+// 128-thread teams are capped at 40 registers so that 12 CTAs (the shared-memory limit of the
+// 2D workload) fit an SM.
+template <int D, bool PACKED, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_j, s_q;
     const short* sbasis = load_basis(smem, a.basis, a.basis_count);
@@ -724,10 +732,10 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
         }
         __syncthreads();
         const int q = s_q;
-        const bool ok = solve_local<D, PACKED>(a, sh, j, q, sm);
-        if (ok) lebesgue_values(n, q, sm);
+        const bool ok = solve_local<D, PACKED, NT>(a, sh, j, q, sm);
+        if (ok) lebesgue_values<NT>(n, q, sm);
         __syncthreads();
-        // Lebesgue test (§4.2.1) per column; q <= n <= kNT, so one thread per column
+        // Lebesgue test (§4.2.1) per column; q <= n <= 128 <= NT, so one thread per column
         const long long base = a.slot_off[j];
         bool failed = false, own = false;
         if (tid < q) {
@@ -749,7 +757,7 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
         double r2c = a.rho2[j];
         if (!(r2c > 0.0)) r2c = 1.0;
         const double inv_r2 = 1.0 / r2c;
-        for (int e = tid; e < q * n; e += kNT) {
+        for (int e = tid; e < q * n; e += NT) {
             const int c = e / n, r = e - c * n;
             if (!sm.keep[c]) continue;
             a.slot_w[(base + sm.cols[c]) * ns + r] =
@@ -763,7 +771,7 @@ __global__ void __launch_bounds__(kNT) k_traversal(SolveArgs a, size_t per_cta, 
         __threadfence();
         __syncthreads();
         // resolve: kept members become covered; every later ball member loses a dependency
-        for (int t = 1 + tid; t < L; t += kNT) {
+        for (int t = 1 + tid; t < L; t += NT) {
             const int i = a.nbr[(size_t)j * ns + t];
             if (i <= j) continue;
             const int c = sm.colof[t];
@@ -806,12 +814,17 @@ __global__ void k_fallback_collect(SolveArgs a) {
     }
 }
 
-template <int D, bool PACKED>
-__global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_cta, int basis_bytes) {
+// FALLBACK re-solves (one right-hand side each), one launch per stencil class: `cls` is the
+// degree this launch handles (-1: all), n_cls/K_cls the largest stencil/system of the class,
+// so shared memory is sized for the class and a single column.
+template <int D, bool PACKED, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_fallback_solve(SolveArgs a, int cls, int n_cls,
+                                                           int K_cls, int xs_cls,
+                                                           int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
     const short* sbasis = load_basis(smem, a.basis, a.basis_count);
     StencilSmem sm;
-    carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
+    carve<D, PACKED>(smem + basis_bytes, n_cls, K_cls, 1, xs_cls, sm);
     __syncthreads();
     const int tid = threadIdx.x;
     const int count = *((volatile int*)&a.ctr->fb_count);
@@ -819,18 +832,19 @@ __global__ void __launch_bounds__(kNT) k_fallback_solve(SolveArgs a, size_t per_
     const double c3 = PACKED ? 1.0 / 3.0 : 2.0 / 3.0;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int i = a.fb_list[w];
+        if (cls >= 0 && (int)a.node_ell[i] != cls) continue;  // another class's launch
         const Shape sh = shape_of<D>(a, sbasis, i);
-        for (int t = tid; t < sh.n; t += kNT) sm.colof[t] = (t == 0) ? 0 : -1;
+        for (int t = tid; t < sh.n; t += NT) sm.colof[t] = (t == 0) ? 0 : -1;
         if (tid == 0) sm.cols[0] = 0;
         __syncthreads();
-        const bool ok = solve_local<D, PACKED>(a, sh, i, 1, sm);
-        if (ok) lebesgue_values(sh.n, 1, sm);
+        const bool ok = solve_local<D, PACKED, NT>(a, sh, i, 1, sm);
+        if (ok) lebesgue_values<NT>(sh.n, 1, sm);
         __syncthreads();
         double r2c = a.rho2[i];
         if (!(r2c > 0.0)) r2c = 1.0;
         const double inv_r2 = 1.0 / r2c;
         const long long slot = a.slot_off[i];
-        for (int r = tid; r < sh.n; r += kNT)
+        for (int r = tid; r < sh.n; r += NT)
             a.slot_w[slot * a.n + r] = ok ? sm.X[sm.rowof[r] * sm.xs] * inv_r2 : nan;
         if (tid == 0) {
             a.slot_lam[slot] = ok ? sm.lam[0] : nan;
@@ -954,91 +968,126 @@ static cudaError_t allow_max_smem(const void* kern) {
                                 mx - (int)fa.sharedSizeBytes);
 }
 
-// Host-side preparation, done once per plan (not per assembly, so that rbffd_assemble only
-// enqueues stream work and can be captured in a CUDA graph): raise the kernels' shared-memory
-// limit and size the persistent grid from the occupancy.
-template <int D, bool PACKED>
-static int prepare(int n, int K, int qcap, int basis_count, int* grid, int* fb_grid) {
-    int stride = 0;
-    const size_t smem =
-        basis_smem_bytes(basis_count) + solve_smem_per_cta(n, K, qcap, D, PACKED, &stride);
-    auto kt = k_traversal<D, PACKED>;
-    auto kf = k_fallback_solve<D, PACKED>;
-    if (RB_CUDA(allow_max_smem((const void*)kt)) || RB_CUDA(allow_max_smem((const void*)kf)))
+// Team size for a launch: 128 threads when several stencils fit an SM's shared memory,
+// else 512 so that the one or few resident stencils still keep enough warps busy.
+template <typename K128, typename K512>
+static int pick_team(K128 k128, K512 k512, size_t smem, int* nt_out, int* per_sm_out,
+                     int force = 0) {
+    int per_sm = 0;
+    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k128, kNT, smem)) ||
+        per_sm < 1)
         return RBFFD_EINVAL;
-    int per_sm = 0, per_sm_f = 0;
-    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kt, kNT, smem)) ||
-        RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, kf, kNT, smem)) ||
-        per_sm < 1 || per_sm_f < 1)
-        return RBFFD_EINVAL;
-    *grid = per_sm * sm_count();
-    *fb_grid = per_sm_f * sm_count();
+    if (force == kMaxNT || (force == 0 && per_sm <= 4)) {
+        int p512 = 0;
+        if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p512, k512, kMaxNT, smem)) ||
+            p512 < 1)
+            return RBFFD_EINVAL;
+        *nt_out = kMaxNT;
+        *per_sm_out = p512;
+        return RBFFD_OK;
+    }
+    *nt_out = kNT;
+    *per_sm_out = per_sm;
     return RBFFD_OK;
 }
 
-int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count, int* grid,
-                          int* fb_grid) {
+// Host-side preparation, done once per plan (not per assembly, so that rbffd_assemble only
+// enqueues stream work and can be captured in a CUDA graph): raise the kernels' shared-memory
+// limit, choose team sizes and size the persistent grid from the occupancy.  fb[c] holds the
+// fallback launch of stencil class c.
+template <int D, bool PACKED>
+static int prepare(int n, int K, int qcap, int basis_count, LaunchPlan* lp) {
+    int stride = 0;
+    const size_t bb = basis_smem_bytes(basis_count);
+    const size_t smem = bb + solve_smem_per_cta(n, K, qcap, D, PACKED, &stride);
+    auto kt1 = k_traversal<D, PACKED, kNT>;
+    auto kt5 = k_traversal<D, PACKED, kMaxNT>;
+    auto kf1 = k_fallback_solve<D, PACKED, kNT>;
+    auto kf5 = k_fallback_solve<D, PACKED, kMaxNT>;
+    if (RB_CUDA(allow_max_smem((const void*)kt1)) || RB_CUDA(allow_max_smem((const void*)kt5)) ||
+        RB_CUDA(allow_max_smem((const void*)kf1)) || RB_CUDA(allow_max_smem((const void*)kf5)))
+        return RBFFD_EINVAL;
+    int per_sm = 0, rc;
+    if ((rc = pick_team(kt1, kt5, smem, &lp->nt, &per_sm, lp->force_nt))) return rc;
+    lp->grid = per_sm * sm_count();
+    lp->smem = smem;
+    for (int c = 0; c < lp->n_fb; ++c) {
+        FallbackClass& f = lp->fb[c];
+        const size_t fs = bb + solve_smem_per_cta(f.n, f.K, 1, D, PACKED, &f.xs);
+        if ((rc = pick_team(kf1, kf5, fs, &f.nt, &per_sm))) return rc;
+        f.grid = per_sm * sm_count();
+        f.smem = fs;
+    }
+    return RBFFD_OK;
+}
+
+int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count,
+                          LaunchPlan* lp) {
     if (D == 2)
-        return packed ? prepare<2, true>(n, K, qcap, basis_count, grid, fb_grid)
-                      : prepare<2, false>(n, K, qcap, basis_count, grid, fb_grid);
-    return packed ? prepare<3, true>(n, K, qcap, basis_count, grid, fb_grid)
-                  : prepare<3, false>(n, K, qcap, basis_count, grid, fb_grid);
+        return packed ? prepare<2, true>(n, K, qcap, basis_count, lp)
+                      : prepare<2, false>(n, K, qcap, basis_count, lp);
+    return packed ? prepare<3, true>(n, K, qcap, basis_count, lp)
+                  : prepare<3, false>(n, K, qcap, basis_count, lp);
 }
 
 template <int D, bool PACKED>
-static int traversal(const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
-                     cudaEvent_t ev0, cudaEvent_t ev1) {
-    int stride = 0;
-    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, PACKED, &stride);
+static int traversal(const SolveArgs& a, const LaunchPlan& lp, const int* indeg, cudaStream_t s,
+                     int* launches, cudaEvent_t ev0, cudaEvent_t ev1) {
     const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
-    const size_t smem = basis_bytes + per_cta;
-    auto kern = k_traversal<D, PACKED>;
     const int tb = 256, nb = (a.N + tb - 1) / tb;
     k_traversal_init<<<nb, tb, 0, s>>>(a.N, indeg, a.state, a.pending, a.owner, a.queue,
                                        a.fb_flag);
     k_traversal_seed<<<nb, tb, 0, s>>>(a, indeg);
     *launches += 2;
-    int grid = min(a.grid, a.N);
+    int grid = min(lp.grid, a.N);
     if (a.max_ctas > 0) grid = min(grid, a.max_ctas);
     // A plain launch suffices: a worker only waits for queue entries that workers already
     // running will push (the smallest unresolved node is always ready once every center
     // that holds a claimed entry is solved), so progress needs no co-residency, and plans
     // on other streams can run beside this grid.
     if (ev0) cudaEventRecord(ev0, s);
-    kern<<<grid, kNT, smem, s>>>(a, per_cta, basis_bytes);
+    if (lp.nt == kMaxNT)
+        k_traversal<D, PACKED, kMaxNT><<<grid, kMaxNT, lp.smem, s>>>(a, lp.smem - basis_bytes, basis_bytes);
+    else
+        k_traversal<D, PACKED, kNT><<<grid, kNT, lp.smem, s>>>(a, lp.smem - basis_bytes, basis_bytes);
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
     return RB_LAUNCHED(__func__);
 }
 
-int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
-                     cudaEvent_t ev0, cudaEvent_t ev1) {
+int launch_traversal(int D, const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
+                     cudaStream_t s, int* launches, cudaEvent_t ev0, cudaEvent_t ev1) {
     const bool packed = a.factor == RBFFD_FACTOR_LDLT;
     if (D == 2)
-        return packed ? traversal<2, true>(a, indeg, s, launches, ev0, ev1)
-                      : traversal<2, false>(a, indeg, s, launches, ev0, ev1);
-    return packed ? traversal<3, true>(a, indeg, s, launches, ev0, ev1)
-                  : traversal<3, false>(a, indeg, s, launches, ev0, ev1);
+        return packed ? traversal<2, true>(a, lp, indeg, s, launches, ev0, ev1)
+                      : traversal<2, false>(a, lp, indeg, s, launches, ev0, ev1);
+    return packed ? traversal<3, true>(a, lp, indeg, s, launches, ev0, ev1)
+                  : traversal<3, false>(a, lp, indeg, s, launches, ev0, ev1);
 }
 
 template <int D, bool PACKED>
-static int fallback(const SolveArgs& a, cudaStream_t s, int* launches) {
+static int fallback(const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s, int* launches) {
     const int tb = 256, nb = (a.N + tb - 1) / tb;
     k_fallback_collect<<<nb, tb, 0, s>>>(a);
-    int stride = 0;
-    const size_t per_cta = solve_smem_per_cta(a.n, a.K, a.qcap, D, PACKED, &stride);
+    ++*launches;
     const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
-    const size_t smem = basis_bytes + per_cta;
-    auto kern = k_fallback_solve<D, PACKED>;
-    kern<<<a.fb_grid, kNT, smem, s>>>(a, per_cta, basis_bytes);
-    *launches += 2;
+    for (int c = 0; c < lp.n_fb; ++c) {
+        const FallbackClass& f = lp.fb[c];
+        if (f.nt == kMaxNT)
+            k_fallback_solve<D, PACKED, kMaxNT><<<f.grid, kMaxNT, f.smem, s>>>(a, f.cls, f.n, f.K, f.xs, basis_bytes);
+        else
+            k_fallback_solve<D, PACKED, kNT><<<f.grid, kNT, f.smem, s>>>(a, f.cls, f.n, f.K, f.xs, basis_bytes);
+        ++*launches;
+    }
     return RB_LAUNCHED(__func__);
 }
 
-int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches) {
+int launch_fallback(int D, const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s,
+                    int* launches) {
     const bool packed = a.factor == RBFFD_FACTOR_LDLT;
-    if (D == 2) return packed ? fallback<2, true>(a, s, launches) : fallback<2, false>(a, s, launches);
-    return packed ? fallback<3, true>(a, s, launches) : fallback<3, false>(a, s, launches);
+    if (D == 2)
+        return packed ? fallback<2, true>(a, lp, s, launches) : fallback<2, false>(a, lp, s, launches);
+    return packed ? fallback<3, true>(a, lp, s, launches) : fallback<3, false>(a, lp, s, launches);
 }
 
 int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* val,

@@ -129,8 +129,7 @@ struct SolveArgs {
     int no_seed;               // fault injection: push no initial center (waits run out)
     int factor;                // RBFFD_FACTOR_LDLT (packed layout) or RBFFD_FACTOR_LU (full)
     int max_ctas;              // cap on the persistent grid (0 = fill the GPU)
-    int grid;                  // persistent grid from the occupancy (set at plan time)
-    int fb_grid;               // grid of the fallback solves
+
     unsigned long long timeout_ns;
     // traversal state
     int* state;
@@ -148,11 +147,28 @@ struct SolveArgs {
 
 size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride_out);
 size_t basis_smem_bytes(int count);
-int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count, int* grid,
-                          int* fb_grid);
-int launch_traversal(int D, const SolveArgs& a, const int* indeg, cudaStream_t s, int* launches,
-                     cudaEvent_t ev0, cudaEvent_t ev1);
-int launch_fallback(int D, const SolveArgs& a, cudaStream_t s, int* launches);
+
+// Launch geometry decided once per plan.  Fallback re-solves run per stencil class (one
+// class per polynomial degree for per-node stencils, one class otherwise).
+struct FallbackClass {
+    int cls;        // degree handled (-1: every node)
+    int n, K, xs;   // largest stencil / system of the class, right-hand-side stride
+    int nt, grid;
+    size_t smem;
+};
+struct LaunchPlan {
+    int force_nt = 0;  // 0: choose; 128 or 512: forced team size of the traversal
+    int nt = 128, grid = 0;
+    size_t smem = 0;
+    int n_fb = 0;
+    FallbackClass fb[kMaxEll + 1];
+};
+int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count,
+                          LaunchPlan* lp);
+int launch_traversal(int D, const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
+                     cudaStream_t s, int* launches, cudaEvent_t ev0, cudaEvent_t ev1);
+int launch_fallback(int D, const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s,
+                    int* launches);
 int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* val,
                     double* lam_row, unsigned char* is_center, cudaStream_t s, int* launches);
 int launch_spmv(int N, int n, const long long* row_ptr, const int* col, const double* val,

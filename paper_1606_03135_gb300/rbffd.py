@@ -23,7 +23,7 @@ FACTOR_LDLT, FACTOR_LU = 0, 1
 class rbffd_opts(C.Structure):
     _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
                 ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int),
-                ("max_ctas", C.c_int)]
+                ("max_ctas", C.c_int), ("team", C.c_int)]
 
 
 class rbffd_csr(C.Structure):
@@ -177,7 +177,7 @@ class Plan:
     the library inside ``rbffd_plan``)."""
 
     def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
-                 stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0):
+                 stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0, team=0):
         self._plan = None
         self._stream = stream
         if isinstance(nodes, np.ndarray):
@@ -193,7 +193,7 @@ class Plan:
         self.ell, self.m, self.delta, self.mode = ell, m, delta, mode
         self.sync = bool(sync)
         opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor,
-                          max_ctas)
+                          max_ctas, team)
         if np.ndim(n) == 0:  # one stencil size, degree and exponent for every node
             self.n = int(n)
             rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
@@ -277,3 +277,34 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ------------------------------------------------------------------ schedule autotuner
+def autotune(nodes, n, ell, m, delta, mode=STAB_SEQ, candidates=None, repeats=2):
+    """Pick the traversal schedule (team size x persistent-grid cap) for a workload by timing
+    one assembly of each candidate on the device (CUDA events, after a warm-up assembly).
+    Returns (best kwargs for Plan, {candidate: ms}).  Results do not depend on the schedule
+    (the same stencils are solved the same way), only the time does."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if candidates is None:
+        candidates = [dict(team=t, max_ctas=c) for t in (0, 128, 512)
+                      for c in (0, 8 * sms, 4 * sms)]
+    timings = {}
+    for cand in candidates:
+        try:
+            with Plan(nodes, n, ell, m, delta, mode=mode, **cand) as p:
+                p.assemble()
+                best = float("inf")
+                for _ in range(repeats):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    p.assemble()
+                    e1.record()
+                    e1.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+        except RbffdError:
+            continue
+        timings[tuple(sorted(cand.items()))] = best
+    key = min(timings, key=timings.get)
+    return dict(key), timings
