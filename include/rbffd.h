@@ -64,7 +64,9 @@ typedef struct {
                            concurrently on several streams share the GPU; 0 = fill the GPU */
     int team;           /* threads per stencil team: 0 = chosen from the shared-memory
                            footprint (128 when several stencils fit an SM, else 512), or
-                           128 / 512 to force one (used by the schedule autotuner) */
+                           32 (one warp per stencil), 64, 96, 128 or 512 to force one (used
+                           by the schedule autotuner); 32, 64 and 96 need RBFFD_FACTOR_LDLT,
+                           else RBFFD_EINVAL */
 } rbffd_opts;
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */

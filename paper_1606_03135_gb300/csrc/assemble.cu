@@ -27,10 +27,17 @@
 
 namespace rbffd {
 
-constexpr int kNT = 128;     // smallest stencil team: one warp per SM sub-partition
+constexpr int kNT = 128;     // default stencil team: one warp per SM sub-partition
 constexpr int kMaxNT = 512;  // largest team (big systems, when few fit in shared memory)
 // Device code is compiled for a team size NT of 128 (small systems, many per SM) or 512
-// (large systems, one or a few per SM); the host picks the instantiation per launch.
+// (large systems, one or a few per SM); the LDL^T traversal also for 96, 64 and 32 (one warp
+// per stencil).  The host picks the instantiation per launch.
+
+// CTAs per SM the register allocation must allow for a team size (the shared-memory limit of
+// small systems): 40 registers for 96- and 128-thread teams, 64 for 32- and 64-thread teams.
+__host__ __device__ constexpr int team_min_blocks(int nt) {
+    return nt == 32 ? 32 : (nt == 64 ? 16 : (nt == 96 ? 17 : (nt == 128 ? 12 : 1)));
+}
 
 // Per-CTA shared-memory views of one local system.  Two layouts:
 //   full   (LU):     A is K x S row-major holding [A_hat | B_hat]; X = A + K, xs = S
@@ -311,6 +318,12 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 
+// Sign-free top 32 bits of an FP64 value (exponent and 20 mantissa bits): ordering these keys
+// orders the magnitudes up to a relative 2^-20, with no FP64 instruction.
+__device__ __forceinline__ unsigned mag_key(double v) {
+    return (unsigned)__double2hiint(v) & 0x7fffffffu;
+}
+
 // LU with partial pivoting of [A_hat | B_hat] in the full layout (the paper's decomposition,
 // §4.3 cost model (2/3) K^3 + 2 K^2 q), then back substitution.  Returns false (uniformly)
 // on an exactly zero pivot; on success row r of the right-hand-side block holds unknown r.
@@ -374,7 +387,7 @@ __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
     }
     // back substitution, q columns at once
     for (int p = K - 1; p >= 0; --p) {
-        if (tid < q) sm.A[p * S + K + tid] *= sm.rdiag[p];
+        for (int c = tid; c < q; c += NT) sm.A[p * S + K + c] *= sm.rdiag[p];
         __syncthreads();
         const int total = p * q;
         if (tid < total) {
@@ -414,18 +427,19 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
     int p = 0;
     while (p < K) {
         if (wid == 0) {
-            // lambda = max |A[i][p]|, i > p, lowest index on ties
-            unsigned long long lv = 0ull;
+            // lambda = max |A[i][p]|, i > p, on magnitude keys (the top 32 bits of |A[i][p]|,
+            // an order-preserving truncation), lowest index among equal keys; two warp
+            // reductions instead of a shuffle tree
+            unsigned lk = 0u;
             int r = 0x7fffffff;
             for (int i = p + 1 + lane; i < K; i += 32) {
-                const unsigned long long v = abs_bits(T[tri(i) + p]);
-                if (v > lv || (v == lv && i < r)) { lv = v; r = i; }
+                const unsigned v = mag_key(T[tri(i) + p]);
+                if (v > lk) { lk = v; r = i; }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long ov = __shfl_xor_sync(0xffffffffu, lv, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, r, o);
-                if (ov > lv || (ov == lv && oi < r)) { lv = ov; r = oi; }
-            }
+            const unsigned lmax = __reduce_max_sync(0xffffffffu, lk);
+            r = (int)__reduce_min_sync(0xffffffffu,
+                                       (lk == lmax && lmax != 0u) ? (unsigned)r : 0x7fffffffu);
+            const unsigned long long lv = (unsigned long long)lmax << 32;
             // the pivot choice only has to be a valid Bunch-Kaufman choice, so the tests run in
             // FP32 on values rebuilt from the FP64 bit patterns (no FP64 instructions)
             const unsigned long long pv = abs_bits(T[tri(p) + p]);
@@ -437,17 +451,15 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
                 ok = pv != 0ull;  // column already eliminated: 1x1 pivot if nonzero
             } else if (!(app >= af * lam)) {
                 // sigma = max |A_rj| over the active part of row/column r, j != r
-                unsigned long long sv = 0ull;
+                unsigned sk = 0u;
                 for (int jj = p + lane; jj < K; jj += 32) {
                     if (jj == r) continue;
-                    const unsigned long long b = abs_bits(jj < r ? T[tri(r) + jj] : T[tri(jj) + r]);
-                    sv = b > sv ? b : sv;
+                    const unsigned b = mag_key(jj < r ? T[tri(r) + jj] : T[tri(jj) + r]);
+                    sk = b > sk ? b : sk;
                 }
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, sv, o);
-                    sv = ov > sv ? ov : sv;
-                }
-                const float sig = approx_f32(sv), arr = approx_f32(abs_bits(T[tri(r) + r]));
+                sk = __reduce_max_sync(0xffffffffu, sk);
+                const float sig = approx_f32((unsigned long long)sk << 32),
+                            arr = approx_f32(abs_bits(T[tri(r) + r]));
                 if (app * sig >= af * lam * lam) {
                     kind = 1;
                 } else if (arr >= af * sig) {
@@ -607,8 +619,13 @@ __device__ __forceinline__ void lebesgue_values(int n, int q, const StencilSmem&
 }
 
 // ------------------------------------------------------------------ traversal state machine
+// Acquire-release fence at device scope: orders this thread's earlier memory operations, and
+// those of its CTA that a barrier made visible to it, before its later ones, as seen by every
+// thread of the device.  Only threads that publish (or consume) traversal state execute it.
+__device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void push_center(const SolveArgs& a, int k) {
-    __threadfence();
+    fence_gpu();
     const int slot = atomicAdd(&a.ctr->q_tail, 1);
     atomicExch(&a.queue[slot], k);
 }
@@ -616,7 +633,7 @@ __device__ __forceinline__ void push_center(const SolveArgs& a, int k) {
 __device__ __forceinline__ void release(const SolveArgs& a, int k) {
     const int old = atomicSub(&a.pending[k], 1);
     if (old == 1) {
-        __threadfence();
+        fence_gpu();
         if (atomicCAS(&a.state[k], kUndecided, kCenter) == kUndecided) {
             atomicMin(&a.owner[k], k);
             push_center(a, k);
@@ -660,12 +677,12 @@ __global__ void k_traversal_seed(SolveArgs a, const int* __restrict__ indeg) {
 // One CTA per center.  Thread 0 claims the next queue slot and waits (bounded) for it to be
 // filled; the CTA then solves the center, tests and writes its columns, and resolves the
 // traversal state of its ball members.
-// 128-thread teams are capped at 40 registers so that 12 CTAs (the shared-memory limit of the
-// 2D workload) fit an SM.
+// Registers are capped per team size (team_min_blocks) so that the CTAs that fit an SM's
+// shared memory also fit its register file.
 template <int D, bool PACKED, int NT>
-__global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
+__global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
-    __shared__ int s_j, s_q;
+    __shared__ int s_j, s_q, s_rej, s_own;
     const short* sbasis = load_basis(smem, a.basis, a.basis_count);
     StencilSmem sm;
     carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
@@ -699,12 +716,14 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_traversal(SolveArgs 
                     if (nsl < 2048) nsl <<= 1;
                 }
             }
+            if (j >= 0) fence_gpu();  // acquire what the centers that released j published
             s_j = j;
+            s_rej = 0;
+            s_own = 0;
         }
         __syncthreads();
         const int j = s_j;
         if (j < 0) break;
-        __threadfence();
         const Shape sh = shape_of<D>(a, sbasis, j);
         const int n = sh.n;
 
@@ -735,25 +754,26 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_traversal(SolveArgs 
         const bool ok = solve_local<D, PACKED, NT>(a, sh, j, q, sm);
         if (ok) lebesgue_values<NT>(n, q, sm);
         __syncthreads();
-        // Lebesgue test (§4.2.1) per column; q <= n <= 128 <= NT, so one thread per column
+        // Lebesgue test (§4.2.1) per column
         const long long base = a.slot_off[j];
-        bool failed = false, own = false;
-        if (tid < q) {
-            const double lam = ok ? sm.lam[tid] : nan;
+        int failed = 0, own = 0;
+        for (int c = tid; c < q; c += NT) {
+            const double lam = ok ? sm.lam[c] : nan;
             const bool test_ok =
                 ok && __double_as_longlong(lam) <= __double_as_longlong(sm.lam[0]);
             bool keep;
-            if (!ok) keep = (tid == 0);
+            if (!ok) keep = (c == 0);
             else if (a.mode != RBFFD_STAB_SEQ) keep = true;
             else keep = test_ok;
-            sm.keep[tid] = keep ? 1 : 0;
-            a.slot_lam[base + sm.cols[tid]] = lam;
-            a.slot_pass[base + sm.cols[tid]] = (tid == 0 || test_ok) ? 1 : 0;
-            failed = tid > 0 && !test_ok;
-            own = keep && (a.mode != RBFFD_STAB_FALLBACK || tid == 0 || test_ok);
+            sm.keep[c] = keep ? 1 : 0;
+            a.slot_lam[base + sm.cols[c]] = lam;
+            a.slot_pass[base + sm.cols[c]] = (c == 0 || test_ok) ? 1 : 0;
+            failed += c > 0 && !test_ok;
+            own += keep && (a.mode != RBFFD_STAB_FALLBACK || c == 0 || test_ok);
         }
-        const int rejected = __syncthreads_count(failed);
-        const int owned = __syncthreads_count(own);
+        if (failed) atomicAdd_block(&s_rej, failed);
+        if (own) atomicAdd_block(&s_own, own);
+        __syncthreads();
         double r2c = a.rho2[j];
         if (!(r2c > 0.0)) r2c = 1.0;
         const double inv_r2 = 1.0 / r2c;
@@ -764,20 +784,20 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_traversal(SolveArgs 
                 ok ? sm.X[sm.rowof[r] * sm.xs + c] * inv_r2 : nan;
         }
         // ownership: the earliest center keeping a row owns it
-        if (tid > 0 && tid < q && sm.keep[tid]) {
-            const int i = a.nbr[(size_t)j * ns + sm.cols[tid]];
-            atomicMin(&a.owner[i], j);
+        for (int c = tid; c < q; c += NT) {
+            if (c > 0 && sm.keep[c]) atomicMin(&a.owner[a.nbr[(size_t)j * ns + sm.cols[c]]], j);
         }
-        __threadfence();
         __syncthreads();
-        // resolve: kept members become covered; every later ball member loses a dependency
+        // resolve: kept members become covered; every later ball member loses a dependency.
+        // Each publishing thread fences first, so the CTA's ownership updates (ordered before
+        // it by the barrier) are visible wherever its state changes are.
         for (int t = 1 + tid; t < L; t += NT) {
             const int i = a.nbr[(size_t)j * ns + t];
             if (i <= j) continue;
             const int c = sm.colof[t];
             const bool kept = c >= 0 && sm.keep[c];
+            fence_gpu();
             if (kept && atomicCAS(&a.state[i], kUndecided, kCovered) == kUndecided) on_covered(a, i);
-            __threadfence();
             release(a, i);
         }
         if (tid == 0) {
@@ -786,10 +806,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_traversal(SolveArgs 
                 set_error(a.ctr, RBFFD_ESINGULAR);
             }
             const double K = sh.K;
-            atomicAdd(&a.ctr->alg_flops, c3 * K * K * K + 2.0 * K * K * owned);
+            atomicAdd(&a.ctr->alg_flops, c3 * K * K * K + 2.0 * K * K * s_own);
             atomicAdd(&a.ctr->n_centers, 1ull);
             atomicAdd(&a.ctr->sum_cols, (unsigned long long)q);
-            atomicAdd(&a.ctr->n_rejected, (unsigned long long)rejected);
+            atomicAdd(&a.ctr->n_rejected, (unsigned long long)s_rej);
             atomicAdd(&a.ctr->done, 1);
         }
         __syncthreads();
@@ -818,7 +838,7 @@ __global__ void k_fallback_collect(SolveArgs a) {
 // degree this launch handles (-1: all), n_cls/K_cls the largest stencil/system of the class,
 // so shared memory is sized for the class and a single column.
 template <int D, bool PACKED, int NT>
-__global__ void __launch_bounds__(NT, NT == 128 ? 12 : 1) k_fallback_solve(SolveArgs a, int cls, int n_cls,
+__global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(SolveArgs a, int cls, int n_cls,
                                                            int K_cls, int xs_cls,
                                                            int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
@@ -968,26 +988,63 @@ static cudaError_t allow_max_smem(const void* kern) {
                                 mx - (int)fa.sharedSizeBytes);
 }
 
-// Team size for a launch: 128 threads when several stencils fit an SM's shared memory,
-// else 512 so that the one or few resident stencils still keep enough warps busy.
-template <typename K128, typename K512>
-static int pick_team(K128 k128, K512 k512, size_t smem, int* nt_out, int* per_sm_out,
-                     int force = 0) {
-    int per_sm = 0;
-    if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k128, kNT, smem)) ||
-        per_sm < 1)
-        return RBFFD_EINVAL;
-    if (force == kMaxNT || (force == 0 && per_sm <= 4)) {
-        int p512 = 0;
-        if (RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p512, k512, kMaxNT, smem)) ||
-            p512 < 1)
-            return RBFFD_EINVAL;
-        *nt_out = kMaxNT;
-        *per_sm_out = p512;
-        return RBFFD_OK;
+// Resident CTAs per SM of the traversal kernel at team size nt (0 if nt has no instantiation
+// for this factorization).
+template <int D, bool PACKED>
+static int traversal_occupancy(int nt, size_t smem, int* per_sm) {
+    *per_sm = 0;
+    const void* k = nullptr;
+    switch (nt) {
+        case 32: if constexpr (PACKED) k = (const void*)k_traversal<D, PACKED, 32>; break;
+        case 64: if constexpr (PACKED) k = (const void*)k_traversal<D, PACKED, 64>; break;
+        case 96: if constexpr (PACKED) k = (const void*)k_traversal<D, PACKED, 96>; break;
+        case kNT: k = (const void*)k_traversal<D, PACKED, kNT>; break;
+        case kMaxNT: k = (const void*)k_traversal<D, PACKED, kMaxNT>; break;
+        default: break;
     }
-    *nt_out = kNT;
-    *per_sm_out = per_sm;
+    if (!k) return RBFFD_EINVAL;
+    if (RB_CUDA(allow_max_smem(k)) ||
+        RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, nt, smem)) || *per_sm < 1)
+        return RBFFD_EINVAL;
+    return RBFFD_OK;
+}
+
+template <int D, bool PACKED>
+static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
+    *per_sm = 0;
+    const void* k = nt == kMaxNT ? (const void*)k_fallback_solve<D, PACKED, kMaxNT>
+                                 : (const void*)k_fallback_solve<D, PACKED, kNT>;
+    if (RB_CUDA(allow_max_smem(k)) ||
+        RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, nt, smem)) || *per_sm < 1)
+        return RBFFD_EINVAL;
+    return RBFFD_OK;
+}
+
+// Team size for a launch when none is forced: 128 threads when several stencils fit an SM's
+// shared memory, else 512 so that the one or few resident stencils still keep enough warps
+// busy.  The LDL^T traversal takes 96 threads instead of 128 when that keeps at least two
+// more stencils resident (small systems with one right-hand side, where 128-thread teams are
+// register-bound): more stencils in flight hide more of each one's serial pivot steps.  A
+// forced size (32, 64 and 96 exist for the LDL^T traversal only) is taken as given.
+template <int D, bool PACKED, bool TRAVERSAL>
+static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out) {
+    auto occ = [&](int nt, int* ps) {
+        return TRAVERSAL ? traversal_occupancy<D, PACKED>(nt, smem, ps)
+                         : fallback_occupancy<D, PACKED>(nt, smem, ps);
+    };
+    int nt = force, rc;
+    if (nt == 0) {
+        int per_sm = 0;
+        if ((rc = occ(kNT, &per_sm))) return rc;
+        nt = per_sm <= 4 ? kMaxNT : kNT;
+        if (TRAVERSAL && PACKED && nt == kNT) {
+            int p96 = 0;
+            if ((rc = occ(96, &p96))) return rc;
+            if (p96 >= per_sm + 2) nt = 96;
+        }
+    }
+    if ((rc = occ(nt, per_sm_out))) return rc;
+    *nt_out = nt;
     return RBFFD_OK;
 }
 
@@ -1000,21 +1057,14 @@ static int prepare(int n, int K, int qcap, int basis_count, LaunchPlan* lp) {
     int stride = 0;
     const size_t bb = basis_smem_bytes(basis_count);
     const size_t smem = bb + solve_smem_per_cta(n, K, qcap, D, PACKED, &stride);
-    auto kt1 = k_traversal<D, PACKED, kNT>;
-    auto kt5 = k_traversal<D, PACKED, kMaxNT>;
-    auto kf1 = k_fallback_solve<D, PACKED, kNT>;
-    auto kf5 = k_fallback_solve<D, PACKED, kMaxNT>;
-    if (RB_CUDA(allow_max_smem((const void*)kt1)) || RB_CUDA(allow_max_smem((const void*)kt5)) ||
-        RB_CUDA(allow_max_smem((const void*)kf1)) || RB_CUDA(allow_max_smem((const void*)kf5)))
-        return RBFFD_EINVAL;
     int per_sm = 0, rc;
-    if ((rc = pick_team(kt1, kt5, smem, &lp->nt, &per_sm, lp->force_nt))) return rc;
+    if ((rc = pick_team<D, PACKED, true>(smem, lp->force_nt, &lp->nt, &per_sm))) return rc;
     lp->grid = per_sm * sm_count();
     lp->smem = smem;
     for (int c = 0; c < lp->n_fb; ++c) {
         FallbackClass& f = lp->fb[c];
         const size_t fs = bb + solve_smem_per_cta(f.n, f.K, 1, D, PACKED, &f.xs);
-        if ((rc = pick_team(kf1, kf5, fs, &f.nt, &per_sm))) return rc;
+        if ((rc = pick_team<D, PACKED, false>(fs, 0, &f.nt, &per_sm))) return rc;
         f.grid = per_sm * sm_count();
         f.smem = fs;
     }
@@ -1046,10 +1096,24 @@ static int traversal(const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
     // that holds a claimed entry is solved), so progress needs no co-residency, and plans
     // on other streams can run beside this grid.
     if (ev0) cudaEventRecord(ev0, s);
-    if (lp.nt == kMaxNT)
-        k_traversal<D, PACKED, kMaxNT><<<grid, kMaxNT, lp.smem, s>>>(a, lp.smem - basis_bytes, basis_bytes);
-    else
-        k_traversal<D, PACKED, kNT><<<grid, kNT, lp.smem, s>>>(a, lp.smem - basis_bytes, basis_bytes);
+    const size_t per_cta = lp.smem - basis_bytes;
+    switch (lp.nt) {
+        case 32:
+            if constexpr (PACKED) k_traversal<D, PACKED, 32><<<grid, 32, lp.smem, s>>>(a, per_cta, basis_bytes);
+            break;
+        case 64:
+            if constexpr (PACKED) k_traversal<D, PACKED, 64><<<grid, 64, lp.smem, s>>>(a, per_cta, basis_bytes);
+            break;
+        case 96:
+            if constexpr (PACKED) k_traversal<D, PACKED, 96><<<grid, 96, lp.smem, s>>>(a, per_cta, basis_bytes);
+            break;
+        case kMaxNT:
+            k_traversal<D, PACKED, kMaxNT><<<grid, kMaxNT, lp.smem, s>>>(a, per_cta, basis_bytes);
+            break;
+        default:
+            k_traversal<D, PACKED, kNT><<<grid, kNT, lp.smem, s>>>(a, per_cta, basis_bytes);
+            break;
+    }
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
     return RB_LAUNCHED(__func__);

@@ -13,125 +13,152 @@
 namespace rbffd {
 
 // ------------------------------------------------------------------ exclusive scans
-// Single-CTA tiled exclusive scan: out[0..count] with out[count] = total.  Used for cell
-// offsets and weight-slot offsets (a few hundred thousand entries at most).
+// Single-CTA exclusive scan in one pass: thread t owns a contiguous chunk of the input, sums
+// it, takes the block-wide exclusive scan of the chunk sums and writes its chunk.
+// out[0..count] with out[count] = total.  When count_dev is given the element count is
+// min(count, *count_dev), read on the device (the number of grid cells in use is only known
+// there).  Used for cell offsets, weight-slot offsets and row pointers.
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(1024) k_scan(const TI* __restrict__ in, TO* __restrict__ out,
-                                               int count) {
-    constexpr int kPer = 4;
-    constexpr int kTile = 1024 * kPer;
-    __shared__ TO tile[kTile];
+                                               int count, const int* __restrict__ count_dev) {
     __shared__ TO warp_tot[32];
-    __shared__ TO carry_s;
+    if (count_dev) count = min(count, *count_dev);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) carry_s = 0;
-    __syncthreads();
-    for (int base = 0; base < count; base += kTile) {
-        for (int r = 0; r < kPer; ++r) {
-            int i = base + r * 1024 + tid;
-            tile[r * 1024 + tid] = (i < count) ? (TO)in[i] : (TO)0;
-        }
-        __syncthreads();
-        TO v[kPer];
-        TO s = 0;
-        for (int r = 0; r < kPer; ++r) { v[r] = tile[tid * kPer + r]; s += v[r]; }
-        TO incl = s;  // inclusive warp scan of thread totals
-        for (int o = 1; o < 32; o <<= 1) {
-            TO t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) warp_tot[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            TO w = warp_tot[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                TO t = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += t;
-            }
-            warp_tot[lane] = w;  // inclusive over warps
-        }
-        __syncthreads();
-        TO run = carry_s + (wid > 0 ? warp_tot[wid - 1] : (TO)0) + (incl - s);
-        for (int r = 0; r < kPer; ++r) { tile[tid * kPer + r] = run; run += v[r]; }
-        __syncthreads();
-        for (int r = 0; r < kPer; ++r) {
-            int i = base + r * 1024 + tid;
-            if (i < count) out[i] = tile[r * 1024 + tid];
-        }
-        if (tid == 0) carry_s += warp_tot[31];
-        __syncthreads();
+    const int chunk = (count + 1023) / 1024;
+    const int b = min(tid * chunk, count), e = min(b + chunk, count);
+    TO s = 0;
+    for (int i = b; i < e; ++i) s += (TO)in[i];
+    TO incl = s;  // inclusive warp scan of the chunk sums
+    for (int o = 1; o < 32; o <<= 1) {
+        const TO t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    if (tid == 0) out[count] = carry_s;
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        TO w = warp_tot[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const TO t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    TO run = (wid > 0 ? warp_tot[wid - 1] : (TO)0) + (incl - s);
+    for (int i = b; i < e; ++i) {
+        out[i] = run;
+        run += (TO)in[i];
+    }
+    if (tid == 0) out[count] = warp_tot[31];
 }
 
 int launch_scan_i32_to_i64(const int* in, long long* out, int count, cudaStream_t s,
                            int* launches) {
-    k_scan<int, long long><<<1, 1024, 0, s>>>(in, out, count);
+    k_scan<int, long long><<<1, 1024, 0, s>>>(in, out, count, nullptr);
     ++*launches;
     return RB_LAUNCHED(__func__);
 }
 
 // ------------------------------------------------------------------ grid build
-// One CTA: bounding box, cell size for about 2 nodes per cell, first search ring.
+// Order-preserving map of a finite FP64 value to an unsigned 64-bit key and back, so the
+// bounding box is reduced with integer instructions and atomics (no FP64 min/max).
+__device__ __forceinline__ unsigned long long ord_key(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double ord_val(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// Cell size for about 2 nodes per cell and the first search ring, from the bounding box.
 template <int D>
-__global__ void __launch_bounds__(1024) k_grid_params(const double* __restrict__ X, int N, int n,
-                                                      int ncell_max, GridParams* gp) {
-    __shared__ double smin[3][32], smax[3][32];
-    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int i = threadIdx.x; i < N; i += blockDim.x)
+__device__ void set_grid_params(const double* L, const double* H, int N, int n, int ncell_max,
+                                GridParams* gp) {
+    double ext[3] = {0.0, 0.0, 0.0};
+    double vol = 1.0, maxext = 0.0;
+    for (int a = 0; a < D; ++a) {
+        ext[a] = H[a] - L[a];
+        maxext = fmax(maxext, ext[a]);
+    }
+    if (!(maxext > 0.0)) maxext = 1.0;
+    for (int a = 0; a < D; ++a) vol *= fmax(ext[a], 1e-3 * maxext);
+    const double ppc = 2.0;  // target nodes per cell
+    double h = (D == 2) ? sqrt(vol * ppc / N) : cbrt(vol * ppc / N);
+    if (!(h > 0.0)) h = maxext;
+    int dims[3] = {1, 1, 1};
+    long long nc = 1;
+    for (int it = 0; it < 200; ++it) {
+        nc = 1;
         for (int a = 0; a < D; ++a) {
-            double v = X[(size_t)i * D + a];
-            lo[a] = fmin(lo[a], v);
-            hi[a] = fmax(hi[a], v);
+            double c = floor(ext[a] / h) + 1.0;
+            dims[a] = (int)fmin(c, 1048576.0);
+            nc *= dims[a];
+        }
+        if (nc <= ncell_max) break;
+        h *= 1.1;
+    }
+    for (int a = 0; a < D; ++a) gp->lo[a] = L[a];
+    for (int a = D; a < 3; ++a) { gp->lo[a] = 0.0; dims[a] = 1; }
+    gp->h = h;
+    gp->inv_h = 1.0 / h;
+    for (int a = 0; a < 3; ++a) gp->dims[a] = dims[a];
+    gp->ncell = (int)nc;
+    // ring whose ball holds about n nodes at the average density
+    double per = (double)N / (double)nc;
+    double w = (D == 2) ? 3.14159265358979 : 4.18879020478639;
+    double r = (D == 2) ? sqrt(n / (per * w)) : cbrt(n / (per * w));
+    gp->r0 = (int)fmax(1.0, ceil(r));
+}
+
+// Bounding box over all CTAs (integer keys, one set of atomics per CTA); the last CTA to
+// finish derives the grid parameters.
+template <int D>
+__global__ void __launch_bounds__(256) k_grid_params(const double* __restrict__ X, int N, int n,
+                                                     int ncell_max, BBoxAcc* acc,
+                                                     GridParams* gp) {
+    __shared__ unsigned long long s_lo[3][8], s_hi[3][8];
+    __shared__ bool s_last;
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        for (int a = 0; a < D; ++a) {
+            const unsigned long long k = ord_key(X[(size_t)i * D + a]);
+            lo[a] = k < lo[a] ? k : lo[a];
+            hi[a] = k > hi[a] ? k : hi[a];
         }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int a = 0; a < D; ++a) {
         for (int o = 16; o > 0; o >>= 1) {
-            lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-            hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+            const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo[a], o);
+            const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi[a], o);
+            lo[a] = l2 < lo[a] ? l2 : lo[a];
+            hi[a] = h2 > hi[a] ? h2 : hi[a];
         }
-        if (lane == 0) { smin[a][wid] = lo[a]; smax[a][wid] = hi[a]; }
+        if (lane == 0) { s_lo[a][wid] = lo[a]; s_hi[a][wid] = hi[a]; }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const int nw = blockDim.x / 32;
-        double L[3], H[3], ext[3];
-        double vol = 1.0, maxext = 0.0;
         for (int a = 0; a < D; ++a) {
-            L[a] = smin[a][0]; H[a] = smax[a][0];
-            for (int w = 1; w < nw; ++w) { L[a] = fmin(L[a], smin[a][w]); H[a] = fmax(H[a], smax[a][w]); }
-            ext[a] = H[a] - L[a];
-            maxext = fmax(maxext, ext[a]);
-        }
-        if (!(maxext > 0.0)) maxext = 1.0;
-        for (int a = 0; a < D; ++a) vol *= fmax(ext[a], 1e-3 * maxext);
-        const double ppc = 2.0;  // target nodes per cell
-        double h = (D == 2) ? sqrt(vol * ppc / N) : cbrt(vol * ppc / N);
-        if (!(h > 0.0)) h = maxext;
-        int dims[3] = {1, 1, 1};
-        long long nc = 1;
-        for (int it = 0; it < 200; ++it) {
-            nc = 1;
-            for (int a = 0; a < D; ++a) {
-                double c = floor(ext[a] / h) + 1.0;
-                dims[a] = (int)fmin(c, 1048576.0);
-                nc *= dims[a];
+            unsigned long long l = s_lo[a][0], h = s_hi[a][0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                l = s_lo[a][w] < l ? s_lo[a][w] : l;
+                h = s_hi[a][w] > h ? s_hi[a][w] : h;
             }
-            if (nc <= ncell_max) break;
-            h *= 1.1;
+            atomicMax(&acc->nlo[a], ~l);
+            atomicMax(&acc->hi[a], h);
         }
-        for (int a = 0; a < D; ++a) gp->lo[a] = L[a];
-        for (int a = D; a < 3; ++a) { gp->lo[a] = 0.0; dims[a] = 1; }
-        gp->h = h;
-        gp->inv_h = 1.0 / h;
-        for (int a = 0; a < 3; ++a) gp->dims[a] = dims[a];
-        gp->ncell = (int)nc;
-        // ring whose ball holds about n nodes at the average density
-        double per = (double)N / (double)nc;
-        double w = (D == 2) ? 3.14159265358979 : 4.18879020478639;
-        double r = (D == 2) ? sqrt(n / (per * w)) : cbrt(n / (per * w));
-        gp->r0 = (int)fmax(1.0, ceil(r));
+        __threadfence();
+        s_last = atomicAdd(&acc->done, 1u) == gridDim.x - 1;
     }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    double L[3], H[3];
+    for (int a = 0; a < D; ++a) {
+        L[a] = ord_val(~*((volatile unsigned long long*)&acc->nlo[a]));
+        H[a] = ord_val(*((volatile unsigned long long*)&acc->hi[a]));
+    }
+    set_grid_params<D>(L, H, N, n, ncell_max, gp);
 }
 
 template <int D>
@@ -326,7 +353,7 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
 static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
 size_t grid_scratch_bytes(int N, int D, int ncell_max) {
-    size_t b = round256(sizeof(GridParams));
+    size_t b = round256(sizeof(GridParams)) + round256(sizeof(BBoxAcc));
     b += 3 * round256((size_t)(ncell_max + 1) * sizeof(int));  // count, start, cursor
     b += 2 * round256((size_t)N * sizeof(int));                // cell_of, sorted_idx
     b += round256((size_t)N * D * sizeof(double));             // sorted_X
@@ -344,6 +371,7 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
         return r;
     };
     GridParams* gp = reinterpret_cast<GridParams*>(take(sizeof(GridParams)));
+    BBoxAcc* acc = reinterpret_cast<BBoxAcc*>(take(sizeof(BBoxAcc)));
     int* count = reinterpret_cast<int*>(take((size_t)(ncell_max + 1) * sizeof(int)));
     int* start = reinterpret_cast<int*>(take((size_t)(ncell_max + 1) * sizeof(int)));
     int* cursor = reinterpret_cast<int*>(take((size_t)(ncell_max + 1) * sizeof(int)));
@@ -352,15 +380,19 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     double* sorted_X = reinterpret_cast<double*>(take((size_t)N * D * sizeof(double)));
 
     int rc;
-    if ((rc = RB_CUDA(cudaMemsetAsync(count, 0, (size_t)(ncell_max + 1) * sizeof(int), s))) ||
+    if ((rc = RB_CUDA(cudaMemsetAsync(acc, 0, sizeof(BBoxAcc), s))) ||
+        (rc = RB_CUDA(cudaMemsetAsync(count, 0, (size_t)(ncell_max + 1) * sizeof(int), s))) ||
         (rc = RB_CUDA(cudaMemsetAsync(cursor, 0, (size_t)(ncell_max + 1) * sizeof(int), s))) ||
         (rc = RB_CUDA(cudaMemsetAsync(indeg, 0, (size_t)N * sizeof(int), s))))
         return rc;
-    k_grid_params<D><<<1, 1024, 0, s>>>(X, N, n, ncell_max, gp);
     const int tb = 256;
     const int nb = (N + tb - 1) / tb;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_grid_params<D><<<nb < sms ? nb : sms, tb, 0, s>>>(X, N, n, ncell_max, acc, gp);
     k_cell_count<D><<<nb, tb, 0, s>>>(X, N, gp, cell_of, count);
-    k_scan<int, int><<<1, 1024, 0, s>>>(count, start, ncell_max);
+    k_scan<int, int><<<1, 1024, 0, s>>>(count, start, ncell_max, &gp->ncell);
     k_cell_fill<D><<<nb, tb, 0, s>>>(X, N, cell_of, start, cursor, sorted_idx, sorted_X);
     const int wpb = 8;
     size_t smem = (size_t)wpb * (2 * n + 32) * (sizeof(unsigned long long) + sizeof(int));

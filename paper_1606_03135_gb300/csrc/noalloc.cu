@@ -16,7 +16,8 @@ constexpr size_t r256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr int kMaxNodes = RBFFD_NOALLOC_MAX_NODES;
 constexpr int kMaxCells = 2 * kMaxNodes + 64;  // the cell-grid bound rbffd_plan uses
 // grid scratch for the largest case (3D) + in-degree counts + device status block
-constexpr size_t kGridBytes = r256(sizeof(GridParams)) + 3 * r256((size_t)(kMaxCells + 1) * 4) +
+constexpr size_t kGridBytes = r256(sizeof(GridParams)) + r256(sizeof(BBoxAcc)) +
+                              3 * r256((size_t)(kMaxCells + 1) * 4) +
                               2 * r256((size_t)kMaxNodes * 4) + r256((size_t)kMaxNodes * 3 * 8);
 constexpr size_t kIndegBytes = r256((size_t)kMaxNodes * 4);
 constexpr size_t kScratchBytes = kGridBytes + kIndegBytes + r256(sizeof(DevCounters));

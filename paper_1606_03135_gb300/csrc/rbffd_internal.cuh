@@ -39,6 +39,14 @@ struct GridParams {
     int r0;        // first search ring (in cells)
 };
 
+// Bounding-box accumulators of the grid build (zeroed before the launch): nlo holds the
+// complement of the smallest order-preserving key, so both bounds grow by atomicMax from zero.
+struct BBoxAcc {
+    unsigned long long nlo[3];
+    unsigned long long hi[3];
+    unsigned int done;
+};
+
 // Device-side counters and status of one plan (one 256-byte block; zeroed per call).
 struct DevCounters {
     int status;              // first error code (RBFFD_*), 0 = OK

@@ -281,15 +281,16 @@ class Plan:
 
 # ------------------------------------------------------------------ schedule autotuner
 def autotune(nodes, n, ell, m, delta, mode=STAB_SEQ, candidates=None, repeats=2):
-    """Pick the traversal schedule (team size x persistent-grid cap) for a workload by timing
-    one assembly of each candidate on the device (CUDA events, after a warm-up assembly).
+    """Pick the traversal schedule for a workload -- warp-per-stencil (32 threads), 64-, 96-, 128-
+    or 512-thread tiles per stencil, and the persistent-grid cap -- by timing assemblies of each
+    candidate on the device (CUDA events, best of `repeats`, after a warm-up assembly).
     Returns (best kwargs for Plan, {candidate: ms}).  Results do not depend on the schedule
     (the same stencils are solved the same way), only the time does."""
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     if candidates is None:
-        candidates = [dict(team=t, max_ctas=c) for t in (0, 128, 512)
-                      for c in (0, 8 * sms, 4 * sms)]
+        candidates = [dict(team=t) for t in (32, 64, 96, 128, 512)]
+        candidates += [dict(team=0, max_ctas=c) for c in (0, 4 * sms)]
     timings = {}
     for cand in candidates:
         try:

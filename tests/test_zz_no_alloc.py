@@ -38,7 +38,8 @@ def _noalloc(X, n, delta):
 
 def test_noalloc_matches_plan_on_two_calls_in_a_row():
     cases = [
-        (NS.jittered_grid(18, 3, seed=11), 45, 3, 7, 0.2),   # 5832 nodes, 3D, larger first
+        (NS.jittered_grid(32, 3, seed=3), 20, 2, 5, 0.5),    # 32768 nodes: the capacity, 3D
+        (NS.jittered_grid(18, 3, seed=11), 45, 3, 7, 0.2),   # 5832 nodes, 3D
         (NS.disk2d(3000, seed=4), 12, 2, 3, 0.5),            # then a smaller 2D set
     ]
     for X, n, ell, m, delta in cases:
