@@ -578,8 +578,9 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
         out->sum_cols = (int64_t)c.sum_cols;
         out->n_singular = c.n_singular;
         out->status = c.status;
-        const double K = p->K;
-        out->alg_flops = c.alg_flops;
+        // (1/3) K^3 (LDL^T) or (2/3) K^3 (LU) per factorization, 2 K^2 per owned row's solve
+        const double c3 = p->opts.factor == RBFFD_FACTOR_LU ? 2.0 / 3.0 : 1.0 / 3.0;
+        out->alg_flops = c3 * (double)c.sum_k3 + 2.0 * (double)c.sum_k2q;
         out->nnz = p->nnz;
         if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) out->ms_traversal = ms;
         if (cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) out->ms_fallback = ms;

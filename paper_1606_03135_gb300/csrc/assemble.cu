@@ -23,6 +23,7 @@
 // flattened over (row, column) pairs to keep lanes busy.
 #include <cuda_runtime.h>
 
+#include "fp64_int.cuh"
 #include "rbffd_internal.cuh"
 
 namespace rbffd {
@@ -91,7 +92,7 @@ __device__ __forceinline__ Shape shape_of(const SolveArgs& a, const short* sbasi
     s.M = a.Mof[ell];
     s.K = s.n + s.M;
     s.m = a.node_m ? (int)a.node_m[j] : a.m;
-    s.coef = (double)(s.m * (s.m + D - 2));
+    s.coef = exact_double(s.m * (s.m + D - 2));
     const short* b = sbasis + a.boff[ell];
     s.bs.parent = b;
     s.bs.var = b + s.M;
@@ -174,14 +175,19 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
     const Basis& bs = sh.bs;
     double* X = sm.X;
     const int xs = sm.xs;
-    double r2c = a.rho2[j];
-    if (!(r2c > 0.0)) r2c = 1.0;
-    const double rho = sqrt(r2c);
     const double* xc = a.X + (size_t)j * D;
-    for (int t = tid; t < n; t += NT) {
-        const int id = a.nbr[(size_t)j * a.n + t];
-        for (int c = 0; c < D; ++c)
-            sm.xi[t * D + c] = __ddiv_rn(__dsub_rn(a.X[(size_t)id * D + c], xc[c]), rho);
+    // Scaled coordinates (x - x_c) / rho_j, correctly rounded: the weights of ill-conditioned
+    // stencils are as sensitive to the node positions as to the solve, so these match the
+    // oracle's exactly.  Only the threads that hold a node compute rho_j.
+    if (tid < n) {
+        double r2c = a.rho2[j];
+        if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
+        const double rho = sqrt(r2c);
+        for (int t = tid; t < n; t += NT) {
+            const int id = a.nbr[(size_t)j * a.n + t];
+            for (int c = 0; c < D; ++c)
+                sm.xi[t * D + c] = __ddiv_rn(__dsub_rn(a.X[(size_t)id * D + c], xc[c]), rho);
+        }
     }
     if (PACKED) {
         for (int e = tid; e < tri(K); e += NT) sm.T[e] = 0.0;
@@ -214,7 +220,7 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
             if (first || ra != pr) {
                 const int rb = ra + 1 + t;
                 const double r2 = sqdist_rn<D>(sm.xi + ra * D, sm.xi + rb * D);
-                const double r = sqrt(r2);
+                const double r = sqrt_fast(r2);
                 double pm2 = r;
                 for (int s = 0; s < (m - 3) / 2; ++s) pm2 = __dmul_rn(pm2, r2);
                 const double pm = __dmul_rn(pm2, r2);
@@ -261,67 +267,12 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
             const int ch = bs.lap_child[l * D + d];
             if (ch >= 0) {
                 const double pv = PACKED ? sm.T[tri(n + ch) + t] : sm.A[t * xs + n + ch];
-                s = fma((double)bs.lap_coef[l * D + d], pv, s);
+                s = fma(exact_double(bs.lap_coef[l * D + d]), pv, s);
             }
         }
         X[(n + l) * xs + c] = s;
     }
     __syncthreads();
-}
-
-// Reciprocal of an FP64 value computed on the integer pipe (GB300's FP64 pipe is ~1/64 of its
-// FP32 rate, and a scalar division issued by one warp occupies it as a full warp
-// instruction): a 24-bit FP32 seed refined by two Newton-Raphson steps t' = t + t (1 - m t)
-// on the mantissa m in 64-bit fixed point, then rounded to 53 bits.  Within 1 ulp of 1/x
-// for normal x; zero, subnormal and near-overflow inputs use the FP64 division.
-__device__ __forceinline__ double rcp_fixed(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned long long sign = b >> 63;
-    const int e = (int)((b >> 52) & 0x7ff);
-    const unsigned long long f = b & 0xFFFFFFFFFFFFFull;
-    if (e == 0 || e >= 0x7fd) return 1.0 / x;
-    if (f == 0)  // a power of two: exact
-        return __longlong_as_double((long long)((sign << 63) | ((unsigned long long)(2046 - e) << 52)));
-    const unsigned long long M = f | (1ull << 52);  // m = M / 2^52 in [1, 2)
-    const float rf = __frcp_rn(__int_as_float(0x3F800000 | (int)(f >> 29)));
-    const unsigned rb = __float_as_uint(rf);
-    unsigned long long Y =  // Y = t * 2^64, t = 1/m in (1/2, 1]
-        rb >= 0x3F800000u ? ~0ull : (unsigned long long)((rb & 0x7FFFFFu) | 0x800000u) << 40;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const unsigned long long lo = M * Y, hi = __umul64hi(M, Y);   // P = M Y
-        const unsigned long long H = (1ull << 52) - hi - (lo != 0ull);  // 2^116 - P, high part
-        const unsigned long long L = 0ull - lo;
-        const long long Dv = (long long)((H << 12) | (L >> 52));  // 2^64 (1 - m t)
-        const unsigned long long C = Dv >= 0 ? __umul64hi(Y, (unsigned long long)Dv)
-                                              : 0ull - __umul64hi(Y, (unsigned long long)(-Dv));
-        Y += C;
-    }
-    unsigned long long m53 = (Y + (1ull << 10)) >> 11;
-    int ex = 1022 - (e - 1023);
-    if (m53 >> 53) { m53 >>= 1; ++ex; }
-    return __longlong_as_double(
-        (long long)((sign << 63) | ((unsigned long long)ex << 52) | (m53 & 0xFFFFFFFFFFFFFull)));
-}
-
-// A float close to the non-negative double with IEEE bits `b` (top 23 mantissa bits,
-// exponent clamped to the float range), built with integer operations only.
-__device__ __forceinline__ float approx_f32(unsigned long long b) {
-    const int e = (int)(b >> 52) - 1023;
-    if (b == 0ull) return 0.0f;
-    const int ef = e < -126 ? -126 : (e > 127 ? 127 : e);
-    const unsigned mant = (unsigned)((b >> 29) & 0x7fffffu);
-    return __int_as_float((int)(((unsigned)(ef + 127) << 23) | mant));
-}
-
-__device__ __forceinline__ unsigned long long abs_bits(double v) {
-    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
-}
-
-// Sign-free top 32 bits of an FP64 value (exponent and 20 mantissa bits): ordering these keys
-// orders the magnitudes up to a relative 2^-20, with no FP64 instruction.
-__device__ __forceinline__ unsigned mag_key(double v) {
-    return (unsigned)__double2hiint(v) & 0x7fffffffu;
 }
 
 // LU with partial pivoting of [A_hat | B_hat] in the full layout (the paper's decomposition,
@@ -690,7 +641,6 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ns = a.n, N = a.N;  // ns: row stride of nbr and of a weight slot
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    const double c3 = PACKED ? 1.0 / 3.0 : 2.0 / 3.0;
 
     for (;;) {
         if (tid == 0) {
@@ -775,8 +725,8 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
         if (own) atomicAdd_block(&s_own, own);
         __syncthreads();
         double r2c = a.rho2[j];
-        if (!(r2c > 0.0)) r2c = 1.0;
-        const double inv_r2 = 1.0 / r2c;
+        if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
+        const double inv_r2 = rcp_fixed(r2c);
         for (int e = tid; e < q * n; e += NT) {
             const int c = e / n, r = e - c * n;
             if (!sm.keep[c]) continue;
@@ -805,8 +755,9 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
                 atomicAdd(&a.ctr->n_singular, 1);
                 set_error(a.ctr, RBFFD_ESINGULAR);
             }
-            const double K = sh.K;
-            atomicAdd(&a.ctr->alg_flops, c3 * K * K * K + 2.0 * K * K * s_own);
+            const unsigned long long K = (unsigned long long)sh.K;
+            atomicAdd(&a.ctr->sum_k3, K * K * K);
+            atomicAdd(&a.ctr->sum_k2q, K * K * (unsigned long long)s_own);
             atomicAdd(&a.ctr->n_centers, 1ull);
             atomicAdd(&a.ctr->sum_cols, (unsigned long long)q);
             atomicAdd(&a.ctr->n_rejected, (unsigned long long)s_rej);
@@ -849,7 +800,6 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
     const int tid = threadIdx.x;
     const int count = *((volatile int*)&a.ctr->fb_count);
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    const double c3 = PACKED ? 1.0 / 3.0 : 2.0 / 3.0;
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int i = a.fb_list[w];
         if (cls >= 0 && (int)a.node_ell[i] != cls) continue;  // another class's launch
@@ -861,8 +811,8 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
         if (ok) lebesgue_values<NT>(sh.n, 1, sm);
         __syncthreads();
         double r2c = a.rho2[i];
-        if (!(r2c > 0.0)) r2c = 1.0;
-        const double inv_r2 = 1.0 / r2c;
+        if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
+        const double inv_r2 = rcp_fixed(r2c);
         const long long slot = a.slot_off[i];
         for (int r = tid; r < sh.n; r += NT)
             a.slot_w[slot * a.n + r] = ok ? sm.X[sm.rowof[r] * sm.xs] * inv_r2 : nan;
@@ -872,8 +822,9 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
                 atomicAdd(&a.ctr->n_singular, 1);
                 set_error(a.ctr, RBFFD_ESINGULAR);
             }
-            const double K = sh.K;
-            atomicAdd(&a.ctr->alg_flops, c3 * K * K * K + 2.0 * K * K);
+            const unsigned long long K = (unsigned long long)sh.K;
+            atomicAdd(&a.ctr->sum_k3, K * K * K);
+            atomicAdd(&a.ctr->sum_k2q, K * K);
             atomicAdd(&a.ctr->n_fallback, 1ull);
             atomicAdd(&a.ctr->sum_cols, 1ull);
         }

@@ -61,8 +61,9 @@ struct DevCounters {
     unsigned long long n_rejected;
     unsigned long long sum_cols;
     unsigned long long n_fallback;
-    double alg_flops;        // sum over factored stencils of c K^3 + 2 K^2 (rows they own)
-    unsigned long long pad[21];
+    unsigned long long sum_k3;   // sum over factored stencils of K^3
+    unsigned long long sum_k2q;  // sum over factored stencils of K^2 (rows they own)
+    unsigned long long pad[20];
 };
 
 // Map a CUDA status to an RBFFD code; with RBFFD_DEBUG set in the environment the failing
