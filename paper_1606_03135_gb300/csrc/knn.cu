@@ -207,9 +207,114 @@ __device__ __forceinline__ bool key_less(unsigned long long ka, int ia, unsigned
     return ka < kb || (ka == kb && ia < ib);
 }
 
-// One warp per query node.  The warp keeps the n best candidates seen so far as a sorted
-// list in shared memory and merges batches of 32 candidates into it (ranks computed by
-// comparison counting, so the order is exact).
+// Search box of ring r around the query's cell and the squared radius that no point outside
+// the box can reach (+inf when the box covers the whole grid).
+template <int D>
+__device__ __forceinline__ bool ring_box(const GridParams& g, const int* c0, int r, int* clo,
+                                         int* chi, unsigned long long* bkey) {
+    bool all = true;
+    for (int a = 0; a < D; ++a) {
+        clo[a] = max(c0[a] - r, 0);
+        chi[a] = min(c0[a] + r, g.dims[a] - 1);
+        all = all && clo[a] == 0 && chi[a] == g.dims[a] - 1;
+    }
+    const double rb = (double)r * g.h;
+    *bkey = dkey(all ? __longlong_as_double(0x7ff0000000000000LL)  // +inf
+                     : rb * rb * (1.0 - 1e-8));
+    return all;
+}
+
+// Streaming search (any number of candidates): the warp keeps the n best candidates seen so
+// far as a sorted list in shared memory and merges batches of 32 into it (ranks by comparison
+// counting, so the order is exact), growing the ring from r until n candidates lie inside the
+// guaranteed radius.  Returns the buffer (0 or 1) that holds the list.
+template <int D>
+__device__ int knn_stream(const GridParams& g, const double* xq, const int* c0, int r, int n,
+                          const int* __restrict__ cell_start, const int* __restrict__ sorted_idx,
+                          const double* __restrict__ sorted_X, unsigned long long* lk, int* li,
+                          unsigned long long* bk, int* bi) {
+    const int lane = threadIdx.x & 31;
+    int cnt = 0, cur = 0;
+    for (;;) {
+        int clo[3], chi[3];
+        unsigned long long bkey;
+        const bool all = ring_box<D>(g, c0, r, clo, chi, &bkey);
+        cnt = 0;
+        cur = 0;
+        const int ny = chi[1] - clo[1] + 1;
+        const int nz = (D == 3) ? chi[2] - clo[2] + 1 : 1;
+        for (int rz = 0; rz < nz; ++rz)
+            for (int ry = 0; ry < ny; ++ry) {
+                int cc[3] = {clo[0], clo[1] + ry, (D == 3) ? clo[2] + rz : 0};
+                const int row0 = cell_index<D>(g, cc);
+                const int beg = cell_start[row0];
+                const int end = cell_start[row0 + (chi[0] - clo[0]) + 1];
+                for (int b0 = beg; b0 < end; b0 += 32) {
+                    const int p = b0 + lane;
+                    bool valid = p < end;
+                    unsigned long long key = ~0ull;
+                    int id = 0x7fffffff;
+                    if (valid) {
+                        double xp[3];
+                        for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)p * D + a];
+                        key = dkey(sqdist_rn<D>(xq, xp));
+                        id = sorted_idx[p];
+                        valid = key < bkey;
+                        if (valid && cnt == n) valid = key_less(key, id, lk[cur * n + n - 1], li[cur * n + n - 1]);
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, valid);
+                    if (bal == 0) continue;
+                    int rb_ = 0;  // rank among the valid batch members
+                    for (int s2 = 0; s2 < 32; ++s2) {
+                        const unsigned long long ks = __shfl_sync(0xffffffffu, key, s2);
+                        const int is = __shfl_sync(0xffffffffu, id, s2);
+                        if (((bal >> s2) & 1u) && key_less(ks, is, key, id)) ++rb_;
+                    }
+                    int lo_ = 0, hi_ = cnt;  // position in the current list
+                    while (lo_ < hi_) {
+                        const int mid = (lo_ + hi_) >> 1;
+                        if (key_less(lk[cur * n + mid], li[cur * n + mid], key, id)) lo_ = mid + 1;
+                        else hi_ = mid;
+                    }
+                    bk[lane] = valid ? key : ~0ull;
+                    bi[lane] = valid ? id : 0x7fffffff;
+                    __syncwarp();
+                    const int nxt = cur ^ 1;
+                    for (int e = lane; e < cnt; e += 32) {
+                        const unsigned long long ke = lk[cur * n + e];
+                        const int ie = li[cur * n + e];
+                        int before = 0;
+                        for (int s2 = 0; s2 < 32; ++s2)
+                            if (((bal >> s2) & 1u) && key_less(bk[s2], bi[s2], ke, ie)) ++before;
+                        const int np = e + before;
+                        if (np < n) { lk[nxt * n + np] = ke; li[nxt * n + np] = ie; }
+                    }
+                    if (valid) {
+                        const int np = lo_ + rb_;
+                        if (np < n) { lk[nxt * n + np] = key; li[nxt * n + np] = id; }
+                    }
+                    __syncwarp();
+                    cnt = min(cnt + __popc(bal), n);
+                    cur = nxt;
+                }
+            }
+        if (cnt == n || all) break;
+        ++r;
+    }
+    return cur;
+}
+
+// One warp per query node.  Usual case: every candidate of the search box that lies inside
+// the guaranteed radius is collected into shared memory (growing the ring until there are n),
+// and the warp sorts them by (IEEE bits of d2, index) with a bitonic network; the first n
+// are the stencil.  Boxes with more than kCollect such candidates (strongly clustered nodes)
+// take the streaming search instead.  Either way the order is exact.
+constexpr int kCollect = 256;
+
+__device__ __forceinline__ int knn_words(int n) {  // per-warp buffer entries
+    return max(2 * n + 32, kCollect);
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N, int n,
                                              double omd2, const GridParams* __restrict__ gp,
@@ -223,12 +328,9 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    // per warp: keys[2][n], ids[2][n], batch keys[32], batch ids[32]
-    unsigned long long* lk = knn_smem + (size_t)wib * (2 * n + 32);
-    unsigned long long* bk = lk + 2 * n;
-    int* ids_base = reinterpret_cast<int*>(knn_smem + (size_t)wpb * (2 * n + 32));
-    int* li = ids_base + (size_t)wib * (2 * n + 32);
-    int* bi = li + 2 * n;
+    const int W = knn_words(n);
+    unsigned long long* wk = knn_smem + (size_t)wib * W;
+    int* wi = reinterpret_cast<int*>(knn_smem + (size_t)wpb * W) + (size_t)wib * W;
     const GridParams g = *gp;
 
     for (int q = blockIdx.x * wpb + wib; q < N; q += gridDim.x * wpb) {
@@ -238,96 +340,84 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
             xq[a] = X[(size_t)q * D + a];
             c0[a] = cell_coord<D>(g, xq[a], a);
         }
-        int r = g.r0;
-        int cnt = 0, cur = 0;
-        for (;;) {
+        int r = g.r0, cnt = 0;
+        bool all = false;
+        for (;;) {  // collect the candidates inside the guaranteed radius of ring r
             int clo[3], chi[3];
-            bool all = true;
-            for (int a = 0; a < D; ++a) {
-                clo[a] = max(c0[a] - r, 0);
-                chi[a] = min(c0[a] + r, g.dims[a] - 1);
-                all = all && clo[a] == 0 && chi[a] == g.dims[a] - 1;
-            }
-            double rb = (double)r * g.h;
-            double bound = all ? __longlong_as_double(0x7ff0000000000000LL)  // +inf
-                               : rb * rb * (1.0 - 1e-8);
-            const unsigned long long bkey = dkey(bound);
+            unsigned long long bkey;
+            all = ring_box<D>(g, c0, r, clo, chi, &bkey);
             cnt = 0;
-            cur = 0;
             const int ny = chi[1] - clo[1] + 1;
             const int nz = (D == 3) ? chi[2] - clo[2] + 1 : 1;
-            for (int rz = 0; rz < nz; ++rz)
-                for (int ry = 0; ry < ny; ++ry) {
+            for (int rz = 0; rz < nz && cnt <= kCollect; ++rz)
+                for (int ry = 0; ry < ny && cnt <= kCollect; ++ry) {
                     int cc[3] = {clo[0], clo[1] + ry, (D == 3) ? clo[2] + rz : 0};
-                    int row0 = cell_index<D>(g, cc);
-                    int beg = cell_start[row0];
-                    int end = cell_start[row0 + (chi[0] - clo[0]) + 1];
-                    for (int b0 = beg; b0 < end; b0 += 32) {
-                        int p = b0 + lane;
-                        bool valid = p < end;
+                    const int row0 = cell_index<D>(g, cc);
+                    const int beg = cell_start[row0];
+                    const int end = cell_start[row0 + (chi[0] - clo[0]) + 1];
+                    for (int b0 = beg; b0 < end && cnt <= kCollect; b0 += 32) {
+                        const int p = b0 + lane;
                         unsigned long long key = ~0ull;
-                        int id = 0x7fffffff;
-                        if (valid) {
+                        int id = 0;
+                        if (p < end) {
                             double xp[3];
                             for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)p * D + a];
-                            double s = sqdist_rn<D>(xq, xp);
-                            key = dkey(s);
+                            key = dkey(sqdist_rn<D>(xq, xp));
                             id = sorted_idx[p];
-                            valid = key < bkey;
-                            if (valid && cnt == n) valid = key_less(key, id, lk[cur * n + n - 1], li[cur * n + n - 1]);
                         }
-                        unsigned bal = __ballot_sync(0xffffffffu, valid);
-                        if (bal == 0) continue;
-                        // rank among the valid batch members
-                        int rb_ = 0;
-                        for (int s2 = 0; s2 < 32; ++s2) {
-                            unsigned long long ks = __shfl_sync(0xffffffffu, key, s2);
-                            int is = __shfl_sync(0xffffffffu, id, s2);
-                            if (((bal >> s2) & 1u) && key_less(ks, is, key, id)) ++rb_;
-                        }
-                        // position in the current list
-                        int lo_ = 0, hi_ = cnt;
-                        while (lo_ < hi_) {
-                            int mid = (lo_ + hi_) >> 1;
-                            if (key_less(lk[cur * n + mid], li[cur * n + mid], key, id)) lo_ = mid + 1;
-                            else hi_ = mid;
-                        }
-                        bk[lane] = valid ? key : ~0ull;
-                        bi[lane] = valid ? id : 0x7fffffff;
-                        __syncwarp();
-                        const int nxt = cur ^ 1;
-                        for (int e = lane; e < cnt; e += 32) {
-                            unsigned long long ke = lk[cur * n + e];
-                            int ie = li[cur * n + e];
-                            int before = 0;
-                            for (int s2 = 0; s2 < 32; ++s2)
-                                if (((bal >> s2) & 1u) && key_less(bk[s2], bi[s2], ke, ie)) ++before;
-                            int np = e + before;
-                            if (np < n) { lk[nxt * n + np] = ke; li[nxt * n + np] = ie; }
-                        }
-                        if (valid) {
-                            int np = lo_ + rb_;
-                            if (np < n) { lk[nxt * n + np] = key; li[nxt * n + np] = id; }
-                        }
-                        __syncwarp();
-                        cnt = min(cnt + __popc(bal), n);
-                        cur = nxt;
+                        const bool in = p < end && key < bkey;
+                        const unsigned bal = __ballot_sync(0xffffffffu, in);
+                        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                        if (in && pos < kCollect) { wk[pos] = key; wi[pos] = id; }
+                        cnt += __popc(bal);
                     }
                 }
-            if (cnt == n || all) break;
+            if (cnt > kCollect || cnt >= n || all) break;
             ++r;
+        }
+        const unsigned long long* rk;
+        const int* ri;
+        if (cnt > kCollect) {  // too many candidates to sort: stream them
+            __syncwarp();
+            const int cur = knn_stream<D>(g, xq, c0, r, n, cell_start, sorted_idx, sorted_X, wk,
+                                          wi, wk + 2 * n, wi + 2 * n);
+            rk = wk + cur * n;
+            ri = wi + cur * n;
+        } else {
+            int P = 32;
+            while (P < cnt) P <<= 1;
+            for (int e = cnt + lane; e < P; e += 32) { wk[e] = ~0ull; wi[e] = 0x7fffffff; }
+            __syncwarp();
+            for (int k = 2; k <= P; k <<= 1)  // bitonic sort, ascending
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const int lj = 31 - __clz(j);
+                    for (int t = lane; t < (P >> 1); t += 32) {
+                        const int i = ((t >> lj) << (lj + 1)) | (t & (j - 1));
+                        const int l = i + j;
+                        const unsigned long long ki = wk[i], kl = wk[l];
+                        const int ii = wi[i], il = wi[l];
+                        const bool up = (i & k) == 0;
+                        if (up ? key_less(kl, il, ki, ii) : key_less(ki, ii, kl, il)) {
+                            wk[i] = kl; wi[i] = il;
+                            wk[l] = ki; wi[l] = ii;
+                        }
+                    }
+                    __syncwarp();
+                }
+            rk = wk;
+            ri = wi;
         }
         // write the stencil (the first nq of the n nearest), its width and retention ball
         const int nq = node_n ? node_n[q] : n;
-        const double r2k = __longlong_as_double((long long)lk[cur * n + nq - 1]);
+        const double r2k = __longlong_as_double((long long)rk[nq - 1]);
         const double rball = __dmul_rn(omd2, r2k);
         int blen = 0;
         for (int t0 = 0; t0 < n; t0 += 32) {
-            int t = t0 + lane;
+            const int t = t0 + lane;
             bool inb = false;
             if (t < n) {
-                int id = li[cur * n + t];
-                double dd = __longlong_as_double((long long)lk[cur * n + t]);
+                const int id = ri[t];
+                const double dd = __longlong_as_double((long long)rk[t]);
                 nbr[(size_t)q * n + t] = id;
                 inb = t < nq && dd <= rball;
                 if (t >= 1 && dd == 0.0) set_error(ctr, RBFFD_EDUPLICATE);
@@ -335,13 +425,13 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
             blen += __popc(__ballot_sync(0xffffffffu, inb));
         }
         if (lane == 0) {
-            if (li[cur * n] != q) set_error(ctr, RBFFD_EDUPLICATE);
+            if (ri[0] != q) set_error(ctr, RBFFD_EDUPLICATE);
             rho2[q] = r2k;
             ball_len[q] = blen;
             atomicMax(&ctr->max_ball, blen);
         }
         for (int t = 1 + lane; t < blen; t += 32) {
-            int i = li[cur * n + t];
+            const int i = ri[t];
             if (i > q) atomicAdd(&indeg[i], 1);
         }
         __syncwarp();
@@ -395,7 +485,8 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     k_scan<int, int><<<1, 1024, 0, s>>>(count, start, ncell_max, &gp->ncell);
     k_cell_fill<D><<<nb, tb, 0, s>>>(X, N, cell_of, start, cursor, sorted_idx, sorted_X);
     const int wpb = 8;
-    size_t smem = (size_t)wpb * (2 * n + 32) * (sizeof(unsigned long long) + sizeof(int));
+    const int words = 2 * n + 32 > kCollect ? 2 * n + 32 : kCollect;  // knn_words(n)
+    size_t smem = (size_t)wpb * words * (sizeof(unsigned long long) + sizeof(int));
     int blocks = (N + wpb - 1) / wpb;
     k_knn<D><<<blocks, wpb * 32, smem, s>>>(X, N, n, omd2, gp, start, sorted_idx, sorted_X, nbr,
                                             rho2, ball_len, indeg, node_n, ctr);
