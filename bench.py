@@ -182,16 +182,23 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
 
     def one_step(detail=None, nodes=None, host_out=False):
+        # The sweep keeps its plans (and their CSR) on the device until every delta is
+        # assembled, so the host plans the next delta while the GPU assembles the current one.
         launches = 0
         alg = trav_ms = 0.0
         d2h = 0
+        plans = []
         for delta in deltas:
-            p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta)
+            p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta, sync=False)
             p.assemble()
             if host_out:
                 row_ptr, col, val, owner = p.export()
                 d2h += row_ptr.nbytes + col.nbytes + val.nbytes + owner.nbytes
+            plans.append((delta, p))
+        for delta, p in plans:
             st = p.stats()
+            if st["status"] != 0:
+                raise RuntimeError(f"delta {delta}: {R.rbffd_strerror(st['status'])}")
             launches += st["n_launches"]
             alg += st["alg_flops"]
             trav_ms += st["ms_traversal"]

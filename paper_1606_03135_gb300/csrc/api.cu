@@ -9,6 +9,7 @@
 
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "rbffd_internal.cuh"
 
@@ -108,6 +109,35 @@ int pool_for(int dev, cudaMemPool_t* out) {
     }
     *out = g_pool[dev];
     return RBFFD_OK;
+}
+
+// Timing events are recycled per device: creating eight events per plan would cost host time
+// while the GPU waits.  Events go back to the list only after their plan's stream is drained.
+std::mutex g_ev_mu;
+std::vector<cudaEvent_t> g_free_ev[kMaxDevices];
+
+int event_acquire(int dev, cudaEvent_t* e) {
+    if (dev < 0 || dev >= kMaxDevices) return RBFFD_ECUDA;
+    {
+        std::lock_guard<std::mutex> lock(g_ev_mu);
+        if (!g_free_ev[dev].empty()) {
+            *e = g_free_ev[dev].back();
+            g_free_ev[dev].pop_back();
+            return RBFFD_OK;
+        }
+    }
+    return bad(cudaEventCreate(e));
+}
+
+void event_release(int dev, cudaEvent_t e) {
+    if (dev >= 0 && dev < kMaxDevices) {
+        std::lock_guard<std::mutex> lock(g_ev_mu);
+        if (g_free_ev[dev].size() < 256) {
+            g_free_ev[dev].push_back(e);
+            return;
+        }
+    }
+    cudaEventDestroy(e);
 }
 
 // Lays several arrays out in one allocation, each on a 256-byte boundary.
@@ -225,7 +255,7 @@ void free_plan(rbffd_plan_s* p) {
     if (p->plan_block) cudaFreeAsync(p->plan_block, s);
     cudaStreamSynchronize(s);
     for (auto& e : p->ev)
-        if (e) cudaEventDestroy(e);
+        if (e) event_release(p->device, e);
     delete p;
 }
 
@@ -339,7 +369,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
     }
     p->basis_count = (int)basis_count;
     for (auto& e : p->ev)
-        if ((rc = bad(cudaEventCreate(&e))) != RBFFD_OK) goto fail;
+        if ((rc = event_acquire(p->device, &e)) != RBFFD_OK) goto fail;
     {
         Carver c;
         const size_t oX = c.add<double>((size_t)N * d), oN = c.add<int>((size_t)N * n),

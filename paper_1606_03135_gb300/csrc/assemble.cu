@@ -23,6 +23,8 @@
 // flattened over (row, column) pairs to keep lanes busy.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "fp64_int.cuh"
 #include "rbffd_internal.cuh"
 
@@ -420,20 +422,19 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
                 }
             }
             if (ok && swap_a != swap_b) {
-                // symmetric swap of unknowns ua < ub in the packed lower triangle
+                // symmetric swap of unknowns ua < ub in the packed lower triangle, one uniform
+                // loop per segment (row parts left of ua, the part between, the columns below
+                // ub, the right-hand-side rows, the diagonal pair)
                 const int ua = swap_a, ub = swap_b;
-                const int n1 = ua, n2 = ub - ua - 1, n3 = K - ub - 1, nq = q;
-                const int tot = n1 + n2 + n3 + nq + 1;
-                for (int e = lane; e < tot; e += 32) {
-                    double *x, *y;
-                    if (e < n1) { x = T + tri(ua) + e; y = T + tri(ub) + e; }
-                    else if (e < n1 + n2) { const int i = ua + 1 + (e - n1); x = T + tri(i) + ua; y = T + tri(ub) + i; }
-                    else if (e < n1 + n2 + n3) { const int i = ub + 1 + (e - n1 - n2); x = T + tri(i) + ua; y = T + tri(i) + ub; }
-                    else if (e < n1 + n2 + n3 + nq) { const int c = e - n1 - n2 - n3; x = X + ua * xs + c; y = X + ub * xs + c; }
-                    else { x = T + tri(ua) + ua; y = T + tri(ub) + ub; }
-                    const double t = *x; *x = *y; *y = t;
+                auto exch = [](double* x, double* y) { const double t = *x; *x = *y; *y = t; };
+                for (int e = lane; e < ua; e += 32) exch(T + tri(ua) + e, T + tri(ub) + e);
+                for (int i = ua + 1 + lane; i < ub; i += 32) exch(T + tri(i) + ua, T + tri(ub) + i);
+                for (int i = ub + 1 + lane; i < K; i += 32) exch(T + tri(i) + ua, T + tri(i) + ub);
+                for (int c = lane; c < q; c += 32) exch(X + ua * xs + c, X + ub * xs + c);
+                if (lane == 0) {
+                    exch(T + tri(ua) + ua, T + tri(ub) + ub);
+                    const int t = sm.perm[ua]; sm.perm[ua] = sm.perm[ub]; sm.perm[ub] = t;
                 }
-                if (lane == 0) { const int t = sm.perm[ua]; sm.perm[ua] = sm.perm[ub]; sm.perm[ub] = t; }
                 __syncwarp();
             }
             if (ok) {
@@ -927,16 +928,53 @@ static int sm_count() {
 
 // The dynamic shared-memory limit is a per-kernel setting shared by every host thread, so it
 // is always raised to the device maximum (never lowered to one plan's need): plans assembled
-// concurrently on other streams cannot undercut each other's launches.
+// concurrently on other streams cannot undercut each other's launches.  Raised once per
+// (device, kernel); occupancy answers are cached per (device, kernel, block, shared memory),
+// so planning does not repeat these driver queries while the GPU waits.
+namespace {
+struct SmemRaised { int dev; const void* k; };
+struct OccEntry { int dev; const void* k; int nt; size_t smem; int per_sm; };
+std::mutex g_attr_mu;
+SmemRaised g_raised[128];
+int g_n_raised = 0;
+OccEntry g_occ[512];
+int g_n_occ = 0;
+}  // namespace
+
 static cudaError_t allow_max_smem(const void* kern) {
     int dev = 0, mx = 0;
     cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    for (int i = 0; i < g_n_raised; ++i)
+        if (g_raised[i].dev == dev && g_raised[i].k == kern) return cudaSuccess;
     cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                mx - (int)fa.sharedSizeBytes);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             mx - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess && g_n_raised < 128) g_raised[g_n_raised++] = {dev, kern};
+    return e;
+}
+
+static cudaError_t occupancy(int* per_sm, const void* kern, int nt, size_t smem) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        for (int i = 0; i < g_n_occ; ++i)
+            if (g_occ[i].dev == dev && g_occ[i].k == kern && g_occ[i].nt == nt &&
+                g_occ[i].smem == smem) {
+                *per_sm = g_occ[i].per_sm;
+                return cudaSuccess;
+            }
+    }
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, nt, smem);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        if (g_n_occ < 512) g_occ[g_n_occ++] = {dev, kern, nt, smem, *per_sm};
+    }
+    return e;
 }
 
 // Resident CTAs per SM of the traversal kernel at team size nt (0 if nt has no instantiation
@@ -955,7 +993,7 @@ static int traversal_occupancy(int nt, size_t smem, int* per_sm) {
     }
     if (!k) return RBFFD_EINVAL;
     if (RB_CUDA(allow_max_smem(k)) ||
-        RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, nt, smem)) || *per_sm < 1)
+        RB_CUDA(occupancy(per_sm, k, nt, smem)) || *per_sm < 1)
         return RBFFD_EINVAL;
     return RBFFD_OK;
 }
@@ -966,7 +1004,7 @@ static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
     const void* k = nt == kMaxNT ? (const void*)k_fallback_solve<D, PACKED, kMaxNT>
                                  : (const void*)k_fallback_solve<D, PACKED, kNT>;
     if (RB_CUDA(allow_max_smem(k)) ||
-        RB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, nt, smem)) || *per_sm < 1)
+        RB_CUDA(occupancy(per_sm, k, nt, smem)) || *per_sm < 1)
         return RBFFD_EINVAL;
     return RBFFD_OK;
 }
