@@ -286,7 +286,7 @@ __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int S = sm.xs;
     const int Wd = K + q;
-    for (int r = tid; r < K; r += NT) sm.rowof[r] = r;
+    for (int r = tid; r < K; r += NT) { sm.rowof[r] = r; sm.perm[r] = r; }  // unknowns stay in place
     // the pivot search, row swap, reciprocal and multipliers are done by warp 0 alone (FP64
     // work counts per warp instruction, so the other warps must not repeat it)
     for (int p = 0; p < K; ++p) {
@@ -512,7 +512,40 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
         __syncthreads();
         p += kind;
     }
-    // D solve: 1x1 rows scale by the reciprocal pivot, 2x2 blocks multiply by their inverse
+    // The inverse permutation (read after the caller's next barrier).
+    for (int r = tid; r < K; r += NT) sm.rowof[sm.perm[r]] = r;
+    // D solve: 1x1 rows scale by the reciprocal pivot, 2x2 blocks multiply by their inverse;
+    // then back substitution with L^T: once x_i is final, x_j -= L[i][j] x_i for j < i.
+    // With at most one column per warp (q <= NW), warp w owns column w and its K sequential
+    // steps need only warp synchronisation; otherwise all threads share every step (the
+    // flattened (row, column) pairs keep the lanes busy) with a barrier per step.  Both do
+    // the same operations on every element.
+    constexpr int NW = NT / 32;
+    if (q <= NW) {
+        if (wid < q) {
+            double* Xc = X + wid;
+            for (int i = lane; i < K; i += 32) {
+                const int k = sm.pk[i];
+                double* Bi = Xc + i * xs;
+                if (k == 1) {
+                    *Bi *= sm.rdiag[i];
+                } else if (k == 2) {  // rows i, i + 1 form a 2x2 block
+                    double* Bn = Bi + xs;
+                    const double y0 = *Bi, y1 = *Bn;
+                    *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
+                    *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
+                }
+            }
+            __syncwarp();
+            for (int i = K - 1; i > 0; --i) {
+                const double* Li = T + tri(i);
+                const double xv = Xc[i * xs];
+                for (int jj = lane; jj < i; jj += 32) Xc[jj * xs] = fma(-Li[jj], xv, Xc[jj * xs]);
+                __syncwarp();
+            }
+        }
+        return true;
+    }
     for (int e = tid; e < K * q; e += NT) {
         const int i = e / q, c = e - (e / q) * q;
         const int k = sm.pk[i];
@@ -527,7 +560,6 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
         }
     }
     __syncthreads();
-    // back substitution with L^T: once x_i is final, x_j -= L[i][j] x_i for j < i
     for (int i = K - 1; i > 0; --i) {
         const int total = i * q;
         if (tid < total) {
@@ -546,8 +578,6 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
         }
         __syncthreads();
     }
-    for (int r = tid; r < K; r += NT) sm.rowof[sm.perm[r]] = r;
-    __syncthreads();
     return true;
 }
 
@@ -558,13 +588,18 @@ __device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
     return PACKED ? factor_solve_ldlt<NT>(sh.K, q, sm) : factor_solve_lu<NT>(sh.K, q, sm);
 }
 
-// Local L-Lebesgue value sum_r |w_r| of every solved column (one warp per column).
+// Local L-Lebesgue value sum_r |w_r| of every solved column: warp w sums the columns w, w + NW,
+// ... (the columns it back-substituted), over the unknowns u whose original index perm[u] is
+// a stencil node (not a polynomial coefficient).
 template <int NT>
-__device__ __forceinline__ void lebesgue_values(int n, int q, const StencilSmem& sm) {
+__device__ __forceinline__ void lebesgue_values(int n, int K, int q, const StencilSmem& sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = wid; c < q; c += (NT / 32)) {
         double s = 0.0;
-        for (int r = lane; r < n; r += 32) s += fabs(sm.X[sm.rowof[r] * sm.xs + c]);
+        for (int u = lane; u < K; u += 32) {
+            const double v = sm.X[u * sm.xs + c];
+            s += sm.perm[u] < n ? fabs(v) : 0.0;
+        }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) sm.lam[c] = s;
     }
@@ -703,7 +738,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
         __syncthreads();
         const int q = s_q;
         const bool ok = solve_local<D, PACKED, NT>(a, sh, j, q, sm);
-        if (ok) lebesgue_values<NT>(n, q, sm);
+        if (ok) lebesgue_values<NT>(n, sh.K, q, sm);
         __syncthreads();
         // Lebesgue test (§4.2.1) per column
         const long long base = a.slot_off[j];
@@ -809,7 +844,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
         if (tid == 0) sm.cols[0] = 0;
         __syncthreads();
         const bool ok = solve_local<D, PACKED, NT>(a, sh, i, 1, sm);
-        if (ok) lebesgue_values<NT>(sh.n, 1, sm);
+        if (ok) lebesgue_values<NT>(sh.n, sh.K, 1, sm);
         __syncthreads();
         double r2c = a.rho2[i];
         if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
