@@ -39,7 +39,7 @@ constexpr int kMaxNT = 512;  // largest team (big systems, when few fit in share
 // CTAs per SM the register allocation must allow for a team size (the shared-memory limit of
 // small systems): 40 registers for 96- and 128-thread teams, 64 for 32- and 64-thread teams.
 __host__ __device__ constexpr int team_min_blocks(int nt) {
-    return nt == 32 ? 32 : (nt == 64 ? 16 : (nt == 96 ? 17 : (nt == 128 ? 12 : 1)));
+    return nt == 32 ? 32 : (nt == 64 ? 16 : (nt == 96 ? 16 : (nt == 128 ? 12 : 1)));
 }
 
 // Per-CTA shared-memory views of one local system.  Two layouts:
@@ -380,12 +380,28 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
     int p = 0;
     while (p < K) {
         if (wid == 0) {
+            // The lane's first two entries of the pivot column and the reciprocal of the
+            // diagonal, in one straight-line block so the reciprocal's integer chain overlaps
+            // the loads and the search; the usual 1x1 step without a swap then scales these
+            // registers directly.
+            const double dpp = T[tri(p) + p];
+            const int i0 = p + 1 + lane, i1 = i0 + 32;
+            const double w0 = i0 < K ? T[tri(i0) + p] : 0.0;
+            const double w1 = i1 < K ? T[tri(i1) + p] : 0.0;
+            bool slow;
+            const double rcp_p = rcp_core(dpp, &slow);
             // lambda = max |A[i][p]|, i > p, on magnitude keys (the top 32 bits of |A[i][p]|,
             // an order-preserving truncation), lowest index among equal keys; two warp
             // reductions instead of a shuffle tree
             unsigned lk = 0u;
             int r = 0x7fffffff;
-            for (int i = p + 1 + lane; i < K; i += 32) {
+            {
+                const unsigned k0 = i0 < K ? mag_key(w0) : 0u;
+                const unsigned k1 = i1 < K ? mag_key(w1) : 0u;
+                if (k0 > lk) { lk = k0; r = i0; }
+                if (k1 > lk) { lk = k1; r = i1; }
+            }
+            for (int i = i1 + 32; i < K; i += 32) {  // columns longer than 64
                 const unsigned v = mag_key(T[tri(i) + p]);
                 if (v > lk) { lk = v; r = i; }
             }
@@ -395,7 +411,7 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
             const unsigned long long lv = (unsigned long long)lmax << 32;
             // the pivot choice only has to be a valid Bunch-Kaufman choice, so the tests run in
             // FP32 on values rebuilt from the FP64 bit patterns (no FP64 instructions)
-            const unsigned long long pv = abs_bits(T[tri(p) + p]);
+            const unsigned long long pv = abs_bits(dpp);
             const float lam = approx_f32(lv), app = approx_f32(pv);
             const float af = 0.6403882f;
             int kind = 1, swap_a = p, swap_b = p;
@@ -438,7 +454,17 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
                 __syncwarp();
             }
             if (ok) {
-                if (kind == 1) {
+                if (kind == 1 && swap_a == swap_b && !slow) {  // the usual step: all in registers
+                    if (lane == 0) { sm.rdiag[p] = rcp_p; sm.pk[p] = 1; }
+                    const double s0 = w0 * rcp_p, s1 = w1 * rcp_p;
+                    if (i0 < K) { sm.wv[i0] = w0; T[tri(i0) + p] = s0; }
+                    if (i1 < K) { sm.wv[i1] = w1; T[tri(i1) + p] = s1; }
+                    for (int i = i1 + 32; i < K; i += 32) {
+                        const double w = T[tri(i) + p];
+                        sm.wv[i] = w;
+                        T[tri(i) + p] = w * rcp_p;
+                    }
+                } else if (kind == 1) {  // after a swap (or an extreme pivot): reload
                     const double rcp = rcp_fixed(T[tri(p) + p]);
                     if (lane == 0) { sm.rdiag[p] = rcp; sm.pk[p] = 1; }
                     for (int i = p + 1 + lane; i < K; i += 32) {

@@ -17,39 +17,47 @@ __device__ __forceinline__ double exact_double(int v) {
     return __longlong_as_double((long long)(((unsigned long long)(1023 + e) << 52) | mant));
 }
 
-// Reciprocal of an FP64 value computed on the integer pipe (GB300's FP64 pipe is ~1/64 of its
-// FP32 rate, and a scalar division issued by one warp occupies it as a full warp
-// instruction): a 24-bit FP32 seed refined by two Newton-Raphson steps t' = t + t (1 - m t)
-// on the mantissa m in 64-bit fixed point, then rounded to 53 bits.  Within 1 ulp of 1/x
-// for normal x; zero, subnormal and near-overflow inputs use the FP64 division.
-__device__ __forceinline__ double rcp_fixed(double x) {
+// Reciprocal of an FP64 value on the integer pipe (GB300's FP64 pipe is ~1/64 of its FP32
+// rate, and a scalar division issued by one warp occupies it as a full warp instruction).
+// rcp_core covers normal x whose reciprocal is normal (biased exponent in [1, 0x7fc]) and
+// sets *slow for every other input; it has no branches, so the compiler can interleave it
+// with independent work.  A 24-bit FP32 seed t0 of 1/m for the mantissa m is refined by one
+// cubic Newton-Raphson step t1 = t0 (1 + e + e^2), e = 1 - m t0, in 64-bit fixed point
+// (error about e^3, below 2^-62), then rounded to 53 bits: within 1 ulp of 1/x.  Powers of
+// two are exact.
+__device__ __forceinline__ double rcp_core(double x, bool* slow) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned long long sign = b >> 63;
     const int e = (int)((b >> 52) & 0x7ff);
     const unsigned long long f = b & 0xFFFFFFFFFFFFFull;
-    if (e == 0 || e >= 0x7fd) return 1.0 / x;
-    if (f == 0)  // a power of two: exact
-        return __longlong_as_double((long long)((sign << 63) | ((unsigned long long)(2046 - e) << 52)));
+    *slow = (e == 0) | (e >= 0x7fd);
     const unsigned long long M = f | (1ull << 52);  // m = M / 2^52 in [1, 2)
-    const float rf = __frcp_rn(__int_as_float(0x3F800000 | (int)(f >> 29)));
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(0x3F800000 | (int)(f >> 29))));
     const unsigned rb = __float_as_uint(rf);
-    unsigned long long Y =  // Y = t * 2^64, t = 1/m in (1/2, 1]
+    unsigned long long Y =  // Y = t0 2^64, t0 in (1/2, 1]
         rb >= 0x3F800000u ? ~0ull : (unsigned long long)((rb & 0x7FFFFFu) | 0x800000u) << 40;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const unsigned long long lo = M * Y, hi = __umul64hi(M, Y);   // P = M Y
-        const unsigned long long H = (1ull << 52) - hi - (lo != 0ull);  // 2^116 - P, high part
-        const unsigned long long L = 0ull - lo;
-        const long long Dv = (long long)((H << 12) | (L >> 52));  // 2^64 (1 - m t)
-        const unsigned long long C = Dv >= 0 ? __umul64hi(Y, (unsigned long long)Dv)
-                                              : 0ull - __umul64hi(Y, (unsigned long long)(-Dv));
-        Y += C;
-    }
+    const unsigned long long lo = M * Y, hi = __umul64hi(M, Y);    // P = M Y = m t0 2^116
+    const unsigned long long H = (1ull << 52) - hi - (lo != 0ull);  // 2^116 - P, high part
+    const long long Dv = (long long)((H << 12) | ((0ull - lo) >> 52));  // 2^64 e
+    const unsigned long long aD = Dv >= 0 ? (unsigned long long)Dv : 0ull - (unsigned long long)Dv;
+    const long long S = Dv + (long long)__umul64hi(aD, aD);        // 2^64 (e + e^2)
+    const unsigned long long aS = S >= 0 ? (unsigned long long)S : 0ull - (unsigned long long)S;
+    const unsigned long long C = __umul64hi(Y, aS);
+    Y = S >= 0 ? Y + C : Y - C;
     unsigned long long m53 = (Y + (1ull << 10)) >> 11;
-    int ex = 1022 - (e - 1023);
-    if (m53 >> 53) { m53 >>= 1; ++ex; }
-    return __longlong_as_double(
-        (long long)((sign << 63) | ((unsigned long long)ex << 52) | (m53 & 0xFFFFFFFFFFFFFull)));
+    const int ov = (int)(m53 >> 53);
+    m53 >>= ov;
+    const unsigned long long ex = (unsigned long long)(1022 - (e - 1023) + ov);
+    const unsigned long long nb = (sign << 63) | (ex << 52) | (m53 & 0xFFFFFFFFFFFFFull);
+    const unsigned long long pb = (sign << 63) | ((unsigned long long)(2046 - e) << 52);
+    return __longlong_as_double((long long)(f == 0ull ? pb : nb));
+}
+
+__device__ __forceinline__ double rcp_fixed(double x) {
+    bool slow;
+    const double r = rcp_core(x, &slow);
+    return slow ? 1.0 / x : r;
 }
 
 // Square root of an FP64 value with three FP64 instructions.  A 24-bit seed y0 of 1/sqrt(m)
