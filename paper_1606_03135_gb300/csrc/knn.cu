@@ -208,10 +208,12 @@ __device__ __forceinline__ bool key_less(unsigned long long ka, int ia, unsigned
 }
 
 // Search box of ring r around the query's cell and the squared radius that no point outside
-// the box can reach (+inf when the box covers the whole grid).
+// the box can reach (+inf when the box covers the whole grid).  (The query's exact distance to
+// the box faces is larger, but admitting more candidates only makes the sort dearer.)
 template <int D>
-__device__ __forceinline__ bool ring_box(const GridParams& g, const int* c0, int r, int* clo,
-                                         int* chi, unsigned long long* bkey) {
+__device__ __forceinline__ bool ring_box(const GridParams& g, const double* xq, const int* c0,
+                                         int r, int* clo, int* chi, unsigned long long* bkey) {
+    (void)xq;
     bool all = true;
     for (int a = 0; a < D; ++a) {
         clo[a] = max(c0[a] - r, 0);
@@ -222,6 +224,32 @@ __device__ __forceinline__ bool ring_box(const GridParams& g, const int* c0, int
     *bkey = dkey(all ? __longlong_as_double(0x7ff0000000000000LL)  // +inf
                      : rb * rb * (1.0 - 1e-8));
     return all;
+}
+
+// First ring to search for a query: the radius that holds n nodes at the density of the
+// 3^d cells around the query's cell, rounded up to whole cells (never below 1).  In dense
+// clusters this keeps the box small; the search grows it when too few nodes lie inside.
+template <int D>
+__device__ __forceinline__ int first_ring(const GridParams& g, const int* c0, int n,
+                                          const int* __restrict__ cell_start) {
+    int lo[3], hi[3];
+    for (int a = 0; a < D; ++a) {
+        lo[a] = max(c0[a] - 1, 0);
+        hi[a] = min(c0[a] + 1, g.dims[a] - 1);
+    }
+    int cnt = 0, cells = 0;
+    const int nz = (D == 3) ? hi[2] - lo[2] + 1 : 1;
+    for (int rz = 0; rz < nz; ++rz)
+        for (int ry = lo[1]; ry <= hi[1]; ++ry) {
+            int cc[3] = {lo[0], ry, (D == 3) ? lo[2] + rz : 0};
+            const int row0 = cell_index<D>(g, cc);
+            cnt += cell_start[row0 + (hi[0] - lo[0]) + 1] - cell_start[row0];
+            cells += hi[0] - lo[0] + 1;
+        }
+    const float per = fmaxf((float)cnt / (float)cells, 0.05f);  // nodes per cell
+    const float vol = (D == 2) ? 3.14159265f : 4.18879020f;
+    const float rad = (D == 2) ? sqrtf((float)n / (per * vol)) : cbrtf((float)n / (per * vol));
+    return max(1, (int)ceilf(rad));
 }
 
 // Streaming search (any number of candidates): the warp keeps the n best candidates seen so
@@ -238,7 +266,7 @@ __device__ int knn_stream(const GridParams& g, const double* xq, const int* c0, 
     for (;;) {
         int clo[3], chi[3];
         unsigned long long bkey;
-        const bool all = ring_box<D>(g, c0, r, clo, chi, &bkey);
+        const bool all = ring_box<D>(g, xq, c0, r, clo, chi, &bkey);
         cnt = 0;
         cur = 0;
         const int ny = chi[1] - clo[1] + 1;
@@ -307,12 +335,13 @@ __device__ int knn_stream(const GridParams& g, const double* xq, const int* c0, 
 // One warp per query node.  Usual case: every candidate of the search box that lies inside
 // the guaranteed radius is collected into shared memory (growing the ring until there are n),
 // and the warp sorts them by (IEEE bits of d2, index) with a bitonic network; the first n
-// are the stencil.  Boxes with more than kCollect such candidates (strongly clustered nodes)
-// take the streaming search instead.  Either way the order is exact.
-constexpr int kCollect = 256;
+// are the stencil.  Boxes with more such candidates than the buffer holds (256, or 512 for
+// stencils of more than 64 nodes) take the streaming search instead.  Either way the order is
+// exact.
+__host__ __device__ __forceinline__ int knn_collect_cap(int n) { return n > 64 ? 512 : 256; }
 
-__device__ __forceinline__ int knn_words(int n) {  // per-warp buffer entries
-    return max(2 * n + 32, kCollect);
+__host__ __device__ __forceinline__ int knn_words(int n) {  // per-warp buffer entries
+    return max(2 * n + 32, knn_collect_cap(n));
 }
 
 template <int D>
@@ -340,12 +369,13 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
             xq[a] = X[(size_t)q * D + a];
             c0[a] = cell_coord<D>(g, xq[a], a);
         }
-        int r = g.r0, cnt = 0;
+        const int kCollect = knn_collect_cap(n);
+        int r = first_ring<D>(g, c0, n, cell_start), cnt = 0;
         bool all = false;
         for (;;) {  // collect the candidates inside the guaranteed radius of ring r
             int clo[3], chi[3];
             unsigned long long bkey;
-            all = ring_box<D>(g, c0, r, clo, chi, &bkey);
+            all = ring_box<D>(g, xq, c0, r, clo, chi, &bkey);
             cnt = 0;
             const int ny = chi[1] - clo[1] + 1;
             const int nz = (D == 3) ? chi[2] - clo[2] + 1 : 1;
@@ -485,8 +515,12 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     k_scan<int, int><<<1, 1024, 0, s>>>(count, start, ncell_max, &gp->ncell);
     k_cell_fill<D><<<nb, tb, 0, s>>>(X, N, cell_of, start, cursor, sorted_idx, sorted_X);
     const int wpb = 8;
-    const int words = 2 * n + 32 > kCollect ? 2 * n + 32 : kCollect;  // knn_words(n)
+    const int words = knn_words(n);
     size_t smem = (size_t)wpb * words * (sizeof(unsigned long long) + sizeof(int));
+    if (smem > 48 * 1024 &&
+        (rc = RB_CUDA(cudaFuncSetAttribute(k_knn<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem))))
+        return rc;
     int blocks = (N + wpb - 1) / wpb;
     k_knn<D><<<blocks, wpb * 32, smem, s>>>(X, N, n, omd2, gp, start, sorted_idx, sorted_X, nbr,
                                             rho2, ball_len, indeg, node_n, ctr);
