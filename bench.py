@@ -314,8 +314,12 @@ def run_mixed(args):
     delta = w["deltas"][0]
     stream = torch.cuda.current_stream()
 
+    # schedule picked by the autotuner on this node set (untimed, like a library's heuristics)
+    sched, sched_ms = R.autotune(Xd, n_node, ell_node, m_node, delta, mode=R.STAB_FALLBACK,
+                                 repeats=1)
+
     def step():
-        p = R.Plan(Xd, n_node, ell_node, m_node, delta, mode=R.STAB_FALLBACK)
+        p = R.Plan(Xd, n_node, ell_node, m_node, delta, mode=R.STAB_FALLBACK, **sched)
         p.assemble()
         st = p.stats()
         p.close()
@@ -349,6 +353,31 @@ def run_mixed(args):
             "stats": {k: st[k] for k in ("n_centers", "n_fallback", "n_rejected", "sum_cols",
                                          "max_ball", "nnz", "ms_stencils", "ms_traversal",
                                          "ms_fallback", "ms_finalize")}}
+    # the assembly as one captured CUDA graph (plan outside the graph), replayed
+    with R.Plan(Xd, n_node, ell_node, m_node, delta, mode=R.STAB_FALLBACK, sync=False,
+                **sched) as p:
+        p.assemble()
+        torch.cuda.synchronize()
+        g = p.capture_assemble()
+        g.replay()
+        torch.cuda.synchronize()
+        gs = torch.cuda.Stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(gs):
+            e0.record(gs)
+            for _ in range(args.steps):
+                g.replay()
+            e1.record(gs)
+        torch.cuda.synchronize()
+        rep_ms = e0.elapsed_time(e1) / args.steps
+        gst = p.stats()
+        if gst["status"] != 0:
+            raise RuntimeError(f"graph replay: {R.rbffd_strerror(gst['status'])}")
+    line["schedule"] = {"autotuned": {k: int(v) for k, v in sched.items()},
+                        "candidates_ms": {str(dict(k)): round(v, 3) for k, v in sched_ms.items()}}
+    line["graph_replay"] = {"ms_per_assembly": rep_ms, "assemble_rows_per_s": N / (rep_ms / 1e3),
+                            "eager_assemble_ms": st["ms_traversal"] + st["ms_fallback"]
+                            + st["ms_finalize"]}
     print(json.dumps(line), flush=True)
     return 0
 

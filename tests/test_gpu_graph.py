@@ -37,3 +37,24 @@ def test_graph_replay_reforms_the_matrix(mode):
                 assert np.array_equal(a, b)
             st = p.stats()
             assert st["status"] == 0 and st["n_centers"] == st0["n_centers"]
+
+
+def test_graph_replay_of_a_mixed_degree_plan_with_fallback():
+    """Per-node stencils in FALLBACK mode: the traversal and the per-class fallback launches
+    replay from one graph and rebuild the same matrix."""
+    X = NS.cube3d_clustered(3000, seed=4)
+    nn, ee, mm = NS.mixed_degree_params(X)
+    with R.Plan(torch.from_numpy(X).cuda(), nn, ee, mm, 0.3, mode=R.STAB_FALLBACK,
+                sync=False) as p:
+        csr = p.assemble()
+        torch.cuda.synchronize()
+        ref = p.export()
+        g = p.capture_assemble()
+        torch.cuda.synchronize()
+        _memset_device(csr.val, int(ref[0][-1]) * 8)
+        g.replay()
+        torch.cuda.synchronize()
+        got = p.export()
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b)
+        assert p.stats()["status"] == 0
