@@ -19,7 +19,7 @@ SRC = os.path.join(HERE, "rbffd_oracle.c")
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 OK, EINVAL, EDUPLICATE, ENOMEM, ESINGULAR = 0, -1, -2, -3, -4
-OP_LAPLACIAN, OP_IDENTITY = 0, 1
+OP_LAPLACIAN, OP_IDENTITY, OP_NORMAL = 0, 1, 2
 STAB_SEQ, STAB_OFF, STAB_FALLBACK = 0, 1, 2
 
 _lock = threading.Lock()
@@ -43,7 +43,7 @@ class Stats(C.Structure):
     _fields_ = [("n_centers", C.c_int64), ("n_fallback", C.c_int64),
                 ("n_decisions", C.c_int64), ("n_rejected", C.c_int64),
                 ("n_near_tie", C.c_int64), ("sum_q", C.c_int64), ("sum_cols", C.c_int64),
-                ("min_abs_margin", C.c_double)]
+                ("min_abs_margin", C.c_double), ("n_boundary", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -65,6 +65,11 @@ def lib():
             L.ora_assemble.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
                                        C.c_double, C.c_int, P, P, P, P, P, P, P, P,
                                        C.POINTER(Stats)]
+            L.ora_local_weights_dn.argtypes = [P, C.c_int, P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                               P, P, C.c_int, P, P]
+            L.ora_assemble_bc.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
+                                          C.c_double, C.c_int, P, P, P, P, P, P, P, P, P, P,
+                                          C.POINTER(Stats)]
             L.ora_assemble_mixed.argtypes = [P, C.c_int64, C.c_int, P, P, P, C.c_int,
                                              C.c_double, C.c_int, P, P, P, P, P, P, P, P,
                                              C.POINTER(Stats)]
@@ -136,9 +141,26 @@ def local_weights(X, idx, ell, m, Y, op=OP_LAPLACIAN):
     return W, lam
 
 
-def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None):
+def normal_weights(X, idx, ell, m, nrm):
+    """Weights W [n] of stencil X[idx] for the derivative along the unit vector nrm at the
+    center X[idx[0]] (the Neumann operator), and the scaled local Lebesgue value."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    d = X.shape[1]
+    n = idx.size
+    Y = np.ascontiguousarray(X[idx[0]][None, :])
+    Nr = np.ascontiguousarray(np.asarray(nrm, dtype=np.float64).reshape(1, d))
+    W = np.zeros(n, dtype=np.float64)
+    lam = np.zeros(1, dtype=np.float64)
+    _check(lib().ora_local_weights_dn(_ptr(X), d, _ptr(idx), n, ell, m, OP_NORMAL, _ptr(Y),
+                                      _ptr(Nr), 1, _ptr(W), _ptr(lam)), "local_weights_dn")
+    return W, lam[0]
+
+
+def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None, bc=None, normals=None):
     """The whole sequential construction of L.  Returns a dict with CSR arrays (row_ptr, col,
-    val), owner, is_center, lam_row, stats and the kNN table used."""
+    val), owner, is_center, lam_row, stats and the kNN table used.  bc (uint8 [N]: 0
+    interior, 1 Dirichlet, 2 Neumann) and normals ([N][d]) add the boundary rows of §5."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     N, d = X.shape
     if nbr is None or d2 is None:
@@ -150,11 +172,13 @@ def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None):
     is_center = np.zeros(N, dtype=np.uint8)
     lam_row = np.zeros(N, dtype=np.float64)
     st = Stats()
-    _check(lib().ora_assemble(_ptr(X), N, d, n, ell, m, float(delta), mode,
-                              _ptr(np.ascontiguousarray(nbr, dtype=np.int32)),
-                              _ptr(np.ascontiguousarray(d2, dtype=np.float64)),
-                              _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(owner),
-                              _ptr(is_center), _ptr(lam_row), C.byref(st)), "assemble")
+    bcv = None if bc is None else np.ascontiguousarray(bc, dtype=np.uint8)
+    nrv = None if normals is None else np.ascontiguousarray(normals, dtype=np.float64)
+    _check(lib().ora_assemble_bc(_ptr(X), N, d, n, ell, m, float(delta), mode, _ptr(bcv),
+                                 _ptr(nrv), _ptr(np.ascontiguousarray(nbr, dtype=np.int32)),
+                                 _ptr(np.ascontiguousarray(d2, dtype=np.float64)),
+                                 _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(owner),
+                                 _ptr(is_center), _ptr(lam_row), C.byref(st)), "assemble")
     return dict(row_ptr=row_ptr, col=col, val=val, owner=owner, is_center=is_center,
                 lam_row=lam_row, stats=st.as_dict(), nbr=nbr, d2=d2)
 

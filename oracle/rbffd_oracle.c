@@ -120,6 +120,18 @@ static double lap_mono(const double* x, const int* alpha, int d) {
     return s;
 }
 
+/* Directional derivative of psi along nrm: sum_a nrm_a alpha_a x^(alpha - e_a) */
+static double dn_mono(const double* x, const int* alpha, const double* nrm, int d) {
+    double s = 0.0;
+    for (int a = 0; a < d; ++a) {
+        if (alpha[a] < 1) continue;
+        double p = (double)alpha[a];
+        for (int b = 0; b < d; ++b) p = p * ipow(x[b], b == a ? alpha[b] - 1 : alpha[b]);
+        s = s + nrm[a] * p;
+    }
+    return s;
+}
+
 /* ---------------------------------------------------------------- §2/§4.1 kNN */
 
 int ora_knn(const double* X, int64_t N, int d, int n, int32_t* nbr, double* d2) {
@@ -214,7 +226,18 @@ static void lu_solve(const double* A, int K, const int* piv, double* b) {
  * of the original one times rho^2 for the Laplacian (rho^0 for the identity). */
 int ora_local_weights(const double* X, int d, const int32_t* idx, int n, int ell, int m, int op,
                       const double* Y, int q, double* W, double* lam) {
-    if ((d != 2 && d != 3) || n < 1 || q < 0 || m < 3 || (m % 2) == 0 || ell < 0)
+    if (op == ORA_OP_NORMAL) return ORA_EINVAL;  /* needs normals: ora_local_weights_dn */
+    return ora_local_weights_dn(X, d, idx, n, ell, m, op, Y, NULL, q, W, lam);
+}
+
+/* The same with the operator ORA_OP_NORMAL allowed: the derivative along the unit vector
+ * Nrm[e] at evaluation point e (§5, the Neumann operator of the boundary condition).  For
+ * it the weights of the scaled problem are those of the original one times rho. */
+int ora_local_weights_dn(const double* X, int d, const int32_t* idx, int n, int ell, int m,
+                         int op, const double* Y, const double* Nrm, int q, double* W,
+                         double* lam) {
+    if ((d != 2 && d != 3) || n < 1 || q < 0 || m < 3 || (m % 2) == 0 || ell < 0 ||
+        op < ORA_OP_LAPLACIAN || op > ORA_OP_NORMAL || (op == ORA_OP_NORMAL && !Nrm))
         return ORA_EINVAL;
     int M = ora_poly_terms(d, ell, NULL);
     if (M > n) return ORA_EINVAL;
@@ -262,15 +285,24 @@ int ora_local_weights(const double* X, int d, const int32_t* idx, int n, int ell
             double r2 = sqdist(eta + e * d, xi + j * d, d);
             double r = sqrt(r2);
             double v;
-            if (op == ORA_OP_LAPLACIAN)  /* Laplacian of r^m in d dims: m(m+d-2) r^(m-2) */
+            if (op == ORA_OP_LAPLACIAN) {  /* Laplacian of r^m in d dims: m(m+d-2) r^(m-2) */
                 v = (double)(m * (m + d - 2)) * odd_power(r, r2, m - 2);
-            else
+            } else if (op == ORA_OP_NORMAL) {  /* d/dn r^m = m r^(m-2) (y - xi_j) . n */
+                double dot = 0.0;
+                for (int a = 0; a < d; ++a) dot = dot + (eta[e * d + a] - xi[j * d + a]) * Nrm[e * d + a];
+                v = (double)m * odd_power(r, r2, m - 2) * dot;
+            } else {
                 v = odd_power(r, r2, m);
+            }
             B[j * q + e] = v;
         }
-        for (int l = 0; l < M; ++l)
-            B[(n + l) * q + e] = (op == ORA_OP_LAPLACIAN) ? lap_mono(eta + e * d, alpha + l * d, d)
-                                                           : mono(eta + e * d, alpha + l * d, d);
+        for (int l = 0; l < M; ++l) {
+            double v;
+            if (op == ORA_OP_LAPLACIAN) v = lap_mono(eta + e * d, alpha + l * d, d);
+            else if (op == ORA_OP_NORMAL) v = dn_mono(eta + e * d, alpha + l * d, Nrm + e * d, d);
+            else v = mono(eta + e * d, alpha + l * d, d);
+            B[(n + l) * q + e] = v;
+        }
     }
 
     rc = lu_factor(A, K, piv);
@@ -281,7 +313,8 @@ int ora_local_weights(const double* X, int d, const int32_t* idx, int n, int ell
         double s = 0.0;
         for (int j = 0; j < n; ++j) {
             s = s + fabs(col[j]);
-            W[j * q + e] = (op == ORA_OP_LAPLACIAN) ? col[j] / rho2 : col[j];
+            W[j * q + e] = (op == ORA_OP_LAPLACIAN) ? col[j] / rho2
+                         : (op == ORA_OP_NORMAL) ? col[j] / rho : col[j];
         }
         if (lam) lam[e] = s;
     }
@@ -330,6 +363,21 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
                  const int32_t* nbr, const double* d2, int64_t* row_ptr, int32_t* col,
                  double* val, int32_t* owner, uint8_t* is_center, double* lam_row,
                  ora_stats* st) {
+    return ora_assemble_bc(X, N, d, n, ell, m, delta, mode, NULL, NULL, nbr, d2, row_ptr, col,
+                           val, owner, is_center, lam_row, st);
+}
+
+/* Boundary nodes (§5): bc[i] = 1 (Dirichlet) or 2 (Neumann), 0 for interior nodes.  The
+ * overlapped traversal runs over the interior only: a boundary node is never a center of
+ * it and never a member of a retention set, so its row is never produced by an interior
+ * stencil (the interior block of N_delta = (N_i)_delta + N_b).  Each boundary node then
+ * gets its own row B from its own stencil: the identity for Dirichlet (B_bb = I, B_bi = 0),
+ * the derivative along its unit normal nrm[i] for Neumann.  Boundary rows have is_center
+ * = 3 and are their own owners. */
+int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, double delta,
+                    int mode, const uint8_t* bc, const double* nrm, const int32_t* nbr,
+                    const double* d2, int64_t* row_ptr, int32_t* col, double* val,
+                    int32_t* owner, uint8_t* is_center, double* lam_row, ora_stats* st) {
     if (N < 1 || n < 1 || n > N || (d != 2 && d != 3) || m < 3 || (m % 2) == 0 ||
         !(delta > 0.0 && delta <= 1.0) || mode < 0 || mode > 2)
         return ORA_EINVAL;
@@ -350,14 +398,19 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
     if (!ball || !covered || !redo || !Y || !W || !lam || !cols) { rc = ORA_ENOMEM; goto done; }
     rc = ora_ball_len(d2, N, n, delta, ball);
     if (rc != ORA_OK) goto done;
-    for (int64_t i = 0; i < N; ++i) { owner[i] = -1; is_center[i] = 0; }
+    for (int64_t i = 0; i < N; ++i) {
+        owner[i] = -1;
+        is_center[i] = 0;
+        if (bc && bc[i] > 2) { rc = ORA_EINVAL; goto done; }
+        if (bc && bc[i] == 2 && !nrm) { rc = ORA_EINVAL; goto done; }
+    }
 
     for (int64_t k = 0; k < N; ++k) {
-        if (covered[k]) continue;
+        if (covered[k] || (bc && bc[k])) continue;
         const int32_t* I = nbr + k * n;
         int q = 0;
-        for (int t = 0; t < ball[k]; ++t)
-            if (!covered[I[t]]) cols[q++] = t; /* t = 0 is k itself, never covered here */
+        for (int t = 0; t < ball[k]; ++t) /* t = 0 is k itself, never covered here */
+            if (!covered[I[t]] && !(bc && bc[I[t]])) cols[q++] = t;
         for (int e = 0; e < q; ++e)
             for (int a = 0; a < d; ++a) Y[e * d + a] = X[(int64_t)I[cols[e]] * d + a];
         rc = ora_local_weights(X, d, I, n, ell, m, ORA_OP_LAPLACIAN, Y, q, W, lam);
@@ -398,6 +451,24 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
             if (lam_row) lam_row[i] = lam[0];
             put_row(i, n, I, W, 1, col, val);
         }
+    }
+    for (int64_t i = 0; bc && i < N; ++i) {
+        if (!bc[i]) continue;
+        const int32_t* I = nbr + i * n;
+        if (bc[i] == 1) {  /* identity row */
+            for (int j = 0; j < n; ++j) W[j] = (j == 0) ? 1.0 : 0.0;
+            lam[0] = 1.0;
+        } else {
+            rc = ora_local_weights_dn(X, d, I, n, ell, m, ORA_OP_NORMAL, X + i * d, nrm + i * d, 1,
+                                      W, lam);
+            if (rc != ORA_OK) goto done;
+            s0.sum_cols++;
+        }
+        owner[i] = (int32_t)i;
+        is_center[i] = 3;
+        s0.n_boundary++;
+        if (lam_row) lam_row[i] = lam[0];
+        put_row(i, n, I, W, 1, col, val);
     }
     for (int64_t i = 0; i <= N; ++i) row_ptr[i] = i * n;
 done:

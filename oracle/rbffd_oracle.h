@@ -19,7 +19,7 @@ extern "C" {
 #endif
 
 enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_EDUPLICATE = -2, ORA_ENOMEM = -3, ORA_ESINGULAR = -4 };
-enum { ORA_OP_LAPLACIAN = 0, ORA_OP_IDENTITY = 1 };
+enum { ORA_OP_LAPLACIAN = 0, ORA_OP_IDENTITY = 1, ORA_OP_NORMAL = 2 };
 enum { ORA_STAB_SEQ = 0, ORA_STAB_OFF = 1, ORA_STAB_FALLBACK = 2 };
 
 typedef struct {
@@ -31,6 +31,7 @@ typedef struct {
     int64_t sum_q;          /* rows written by centers (== N in SEQ/OFF) */
     int64_t sum_cols;       /* right-hand sides solved in total */
     double min_abs_margin;  /* min over decisions of |(L_c - L_i) / L_c| (inf if none) */
+    int64_t n_boundary;     /* boundary rows (ora_assemble_bc) */
 } ora_stats;
 
 /* Degree rule of §2: 2D closed form s = floor((sqrt(4n+1)-3)/2); 3D: largest s with
@@ -60,6 +61,12 @@ int ora_ball_len(const double* d2, int64_t N, int n, double delta, int32_t* ball
 int ora_local_weights(const double* X, int d, const int32_t* idx, int n, int ell, int m, int op,
                       const double* Y, int q, double* W, double* lam);
 
+/* As ora_local_weights, also for op = ORA_OP_NORMAL: the derivative along the unit normal
+ * Nrm[e*d..] at evaluation point e (Nrm may be NULL for the other operators). */
+int ora_local_weights_dn(const double* X, int d, const int32_t* idx, int n, int ell, int m,
+                         int op, const double* Y, const double* Nrm, int q, double* W,
+                         double* lam);
+
 /* Full sequential construction of L (§4.1 traversal in index order, §4.2.1 stabilization).
  * Inputs: nodes X [N][d], the kNN table from ora_knn.  Outputs (all caller-allocated):
  * CSR row_ptr[N+1], col[N*n], val[N*n] with columns ascending; owner[N] = stencil that
@@ -69,6 +76,16 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
                  const int32_t* nbr, const double* d2, int64_t* row_ptr, int32_t* col,
                  double* val, int32_t* owner, uint8_t* is_center, double* lam_row,
                  ora_stats* stats);
+
+/* ora_assemble with boundary nodes (§5): bc[i] = 0 interior, 1 Dirichlet, 2 Neumann (unit
+ * outward normal nrm[i*d..], may be NULL without Neumann nodes).  The overlapped traversal
+ * covers the interior only; every boundary node gets its own-stencil row: the identity
+ * (Dirichlet) or the normal derivative (Neumann); is_center = 3 for those rows.  bc may be
+ * NULL (no boundary: ora_assemble). */
+int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, double delta,
+                    int mode, const uint8_t* bc, const double* nrm, const int32_t* nbr,
+                    const double* d2, int64_t* row_ptr, int32_t* col, double* val,
+                    int32_t* owner, uint8_t* is_center, double* lam_row, ora_stats* stats);
 
 /* Mixed stencils: node k has its own n_k <= n_max, ell_k and m_k.  nbr/d2 from ora_knn with
  * n = n_max; node k's stencil is the first n_k entries.  Rows take the length of the stencil

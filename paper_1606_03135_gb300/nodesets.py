@@ -162,6 +162,51 @@ def cube3d_clustered(N: int = 500000, seed: int = 4, n_clusters: int = 8,
     return np.ascontiguousarray(P)
 
 
+def disk2d_bc(N_int: int = 2000, seed: int = 1, refine: bool = True):
+    """Unit disk with boundary nodes for a Neumann problem (the paper's 2D test, §5 and §7.1):
+    N_int jittered Halton nodes inside radius 1 - h (h = sqrt(pi / N_int)), N_b = round(2 pi / h)
+    nodes evenly spaced on the unit circle (seeded rotation) and, with `refine`, the boundary
+    refinement layer of §6: copies of the boundary nodes h/2 inward along the normals.
+    Returns (X, bc, normals): bc = 2 (Neumann) on the circle, 0 elsewhere; normals are the
+    outward unit normals on the circle, zero elsewhere."""
+    h = math.sqrt(math.pi / N_int)
+    inside = lambda P: (P[:, 0] * P[:, 0] + P[:, 1] * P[:, 1]) <= (1.0 - h) * (1.0 - h)
+    P = _jitter_in(_halton_in(N_int, 2, inside), h, 0.1, seed, inside)
+    Nb = int(round(2.0 * math.pi / h))
+    th = 2.0 * math.pi * (np.arange(Nb) + uniform(seed, 1, offset=1 << 47)[0]) / Nb
+    B = np.stack([np.cos(th), np.sin(th)], axis=1)
+    parts = [P] + ([(1.0 - 0.5 * h) * B] if refine else []) + [B]
+    X = np.ascontiguousarray(np.concatenate(parts, axis=0))
+    bc = np.zeros(X.shape[0], dtype=np.uint8)
+    bc[-Nb:] = 2
+    normals = np.zeros_like(X)
+    normals[-Nb:] = B
+    return X, bc, normals
+
+
+def ball3d_bc(N_int: int = 20000, seed: int = 3):
+    """Unit ball with boundary nodes for a Dirichlet problem (the paper's 3D test, §7.2):
+    N_int jittered Halton nodes inside radius 1 - h (h = (4 pi / 3 / N_int)^(1/3)) and
+    N_b = round(4 pi / h^2) nodes on the unit sphere on a Fibonacci lattice (seeded rotation).
+    Returns (X, bc, normals): bc = 1 (Dirichlet) on the sphere; normals = the sphere points."""
+    h = (4.0 * math.pi / 3.0 / N_int) ** (1.0 / 3.0)
+    r2 = (1.0 - h) * (1.0 - h)
+    inside = lambda P: (P[:, 0] * P[:, 0] + P[:, 1] * P[:, 1] + P[:, 2] * P[:, 2]) <= r2
+    P = _jitter_in(_halton_in(N_int, 3, inside), h, 0.1, seed, inside)
+    Nb = int(round(4.0 * math.pi / (h * h)))
+    i = np.arange(Nb, dtype=np.float64)
+    z = 1.0 - (2.0 * i + 1.0) / Nb
+    rr = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    ph = i * (math.pi * (3.0 - math.sqrt(5.0))) + 2.0 * math.pi * uniform(seed, 1, offset=1 << 47)[0]
+    B = np.stack([rr * np.cos(ph), rr * np.sin(ph), z], axis=1)
+    X = np.ascontiguousarray(np.concatenate([P, B], axis=0))
+    bc = np.zeros(X.shape[0], dtype=np.uint8)
+    bc[-Nb:] = 1
+    normals = np.zeros_like(X)
+    normals[-Nb:] = B
+    return X, bc, normals
+
+
 def jittered_grid(side: int, d: int, amp: float = 0.2, seed: int = 7,
                   order: str = "random") -> np.ndarray:
     """side^d cell-centred points in [0,1]^d with U(-amp*h, amp*h) jitter (small test sets)."""

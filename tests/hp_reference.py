@@ -9,9 +9,10 @@ import itertools
 import numpy as np
 
 
-def mp_weights(X, idx, ell, m, Y, dps=40):
+def mp_weights(X, idx, ell, m, Y, dps=40, normal=None):
     """Independent high-precision weights from the definitions of §4.1, in the ORIGINAL
-    coordinates with raw monomials x^a y^b (z^c); Laplacians by sympy differentiation."""
+    coordinates with raw monomials x^a y^b (z^c); Laplacians by sympy differentiation.  With
+    `normal` (a unit vector) the operator is the derivative along it instead (§5, Neumann)."""
     import mpmath as mp
     import sympy as sp
     mp.mp.dps = dps
@@ -19,7 +20,11 @@ def mp_weights(X, idx, ell, m, Y, dps=40):
     syms = sp.symbols("x0:%d" % d)
     cs = sp.symbols("c0:%d" % d)
     r = sp.sqrt(sum((s - c) ** 2 for s, c in zip(syms, cs)))
-    lap = lambda f: sum(sp.diff(f, s, 2) for s in syms)
+    if normal is None:
+        lap = lambda f: sum(sp.diff(f, s, 2) for s in syms)
+    else:
+        nv = [sp.Float(float(v), 60) for v in normal]
+        lap = lambda f: sum(c * sp.diff(f, s) for c, s in zip(nv, syms))
     phi = r ** m
     lphi = sp.simplify(lap(phi))
     f_lphi = sp.lambdify(syms + cs, lphi, "mpmath")

@@ -380,3 +380,77 @@ def test_mixed_traversal_satisfies_its_characterisation():
         assert r["row_ptr"][i + 1] - r["row_ptr"][i] == n_node[j]
         assert np.array_equal(r["col"][sl], cols[o])
         assert np.array_equal(r["val"][sl], acc[j][0][o, t])
+
+
+# ------------------------------------------------------------------ boundary rows (§5)
+def _poly_dn_check(X, idx, ell, m, nrm, d):
+    """sum_j w_j p(x_j) = grad p(x_c) . n for every monomial p = (x - x_c)^alpha, |alpha| <= ell
+    (exactly: n_a for alpha = e_a, 0 otherwise)."""
+    W, lam = O.normal_weights(X, idx, ell, m, nrm)
+    Z = X[idx] - X[idx[0]]
+    worst = 0.0
+    for g in range(ell + 1):
+        for al in itertools.product(range(g + 1), repeat=d):
+            if sum(al) != g:
+                continue
+            pv = np.prod(Z ** np.array(al), axis=1)
+            exact = nrm[al.index(1)] if g == 1 else 0.0
+            scale = np.abs(W * pv).sum() + 1.0
+            worst = max(worst, abs((W * pv).sum() - exact) / scale)
+    return worst, W, lam
+
+
+@pytest.mark.parametrize("d,n,ell,m", [(2, 21, 3, 5), (2, 31, 4, 7), (3, 41, 3, 7)])
+def test_neumann_weights_reproduce_normal_derivatives_of_polynomials(d, n, ell, m):
+    X, bc, nrm = NS.disk2d_bc(500, seed=3) if d == 2 else NS.ball3d_bc(3000, seed=4)
+    nbr, _ = O.knn(X, n)
+    for i in np.flatnonzero(bc)[:: max(1, int(bc.astype(bool).sum()) // 8)]:
+        worst, _, _ = _poly_dn_check(X, nbr[i], ell, m, nrm[i], d)
+        assert worst < 1e-9, (i, worst)
+
+
+@pytest.mark.parametrize("d,n,ell,m", [(2, 12, 2, 3), (3, 20, 2, 5)])
+def test_neumann_weights_match_independent_high_precision_solve(d, n, ell, m):
+    X, bc, nrm = NS.disk2d_bc(300, seed=5) if d == 2 else NS.ball3d_bc(1500, seed=6)
+    nbr, _ = O.knn(X, n)
+    for i in np.flatnonzero(bc)[:3]:
+        W, _ = O.normal_weights(X, nbr[i], ell, m, nrm[i])
+        ref = _mp_weights(X, nbr[i], ell, m, X[i:i + 1], dps=40, normal=nrm[i])[:, 0]
+        assert np.abs(W - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_boundary_rows_and_interior_only_traversal(kind):
+    """Boundary nodes (§5): never a center of the overlapped traversal nor a member of a
+    retention set; each gets its own-stencil row (identity for Dirichlet, normal derivative
+    for Neumann); the interior rows come from interior centers whose balls hold them."""
+    X, bc, nrm = NS.disk2d_bc(400, seed=7)
+    bc = np.where(bc > 0, kind, 0).astype(np.uint8)
+    n, ell, m, delta = 12, 2, 3, 0.5
+    r = O.assemble(X, n, ell, m, delta, bc=bc, normals=nrm)
+    N = X.shape[0]
+    nbr, d2 = r["nbr"], r["d2"]
+    bl = O.ball_len(d2, delta)
+    b = bc > 0
+    assert r["stats"]["n_boundary"] == b.sum()
+    assert np.array_equal(r["is_center"][b], np.full(b.sum(), 3))
+    assert np.array_equal(r["owner"][b], np.flatnonzero(b))
+    assert not np.isin(r["owner"][~b], np.flatnonzero(b)).any()
+    assert np.all(np.isin(r["is_center"][~b], [0, 1]))
+    for i in np.flatnonzero(~b):
+        o = r["owner"][i]
+        assert o <= i and i in nbr[o, :bl[o]]
+    for i in np.flatnonzero(b):
+        sl = slice(r["row_ptr"][i], r["row_ptr"][i + 1])
+        order = np.argsort(nbr[i])
+        assert np.array_equal(r["col"][sl], nbr[i][order])
+        if kind == 1:
+            assert np.array_equal(r["val"][sl], (nbr[i][order] == i).astype(float))
+        else:
+            W, _ = O.normal_weights(X, nbr[i], ell, m, nrm[i])
+            assert np.array_equal(r["val"][sl], W[order])
+    # without boundary nodes it is the plain construction
+    r0 = O.assemble(X, n, ell, m, delta)
+    r1 = O.assemble(X, n, ell, m, delta, bc=np.zeros(N, np.uint8))
+    for key in ("row_ptr", "col", "val", "owner", "is_center"):
+        assert np.array_equal(r0[key], r1[key])
