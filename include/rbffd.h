@@ -105,6 +105,7 @@ typedef struct {
     int64_t nnz;            /* entries of L (N n for uniform stencils) */
     int64_t plan_bytes;     /* device memory the plan holds after rbffd_plan */
     int64_t assemble_bytes; /* device memory rbffd_assemble adds (exact, known after plan) */
+    int64_t n_boundary;      /* boundary rows (rbffd_set_boundary) */
 } rbffd_stats_t;
 
 /* rbffd_plan -- build the stencils of §4.1 for one node set.
@@ -187,6 +188,30 @@ int rbffd_export_lambda(rbffd_plan_t plan, double* lam_row, uint8_t* is_center);
 #define RBFFD_NOALLOC_MAX_NODES 32768
 int rbffd_stencils_noalloc(const double* nodes, int64_t N, int d, int n, double delta,
                            int32_t* nbr, double* rho2, int32_t* ball_len, void* stream);
+
+/* rbffd_set_boundary -- mark boundary nodes (§5: the method-of-lines system, whose boundary
+ * block B replaces the Laplacian rows of the boundary nodes).
+ *   plan     a plan from rbffd_plan (per-node plans: RBFFD_EINVAL)
+ *   bc       host array [N]: 0 interior, 1 Dirichlet, 2 Neumann (other values: RBFFD_EINVAL);
+ *            NULL removes the boundary
+ *   normals  host array [N][d] row-major: the unit outward normal of each Neumann node (other
+ *            rows are ignored); may be NULL when no node is Neumann (else RBFFD_EINVAL);
+ *            non-finite entries of Neumann rows: RBFFD_EINVAL
+ * Takes effect at the next rbffd_assemble: the overlapped traversal then runs over the
+ * interior only (a boundary node is never a center and never in a retention set, so
+ * N_delta = (N_i)_delta + N_b), and every boundary node gets its own-stencil row: the identity
+ * for Dirichlet (B_bb = I, B_bi = 0), the derivative along its normal for Neumann.  Those rows
+ * have is_center = 3 (rbffd_export_lambda) and are their own owners.  Both arrays are copied;
+ * the call waits for the plan's last stream. */
+int rbffd_set_boundary(rbffd_plan_t plan, const uint8_t* bc, const double* normals);
+
+/* rbffd_timestep_matrix -- values of the time-stepping matrix of §5 on L's sparsity pattern:
+ * interior row i: e_i - c L_i (c = nu dt for backward Euler, (12/25) nu dt for BDF4), boundary
+ * row: B_i unchanged.
+ *   val_out  device array of nnz doubles (the count rbffd_assemble reported), caller-owned;
+ *            entry k pairs with L's col[k]
+ * Needs an assembled plan (else RBFFD_ESTATE).  Asynchronous on `stream`. */
+int rbffd_timestep_matrix(rbffd_plan_t plan, double c, double* val_out, void* stream);
 
 /* rbffd_destroy -- free the plan and everything it owns (waits for its last stream). */
 void rbffd_destroy(rbffd_plan_t plan);

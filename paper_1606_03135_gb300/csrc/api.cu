@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -37,6 +38,11 @@ struct rbffd_plan_s {
     int* node_n = nullptr;
     signed char* node_ell = nullptr;
     signed char* node_m = nullptr;
+    // boundary nodes (rbffd_set_boundary)
+    void* bc_block = nullptr;
+    unsigned char* bc = nullptr;
+    double* nrm = nullptr;
+    long long n_boundary = 0;
     long long nnz = 0;
     DevCounters* ctr = nullptr;
     DevCounters h_ctr{};           // host copy of the device counters
@@ -253,6 +259,7 @@ void free_plan(rbffd_plan_s* p) {
     cudaStream_t s = p->last;
     free_assemble(p, s);
     if (p->plan_block) cudaFreeAsync(p->plan_block, s);
+    if (p->bc_block) cudaFreeAsync(p->bc_block, s);
     cudaStreamSynchronize(s);
     for (auto& e : p->ev)
         if (e) event_release(p->device, e);
@@ -541,6 +548,8 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.slot_off = p->slot_off; a.basis = p->basis; a.basis_count = p->basis_count;
     for (int l = 0; l <= kMaxEll; ++l) { a.boff[l] = p->boff[l]; a.Mof[l] = p->Mof[l]; }
     a.node_n = p->node_n; a.node_ell = p->node_ell; a.node_m = p->node_m;
+    a.bc = p->n_boundary > 0 ? p->bc : nullptr;
+    a.nrm = p->nrm;
     a.N = (int)p->N; a.n = p->n; a.M = p->M; a.K = p->K; a.m = p->m; a.ell = p->ell;
     a.qcap = p->qcap; a.stride = p->stride; a.mode = p->opts.stab_mode;
     a.coef = (double)(p->m * (p->m + p->d - 2));
@@ -556,7 +565,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     rc = launch_traversal(p->d, a, p->lp, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
     if (rc) return rc;
     cudaEventRecord(p->ev[4], s);
-    if (p->opts.stab_mode == RBFFD_STAB_FALLBACK) {
+    if (p->opts.stab_mode == RBFFD_STAB_FALLBACK || p->n_boundary > 0) {
         rc = launch_fallback(p->d, a, p->lp, s, &p->launches);
         if (rc) return rc;
     }
@@ -578,6 +587,53 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
         out->val = p->val;
     }
     return p->opts.sync ? p->h_ctr.status : RBFFD_OK;
+}
+
+int rbffd_set_boundary(rbffd_plan_t p, const uint8_t* bc, const double* normals) {
+    if (!p || p->mixed) return RBFFD_EINVAL;
+    cudaStream_t s = p->last;
+    if (!bc) {
+        p->n_boundary = 0;
+        return RBFFD_OK;
+    }
+    const size_t N = (size_t)p->N, d = (size_t)p->d;
+    long long nb = 0;
+    bool neumann = false;
+    for (size_t i = 0; i < N; ++i) {
+        if (bc[i] > 2) return RBFFD_EINVAL;
+        nb += bc[i] != 0;
+        if (bc[i] == 2) {
+            neumann = true;
+            if (!normals) return RBFFD_EINVAL;
+            for (size_t a = 0; a < d; ++a)
+                if (!std::isfinite(normals[i * d + a])) return RBFFD_EINVAL;
+        }
+    }
+    int rc;
+    if (!p->bc_block) {
+        Carver c;
+        const size_t ob = c.add<unsigned char>(N), on = c.add<double>(N * d);
+        if ((rc = pool_alloc(&p->bc_block, c.bytes, p->device, s))) return rc;
+        p->bc = at<unsigned char>(p->bc_block, ob);
+        p->nrm = at<double>(p->bc_block, on);
+        p->plan_bytes += c.bytes;
+    }
+    if ((rc = bad(cudaMemcpyAsync(p->bc, bc, N, cudaMemcpyHostToDevice, s))) ||
+        (neumann && (rc = bad(cudaMemcpyAsync(p->nrm, normals, N * d * sizeof(double),
+                                                cudaMemcpyHostToDevice, s)))) ||
+        (!neumann && (rc = bad(cudaMemsetAsync(p->nrm, 0, N * d * sizeof(double), s)))) ||
+        (rc = bad(cudaStreamSynchronize(s))))
+        return rc;
+    p->n_boundary = nb;
+    return RBFFD_OK;
+}
+
+int rbffd_timestep_matrix(rbffd_plan_t p, double c, double* val_out, void* stream) {
+    if (!p || !val_out || !std::isfinite(c)) return RBFFD_EINVAL;
+    if (!p->assembled) return RBFFD_ESTATE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return launch_timestep((int)p->N, p->row_ptr, p->col, p->val,
+                           p->n_boundary > 0 ? p->bc : nullptr, c, val_out, s, &p->launches);
 }
 
 int rbffd_apply(rbffd_plan_t p, const double* u, double* y, void* stream) {
@@ -604,6 +660,7 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
     if (p->assembled) {
         out->n_centers = (int64_t)c.n_centers;
         out->n_fallback = (int64_t)c.n_fallback;
+        out->n_boundary = (int64_t)p->n_boundary;
         out->n_rejected = (int64_t)c.n_rejected;
         out->sum_cols = (int64_t)c.sum_cols;
         out->n_singular = c.n_singular;

@@ -665,10 +665,11 @@ __device__ void on_covered(const SolveArgs& a, int i) {
     }
 }
 
-__global__ void k_traversal_init(int N, const int* __restrict__ indeg, int* state, int* pending,
+__global__ void k_traversal_init(int N, const int* __restrict__ indeg,
+                                 const unsigned char* __restrict__ bc, int* state, int* pending,
                                  int* owner, int* queue, unsigned char* fb_flag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        state[i] = kUndecided;
+        state[i] = (bc && bc[i]) ? kBoundary : kUndecided;
         pending[i] = indeg[i];
         owner[i] = kNoOwner;
         queue[i] = -1;
@@ -676,10 +677,26 @@ __global__ void k_traversal_init(int N, const int* __restrict__ indeg, int* stat
     }
 }
 
-__global__ void k_traversal_seed(SolveArgs a, const int* __restrict__ indeg) {
+// Boundary nodes (§5) take no part in the overlapped traversal: each releases the later
+// members of its ball (which counted it as a possible center), is done at once, and is queued
+// for its own-stencil row with the fallback rows.
+__global__ void k_boundary_release(SolveArgs a) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.N; q += gridDim.x * blockDim.x) {
+        if (!a.bc[q]) continue;
+        const int* nb = a.nbr + (size_t)q * a.n;
+        for (int t = 1; t < a.ball_len[q]; ++t)
+            if (nb[t] > q) atomicSub(&a.pending[nb[t]], 1);
+        a.owner[q] = q;
+        a.fb_flag[q] = 1;
+        a.fb_list[atomicAdd(&a.ctr->fb_count, 1)] = q;
+        atomicAdd(&a.ctr->done, 1);
+    }
+}
+
+__global__ void k_traversal_seed(SolveArgs a) {
     if (a.no_seed) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += gridDim.x * blockDim.x) {
-        if (indeg[i] == 0) {
+        if (a.pending[i] == 0 && a.state[i] == kUndecided) {
             a.state[i] = kCenter;
             a.owner[i] = i;
             push_center(a, i);
@@ -750,7 +767,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
                     if (t == 0) inc = true;
                     else {
                         const int i = a.nbr[(size_t)j * ns + t];
-                        inc = (i > j) && (__ldcg(&a.owner[i]) >= j);
+                        inc = (i > j) && (__ldcg(&a.owner[i]) >= j) && !(a.bc && a.bc[i]);
                     }
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, inc);
@@ -847,6 +864,34 @@ __global__ void k_fallback_collect(SolveArgs a) {
     }
 }
 
+// Right-hand side of the normal derivative at the stencil center (the origin of the scaled
+// coordinates), replacing column 0 of the right-hand-side block: d/dn ||y - xi_j||^m at y = 0
+// is -m ||xi_j||^(m-2) (xi_j . n), and of the monomials only the linear ones have a nonzero
+// gradient there (d/dn xi_a = n_a).
+template <int D, int NT>
+__device__ void neumann_rhs(const SolveArgs& a, const Shape& sh, int i, const StencilSmem& sm) {
+    const double* nv = a.nrm + (size_t)i * D;
+    const double mm = exact_double(sh.m);
+    for (int j = threadIdx.x; j < sh.n + sh.M; j += NT) {
+        double v;
+        if (j < sh.n) {
+            const double* xj = sm.xi + j * D;
+            double r2 = xj[0] * xj[0], dot = xj[0] * nv[0];
+            for (int c = 1; c < D; ++c) {
+                r2 = fma(xj[c], xj[c], r2);
+                dot = fma(xj[c], nv[c], dot);
+            }
+            double pm2 = sqrt_fast(r2);  // r^(m-2), m odd
+            for (int t = 0; t < (sh.m - 3) / 2; ++t) pm2 *= r2;
+            v = -mm * pm2 * dot;
+        } else {
+            const int l = j - sh.n;
+            v = (l > 0 && sh.bs.parent[l] == 0) ? nv[sh.bs.var[l]] : 0.0;
+        }
+        sm.X[j * sm.xs] = v;
+    }
+}
+
 // FALLBACK re-solves (one right-hand side each), one launch per stencil class: `cls` is the
 // degree this launch handles (-1: all), n_cls/K_cls the largest stencil/system of the class,
 // so shared memory is sized for the class and a single column.
@@ -865,19 +910,31 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int i = a.fb_list[w];
         if (cls >= 0 && (int)a.node_ell[i] != cls) continue;  // another class's launch
+        const int kind = a.bc ? (int)a.bc[i] : 0;  // boundary rows (§5) share this launch
         const Shape sh = shape_of<D>(a, sbasis, i);
+        const long long slot = a.slot_off[i];
+        if (kind == 1) {  // Dirichlet: the identity row, exactly
+            for (int r = tid; r < sh.n; r += NT) a.slot_w[slot * a.n + r] = (r == 0) ? 1.0 : 0.0;
+            if (tid == 0) a.slot_lam[slot] = 1.0;
+            continue;
+        }
         for (int t = tid; t < sh.n; t += NT) sm.colof[t] = (t == 0) ? 0 : -1;
         if (tid == 0) sm.cols[0] = 0;
         __syncthreads();
-        const bool ok = solve_local<D, PACKED, NT>(a, sh, i, 1, sm);
+        assemble_local<D, PACKED, NT>(a, sh, i, 1, sm);
+        if (kind == 2) {
+            neumann_rhs<D, NT>(a, sh, i, sm);
+            __syncthreads();
+        }
+        const bool ok = PACKED ? factor_solve_ldlt<NT>(sh.K, 1, sm) : factor_solve_lu<NT>(sh.K, 1, sm);
         if (ok) lebesgue_values<NT>(sh.n, sh.K, 1, sm);
         __syncthreads();
         double r2c = a.rho2[i];
         if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
-        const double inv_r2 = rcp_fixed(r2c);
-        const long long slot = a.slot_off[i];
+        // weights of the scaled problem times rho^-2 (Laplacian) or rho^-1 (normal derivative)
+        const double scale = kind == 2 ? rcp_fixed(sqrt(r2c)) : rcp_fixed(r2c);
         for (int r = tid; r < sh.n; r += NT)
-            a.slot_w[slot * a.n + r] = ok ? sm.X[sm.rowof[r] * sm.xs] * inv_r2 : nan;
+            a.slot_w[slot * a.n + r] = ok ? sm.X[sm.rowof[r] * sm.xs] * scale : nan;
         if (tid == 0) {
             a.slot_lam[slot] = ok ? sm.lam[0] : nan;
             if (!ok) {
@@ -887,7 +944,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
             const unsigned long long K = (unsigned long long)sh.K;
             atomicAdd(&a.ctr->sum_k3, K * K * K);
             atomicAdd(&a.ctr->sum_k2q, K * K);
-            atomicAdd(&a.ctr->n_fallback, 1ull);
+            if (kind == 0) atomicAdd(&a.ctr->n_fallback, 1ull);
             atomicAdd(&a.ctr->sum_cols, 1ull);
         }
         __syncthreads();
@@ -957,7 +1014,7 @@ __global__ void __launch_bounds__(256) k_finalize(SolveArgs a, long long* __rest
                 if (i == a.N - 1) row_ptr[a.N] = (long long)a.N * ns;
             }
             lam_row[i] = a.slot_lam[slot];
-            is_center[i] = fb ? 2 : (s == i ? 1 : 0);
+            is_center[i] = fb ? ((a.bc && a.bc[i]) ? 3 : 2) : (s == i ? 1 : 0);
         }
         __syncwarp();
     }
@@ -976,6 +1033,25 @@ __global__ void __launch_bounds__(256) k_spmv(int N, const long long* __restrict
         for (long long k = b + lane; k < e; k += 32) s = fma(val[k], __ldg(&u[col[k]]), s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) y[i] = s;
+    }
+}
+
+// Values of the time-stepping matrix of §5 on L's pattern, one warp per row: interior rows
+// e_i - c L_i, boundary rows unchanged.  Rounded as 1 - c v and -(c v).
+__global__ void __launch_bounds__(256) k_timestep(int N, const long long* __restrict__ row_ptr,
+                                                  const int* __restrict__ col,
+                                                  const double* __restrict__ val,
+                                                  const unsigned char* __restrict__ bc, double c,
+                                                  double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < N; i += gridDim.x * wpb) {
+        const bool boundary = bc && bc[i];
+        for (long long k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) {
+            const double v = val[k];
+            const double cv = __dmul_rn(c, v);
+            out[k] = boundary ? v : (col[k] == i ? __dsub_rn(1.0, cv) : -cv);
+        }
     }
 }
 
@@ -1135,9 +1211,13 @@ static int traversal(const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
                      int* launches, cudaEvent_t ev0, cudaEvent_t ev1) {
     const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
     const int tb = 256, nb = (a.N + tb - 1) / tb;
-    k_traversal_init<<<nb, tb, 0, s>>>(a.N, indeg, a.state, a.pending, a.owner, a.queue,
+    k_traversal_init<<<nb, tb, 0, s>>>(a.N, indeg, a.bc, a.state, a.pending, a.owner, a.queue,
                                        a.fb_flag);
-    k_traversal_seed<<<nb, tb, 0, s>>>(a, indeg);
+    if (a.bc) {
+        k_boundary_release<<<nb, tb, 0, s>>>(a);
+        ++*launches;
+    }
+    k_traversal_seed<<<nb, tb, 0, s>>>(a);
     *launches += 2;
     int grid = min(lp.grid, a.N);
     if (a.max_ctas > 0) grid = min(grid, a.max_ctas);
@@ -1182,8 +1262,10 @@ int launch_traversal(int D, const SolveArgs& a, const LaunchPlan& lp, const int*
 template <int D, bool PACKED>
 static int fallback(const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s, int* launches) {
     const int tb = 256, nb = (a.N + tb - 1) / tb;
-    k_fallback_collect<<<nb, tb, 0, s>>>(a);
-    ++*launches;
+    if (a.mode == RBFFD_STAB_FALLBACK) {  // rows that failed the test (boundary rows are queued)
+        k_fallback_collect<<<nb, tb, 0, s>>>(a);
+        ++*launches;
+    }
     const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
     for (int c = 0; c < lp.n_fb; ++c) {
         const FallbackClass& f = lp.fb[c];
@@ -1217,6 +1299,15 @@ int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* va
     const int blocks = (a.N + wpb - 1) / wpb;
     k_finalize<<<blocks, wpb * 32, wpb * a.n * sizeof(int), s>>>(a, row_ptr, col, val, lam_row,
                                                                 is_center);
+    ++*launches;
+    return RB_LAUNCHED(__func__);
+}
+
+int launch_timestep(int N, const long long* row_ptr, const int* col, const double* val,
+                    const unsigned char* bc, double c, double* out, cudaStream_t s, int* launches) {
+    const int wpb = 8;
+    const int blocks = (N + wpb - 1) / wpb;
+    k_timestep<<<blocks, wpb * 32, 0, s>>>(N, row_ptr, col, val, bc, c, out);
     ++*launches;
     return RB_LAUNCHED(__func__);
 }

@@ -28,6 +28,7 @@ constexpr int kWarp = 32;
 constexpr int kUndecided = 0;
 constexpr int kCenter = 1;
 constexpr int kCovered = 2;
+constexpr int kBoundary = 3;  // boundary node: outside the overlapped traversal
 constexpr int kNoOwner = 0x7fffffff;
 
 struct GridParams {
@@ -130,6 +131,8 @@ struct SolveArgs {
     const int* node_n;
     const signed char* node_ell;
     const signed char* node_m;
+    const unsigned char* bc;   // boundary kind per node (0 interior, 1 Dirichlet, 2 Neumann) or null
+    const double* nrm;         // unit normals [N][d] of Neumann nodes (or null)
     int N, n, M, K, m, ell;
     int qcap;                  // columns room per stencil
     int stride;                // row stride of the full matrix (LU) or of the RHS block (LDL^T)
@@ -182,5 +185,7 @@ int launch_finalize(const SolveArgs& a, long long* row_ptr, int* col, double* va
                     double* lam_row, unsigned char* is_center, cudaStream_t s, int* launches);
 int launch_spmv(int N, int n, const long long* row_ptr, const int* col, const double* val,
                 const double* u, double* y, cudaStream_t s, int* launches);
+int launch_timestep(int N, const long long* row_ptr, const int* col, const double* val,
+                    const unsigned char* bc, double c, double* out, cudaStream_t s, int* launches);
 
 }  // namespace rbffd

@@ -39,7 +39,7 @@ class rbffd_stats_t(C.Structure):
                 ("n_launches", C.c_int64), ("ms_stencils", C.c_float),
                 ("ms_traversal", C.c_float), ("ms_fallback", C.c_float),
                 ("ms_finalize", C.c_float), ("nnz", C.c_int64), ("plan_bytes", C.c_int64),
-                ("assemble_bytes", C.c_int64)]
+                ("assemble_bytes", C.c_int64), ("n_boundary", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -57,6 +57,8 @@ _SIGS = {
                                    C.POINTER(C.c_void_p)]),
     "rbffd_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(rbffd_csr)]),
     "rbffd_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_set_boundary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_timestep_matrix": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "rbffd_stats": (C.c_int, [C.c_void_p, C.POINTER(rbffd_stats_t)]),
     "rbffd_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_export_stencils": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -227,6 +229,28 @@ class Plan:
         _check(rc, "rbffd_assemble (capture)")
         self._stream = s
         return g
+
+    def set_boundary(self, bc, normals=None):
+        """Boundary nodes (§5): bc [N] uint8 (0 interior, 1 Dirichlet, 2 Neumann), normals
+        [N][d] unit outward normals of the Neumann nodes; None removes the boundary."""
+        bcv = None if bc is None else np.ascontiguousarray(bc, dtype=np.uint8)
+        nrv = None if normals is None else np.ascontiguousarray(normals, dtype=np.float64)
+        if bcv is not None and bcv.shape != (self.N,):
+            raise ValueError("bc must have one entry per node")
+        if nrv is not None and nrv.shape != (self.N, self.d):
+            raise ValueError("normals must be [N][d]")
+        _check(load().rbffd_set_boundary(self._plan, _p(bcv), _p(nrv)), "rbffd_set_boundary")
+
+    def timestep_matrix(self, c, out=None):
+        """Values of the time-stepping matrix of §5 on L's pattern (interior rows e_i - c L_i,
+        boundary rows unchanged) into a device tensor of nnz doubles, returned."""
+        import torch
+        if out is None:
+            out = torch.empty(self.stats()["nnz"], dtype=torch.float64, device="cuda")
+        _check(load().rbffd_timestep_matrix(self._plan, float(c), C.c_void_p(out.data_ptr()),
+                                            _stream_handle(self._stream)),
+               "rbffd_timestep_matrix")
+        return out
 
     def apply(self, u, y):
         _check(rbffd_apply(self._plan, _p(u), _p(y), _stream_handle(self._stream)),
