@@ -41,10 +41,15 @@ def _env_rank():
 
 
 def _workload(name=None):
+    """(X, workload dict, (bc, normals) or None)."""
     from paper_1606_03135_gb300 import nodesets as NS
     name = name or WORKLOAD
+    if name in NS.BC_WORKLOADS:
+        w = NS.BC_WORKLOADS[name]
+        X, bc, nrm = w["gen"](**w["kw"])
+        return X, w, (bc, nrm)
     w = NS.WORKLOADS[name]
-    return NS.make(name), w
+    return NS.make(name), w, None
 
 
 class ClockSampler:
@@ -124,11 +129,12 @@ def max_over_ranks(x: float, device="cpu") -> float:
     return float(t.item())
 
 
-def cpu_oracle_step(X, w, delta):
+def cpu_oracle_step(X, w, delta, bcw=None):
     """The oracle as it stands, on this host's cores: kNN + traversal + solves + CSR."""
     from oracle import oracle as O
     t = time.perf_counter()
-    O.assemble(X, w["n"], w["ell"], w["m"], delta, O.STAB_SEQ)
+    bc, nrm = bcw if bcw is not None else (None, None)
+    O.assemble(X, w["n"], w["ell"], w["m"], delta, O.STAB_SEQ, bc=bc, normals=nrm)
     return time.perf_counter() - t
 
 
@@ -138,7 +144,7 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     O.build()
-    X, w = _workload()
+    X, w, _ = _workload()
     deltas = w["deltas"]
     for s in range(args.warmup):
         cpu_oracle_step(X, w, deltas[s % len(deltas)])
@@ -174,11 +180,13 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     from paper_1606_03135_gb300 import rbffd as R
     R.load()
-    X, w = _workload(args.workload)
+    X, w, bcw = _workload(args.workload)
     N, n, ell, m, deltas = X.shape[0], w["n"], w["ell"], w["m"], w["deltas"]
     d = X.shape[1]
     Xd = torch.from_numpy(X).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ts_buf = {delta: torch.empty(N * n, dtype=torch.float64, device=dev) for delta in deltas} \
+        if bcw is not None else None
     stream = torch.cuda.current_stream(dev)
 
     def one_step(detail=None, nodes=None, host_out=False):
@@ -190,7 +198,11 @@ def run_gpu(args):
         plans = []
         for delta in deltas:
             p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta, sync=False)
+            if bcw is not None:  # boundary rows and the time-stepping matrix of §5
+                p.set_boundary(*bcw)
             p.assemble()
+            if bcw is not None:
+                p.timestep_matrix(w["timestep_c"], out=ts_buf[delta])
             if host_out:
                 row_ptr, col, val, owner = p.export()
                 d2h += row_ptr.nbytes + col.nbytes + val.nbytes + owner.nbytes
@@ -253,7 +265,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
-        t_cpu = cpu_oracle_step(X, w, deltas[1])
+        t_cpu = cpu_oracle_step(X, w, deltas[1], bcw)
         cpu = {"value": N / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one full assembly at delta={deltas[1]} (N={N}, kNN + traversal + "
                          f"solves + CSR), single-threaded plain C oracle, {t_cpu:.1f} s"}
@@ -282,6 +294,9 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload or WORKLOAD, "N": N, "d": d, "n": n, "ell": ell, "m": m,
                    "deltas": list(deltas), "stab": "seq",
+                   **({"boundary": f"{int((bcw[0] > 0).sum())} boundary rows (kind "
+                                   f"{int(bcw[0].max())}) + time-stepping matrix c="
+                                   f"{w['timestep_c']:.3g}"} if bcw is not None else {}),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline, "cpu_baseline": cpu,

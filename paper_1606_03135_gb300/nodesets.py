@@ -255,6 +255,15 @@ MIXED_WORKLOADS = {
 }
 
 
+#: Workloads with boundary nodes (§5): generator returns (X, bc, normals).  The time-stepping
+#: matrix coefficient c = (12/25) nu dt is the paper's BDF4 with nu = 1, dt = 1e-3 (§7).
+BC_WORKLOADS = {
+    "disk2d_bc_N40000_l4_n31_r7": dict(gen=disk2d_bc, kw=dict(N_int=40000, seed=1), d=2, n=31,
+                                       ell=4, m=7, deltas=(1.0, 0.5, 0.3),
+                                       timestep_c=12.0 / 25.0 * 1e-3),
+}
+
+
 def make(name: str) -> np.ndarray:
     w = WORKLOADS[name]
     return w["gen"](**w["kw"])
