@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -288,6 +289,11 @@ def run_gpu(args):
             "ms_finalize": statistics.median(s["ms_finalize"] for s in sts),
             "traversal_tflops": statistics.median(s["alg_flops"] / s["ms_traversal"] / 1e9
                                                   for s in sts)}
+    from paper_1606_03135_gb300 import model as CM
+    M_terms = math.comb(ell + d, d)
+    speedup = CM.sweep_report({float(k): {"n_centers": v["n_centers"], "sum_cols": v["sum_cols"],
+                                          "ms_traversal": v["ms_traversal"]}
+                               for k, v in per_delta.items()}, N, n, M_terms, d)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -299,7 +305,7 @@ def run_gpu(args):
                                    f"{w['timestep_c']:.3g}"} if bcw is not None else {}),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roofline, "cpu_baseline": cpu,
+        "roofline": roofline, "cpu_baseline": cpu, "speedup_model": speedup,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": int(X.nbytes * len(deltas)),
                 "d2h_bytes_per_step": int(d2h)},

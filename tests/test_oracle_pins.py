@@ -454,3 +454,26 @@ def test_boundary_rows_and_interior_only_traversal(kind):
     r1 = O.assemble(X, n, ell, m, delta, bc=np.zeros(N, np.uint8))
     for key in ("row_ptr", "col", "val", "owner", "is_center"):
         assert np.array_equal(r0[key], r1[key])
+
+
+# ------------------------------------------------------------------ cost model (§4.3, §4.4)
+def test_cost_model_closed_forms():
+    from paper_1606_03135_gb300 import model as Mo
+    # p: the ball holds (1 - delta)^d n nodes, at least the center
+    assert Mo.p_hat(1.0, 31, 2) == 1.0 and Mo.p_hat(0.5, 40, 2) == 10.0
+    assert abs(Mo.p_hat(0.5, 80, 3) - 10.0) < 1e-12
+    # delta from the retained fraction inverts p = t n
+    for d in (2, 3):
+        for t in (0.1, 0.25, 0.5, 1.0):
+            delta = Mo.delta_from_retention(t, d)
+            assert abs(Mo.p_hat(delta, 1000, d) - max(t * 1000, 1.0)) < 1e-9
+    # eta: C at delta = 1 with gamma = 1; the cost ratio of counts reduces to it when
+    # N_delta = N / q and q = p
+    assert abs(Mo.eta_predicted(1.0, 31, 15, 2) - 0.4) < 1e-15
+    n, M, N = 31, 15, 40000
+    for delta in (0.5, 0.3):
+        p = Mo.p_hat(delta, n, 2)
+        assert abs(Mo.eta_from_counts(N, N / p, n, M, p) * 0.4 - Mo.eta_predicted(delta, n, M, 2)) < 1e-12
+    # more retained rows per stencil: larger predicted speedup, bounded by C gamma (n + M + 1)
+    e = [Mo.eta_predicted(dl, n, M, 2) for dl in (0.9, 0.7, 0.5, 0.3, 0.1)]
+    assert all(a < b for a, b in zip(e, e[1:])) and e[-1] < 0.4 * (n + M + 1)
