@@ -261,15 +261,23 @@ class Plan:
         _check(rc, "rbffd_stats")
         return st.as_dict()
 
-    def export(self):
+    def export(self, out=None):
+        """Host copies (row_ptr, col, val, owner) of the CSR and the stencil owning each row.
+        `out` may supply the four arrays (e.g. in pinned memory, reused across calls): int64
+        [N+1], int32 [>= nnz], float64 [>= nnz], int32 [N]; the views of the filled parts are
+        returned."""
         N = self.N
         nnz = self.stats()["nnz"]
-        row_ptr = np.zeros(N + 1, np.int64)
-        col = np.zeros(nnz, np.int32)
-        val = np.zeros(nnz, np.float64)
-        owner = np.zeros(N, np.int32)
+        if out is None:
+            out = (np.zeros(N + 1, np.int64), np.zeros(nnz, np.int32),
+                   np.zeros(nnz, np.float64), np.zeros(N, np.int32))
+        row_ptr, col, val, owner = out
+        for a, dt, size in ((row_ptr, np.int64, N + 1), (col, np.int32, nnz),
+                            (val, np.float64, nnz), (owner, np.int32, N)):
+            if a.dtype != dt or not a.flags.c_contiguous or a.size < size:
+                raise ValueError("export buffers: wrong dtype, layout or size")
         _check(rbffd_export(self._plan, row_ptr, col, val, owner), "rbffd_export")
-        return row_ptr, col, val, owner
+        return row_ptr[:N + 1], col[:nnz], val[:nnz], owner[:N]
 
     def export_stencils(self):
         N, n = self.N, self.n
