@@ -13,14 +13,19 @@
 // dependency of each later ball member.  Every device-side wait is bounded by a timeout and
 // ends the kernel with RBFFD_ETIMEOUT.
 //
-// Local solve (one warp per stencil).  The (n+M) x (n+M) saddle-point matrix [A P; P^T 0]
-// of §4.1 and the q right-hand sides of the overlapped system (one per solved ball member)
-// are assembled side by side in shared memory as one K x (K+q) array and reduced by
-// Gaussian elimination with partial pivoting (the forward substitution rides along with
-// the factorization), followed by back substitution for the q columns.  This is exactly
-// the paper's cost model (2/3) K^3 + 2 K^2 q flops.  Every FP64 warp instruction occupies
-// all 32 lanes of the narrow FP64 pipe whatever its active mask, so the updates are
-// flattened over (row, column) pairs to keep lanes busy.
+// Local solve (one team of 32 to 512 threads per stencil).  The (n+M) x (n+M) saddle-point
+// matrix [A P; P^T 0] of §4.1 and the q right-hand sides of the overlapped system (one per
+// solved ball member) are assembled in shared memory.  The matrix is symmetric, so by
+// default its lower triangle is stored packed and factored as L D L^T with Bunch-Kaufman
+// pivoting, the right-hand sides carried along ((1/3) K^3 + 2 K^2 q flops); the paper's
+// partial-pivot LU of the full [A_hat | B_hat] array ((2/3) K^3 + 2 K^2 q) is the
+// RBFFD_FACTOR_LU option.  Every FP64 warp instruction occupies all 32 lanes of the narrow
+// FP64 pipe whatever its active mask, so the updates are flattened over (row, column) pairs
+// to keep lanes busy, and scalar work (pivot tests, reciprocals, square roots) is moved to
+// the integer and FP32 pipes where it can be.
+//
+// Own-stencil rows (one right-hand side): FALLBACK re-solves of rows that failed the test,
+// and the boundary rows of §5 (Dirichlet identity, Neumann normal derivative).
 #include <cuda_runtime.h>
 
 #include <mutex>
