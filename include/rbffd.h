@@ -106,6 +106,8 @@ typedef struct {
     int64_t plan_bytes;     /* device memory the plan holds after rbffd_plan */
     int64_t assemble_bytes; /* device memory rbffd_assemble adds (exact, known after plan) */
     int64_t n_boundary;      /* boundary rows (rbffd_set_boundary) */
+    int64_t n_speculated;    /* solves made ahead by CTAs that found no ready center */
+    int64_t n_spec_used;     /* centers whose solve had been made ahead */
 } rbffd_stats_t;
 
 /* rbffd_plan -- build the stencils of §4.1 for one node set.

@@ -69,6 +69,7 @@ struct rbffd_plan_s {
     double* val = nullptr;
     double* lam_row = nullptr;
     unsigned char* is_center = nullptr;
+    int* spec = nullptr;
     cudaEvent_t ev[8] = {};
     int launches = 0;
     bool counters_fresh = false;
@@ -452,7 +453,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         c.add<int>(Nz); c.add<int>(Nz); c.add<int>(Nz); c.add<int>(Nz);
         c.add<unsigned char>(Nz); c.add<int>(Nz); c.add<double>(S * nz); c.add<double>(S);
         c.add<unsigned char>(S); c.add<long long>(Nz + 1); c.add<int>(Nz * nz);
-        c.add<double>(Nz * nz); c.add<double>(Nz); c.add<unsigned char>(Nz);
+        c.add<double>(Nz * nz); c.add<double>(Nz); c.add<unsigned char>(Nz); c.add<int>(Nz);
         p->asm_bytes = c.bytes;
     }
     p->qcap = p->max_ball < 1 ? 1 : p->max_ball;
@@ -531,7 +532,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
                      o_sl = c.add<double>(S), o_sp = c.add<unsigned char>(S),
                      o_rp = c.add<long long>(N + 1), o_col = c.add<int>(N * n),
                      o_val = c.add<double>(N * n), o_lam = c.add<double>(N),
-                     o_isc = c.add<unsigned char>(N);
+                     o_isc = c.add<unsigned char>(N), o_spec = c.add<int>(N);
         if ((rc = pool_alloc(&p->asm_block, c.bytes, p->device, s))) return rc;
         void* b = p->asm_block;
         p->state = at<int>(b, o_state); p->pending = at<int>(b, o_pend);
@@ -541,6 +542,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
         p->slot_pass = at<unsigned char>(b, o_sp); p->row_ptr = at<long long>(b, o_rp);
         p->col = at<int>(b, o_col); p->val = at<double>(b, o_val);
         p->lam_row = at<double>(b, o_lam); p->is_center = at<unsigned char>(b, o_isc);
+        p->spec = at<int>(b, o_spec);
         p->have_asm = true;
     }
     SolveArgs a{};
@@ -549,6 +551,8 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     for (int l = 0; l <= kMaxEll; ++l) { a.boff[l] = p->boff[l]; a.Mof[l] = p->Mof[l]; }
     a.node_n = p->node_n; a.node_ell = p->node_ell; a.node_m = p->node_m;
     a.bc = p->n_boundary > 0 ? p->bc : nullptr;
+    // speculation only pays where centers wait on each other (retention balls beyond the center)
+    a.spec = p->max_ball > 1 ? p->spec : nullptr;
     a.nrm = p->nrm;
     a.N = (int)p->N; a.n = p->n; a.M = p->M; a.K = p->K; a.m = p->m; a.ell = p->ell;
     a.qcap = p->qcap; a.stride = p->stride; a.mode = p->opts.stab_mode;
@@ -661,6 +665,8 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
         out->n_centers = (int64_t)c.n_centers;
         out->n_fallback = (int64_t)c.n_fallback;
         out->n_boundary = (int64_t)p->n_boundary;
+        out->n_speculated = (int64_t)c.n_spec;
+        out->n_spec_used = (int64_t)c.n_spec_used;
         out->n_rejected = (int64_t)c.n_rejected;
         out->sum_cols = (int64_t)c.sum_cols;
         out->n_singular = c.n_singular;

@@ -672,9 +672,10 @@ __device__ void on_covered(const SolveArgs& a, int i) {
 
 __global__ void k_traversal_init(int N, const int* __restrict__ indeg,
                                  const unsigned char* __restrict__ bc, int* state, int* pending,
-                                 int* owner, int* queue, unsigned char* fb_flag) {
+                                 int* owner, int* queue, unsigned char* fb_flag, int* spec) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         state[i] = (bc && bc[i]) ? kBoundary : kUndecided;
+        if (spec) spec[i] = 0;
         pending[i] = indeg[i];
         owner[i] = kNoOwner;
         queue[i] = -1;
@@ -709,6 +710,25 @@ __global__ void k_traversal_seed(SolveArgs a) {
     }
 }
 
+// Speculation.  At delta < 1 a center can wait on earlier centers (a chain of dependency
+// levels), so CTAs can find the queue empty.  Such a CTA solves ahead the lowest-index node
+// that is still undecided: its center column and every later ball member not owned by an
+// earlier center at that moment, all written to the node's own weight slots.  Ownership only
+// moves to earlier centers, so the columns the node needs if it does become a center are a
+// subset of these, and their arithmetic is the same as in a regular solve (the columns of a
+// factorization are independent); the center then only runs the test and publishes.  A node
+// that ends up covered wastes its speculative solve, done while the CTA would have been idle.
+__device__ int pick_spec(const SolveArgs& a) {
+    for (int tries = 0; tries < 8; ++tries) {
+        const int k = atomicAdd(&a.ctr->spec_next, 1);
+        if (k >= a.N) return -1;
+        if (*((volatile int*)&a.state[k]) != kUndecided) continue;
+        if (atomicCAS(&a.spec[k], 0, 1) != 0) continue;
+        return k;
+    }
+    return -1;
+}
+
 // One CTA per center.  Thread 0 claims the next queue slot and waits (bounded) for it to be
 // filled; the CTA then solves the center, tests and writes its columns, and resolves the
 // traversal state of its ball members.
@@ -717,7 +737,7 @@ __global__ void k_traversal_seed(SolveArgs a) {
 template <int D, bool PACKED, int NT>
 __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
-    __shared__ int s_j, s_q, s_rej, s_own;
+    __shared__ int s_j, s_q, s_rej, s_own, s_k, s_sp;
     const short* sbasis = load_basis(smem, a.basis, a.basis_count);
     StencilSmem sm;
     carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
@@ -725,11 +745,12 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ns = a.n, N = a.N;  // ns: row stride of nbr and of a weight slot
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    int slot = -1;  // thread 0: the claimed queue slot, kept while the CTA speculates
 
     for (;;) {
         if (tid == 0) {
-            int j = -1;
-            const int slot = atomicAdd(&a.ctr->q_head, 1);
+            int j = -1, k = -1, sp = 0;
+            if (slot < 0) slot = atomicAdd(&a.ctr->q_head, 1);
             if (slot < N) {
                 const unsigned long long t0 = globaltimer_ns();
                 unsigned nsl = 32;
@@ -746,18 +767,28 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
                         j = -1;
                         break;
                     }
+                    if (a.spec && (k = pick_spec(a)) >= 0) break;  // idle: solve ahead
                     __nanosleep(nsl);
                     if (nsl < 2048) nsl <<= 1;
                 }
             }
-            if (j >= 0) fence_gpu();  // acquire what the centers that released j published
+            if (j >= 0) {
+                slot = -1;
+                if (a.spec) sp = *((volatile int*)&a.spec[j]);
+                fence_gpu();  // acquire what the centers that released j (or its solve) published
+            }
             s_j = j;
+            s_k = k;
+            s_sp = sp;
             s_rej = 0;
             s_own = 0;
         }
         __syncthreads();
-        const int j = s_j;
-        if (j < 0) break;
+        const int jc = s_j, ks = s_k;
+        if (jc < 0 && ks < 0) break;
+        const bool ahead = jc < 0;           // a speculative solve of node ks
+        const bool made = !ahead && s_sp == 2;  // center jc whose solve was made ahead
+        const int j = ahead ? ks : jc;
         const Shape sh = shape_of<D>(a, sbasis, j);
         const int n = sh.n;
 
@@ -785,11 +816,35 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
         }
         __syncthreads();
         const int q = s_q;
-        const bool ok = solve_local<D, PACKED, NT>(a, sh, j, q, sm);
-        if (ok) lebesgue_values<NT>(n, sh.K, q, sm);
-        __syncthreads();
-        // Lebesgue test (§4.2.1) per column
         const long long base = a.slot_off[j];
+        double r2c = a.rho2[j];
+        if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
+        const double inv_r2 = rcp_fixed(r2c);
+        bool ok = true;
+        if (made) {  // the Lebesgue values of the solve made ahead
+            for (int c = tid; c < q; c += NT) sm.lam[c] = __ldcg(&a.slot_lam[base + sm.cols[c]]);
+        } else {
+            ok = solve_local<D, PACKED, NT>(a, sh, j, q, sm);
+            if (ok) lebesgue_values<NT>(n, sh.K, q, sm);
+        }
+        __syncthreads();
+        if (ahead) {  // publish every column, then the node's flag
+            if (ok) {
+                for (int e = tid; e < q * n; e += NT) {
+                    const int c = e / n, r = e - c * n;
+                    a.slot_w[(base + sm.cols[c]) * ns + r] = sm.X[sm.rowof[r] * sm.xs + c] * inv_r2;
+                }
+                for (int c = tid; c < q; c += NT) a.slot_lam[base + sm.cols[c]] = sm.lam[c];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                fence_gpu();
+                atomicExch(&a.spec[j], ok ? 2 : 3);
+                atomicAdd(&a.ctr->n_spec, 1ull);
+            }
+            continue;
+        }
+        // Lebesgue test (§4.2.1) per column
         int failed = 0, own = 0;
         for (int c = tid; c < q; c += NT) {
             const double lam = ok ? sm.lam[c] : nan;
@@ -808,10 +863,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
         if (failed) atomicAdd_block(&s_rej, failed);
         if (own) atomicAdd_block(&s_own, own);
         __syncthreads();
-        double r2c = a.rho2[j];
-        if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
-        const double inv_r2 = rcp_fixed(r2c);
-        for (int e = tid; e < q * n; e += NT) {
+        for (int e = tid; !made && e < q * n; e += NT) {  // (made ahead: already in the slots)
             const int c = e / n, r = e - c * n;
             if (!sm.keep[c]) continue;
             a.slot_w[(base + sm.cols[c]) * ns + r] =
@@ -845,6 +897,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
             atomicAdd(&a.ctr->n_centers, 1ull);
             atomicAdd(&a.ctr->sum_cols, (unsigned long long)q);
             atomicAdd(&a.ctr->n_rejected, (unsigned long long)s_rej);
+            if (made) atomicAdd(&a.ctr->n_spec_used, 1ull);
             atomicAdd(&a.ctr->done, 1);
         }
         __syncthreads();
@@ -1217,7 +1270,7 @@ static int traversal(const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
     const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
     const int tb = 256, nb = (a.N + tb - 1) / tb;
     k_traversal_init<<<nb, tb, 0, s>>>(a.N, indeg, a.bc, a.state, a.pending, a.owner, a.queue,
-                                       a.fb_flag);
+                                       a.fb_flag, a.spec);
     if (a.bc) {
         k_boundary_release<<<nb, tb, 0, s>>>(a);
         ++*launches;

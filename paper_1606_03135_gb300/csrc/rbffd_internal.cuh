@@ -64,7 +64,11 @@ struct DevCounters {
     unsigned long long n_fallback;
     unsigned long long sum_k3;   // sum over factored stencils of K^3
     unsigned long long sum_k2q;  // sum over factored stencils of K^2 (rows they own)
-    unsigned long long pad[20];
+    unsigned long long n_spec;       // speculative solves made by idle CTAs
+    unsigned long long n_spec_used;  // centers that found their solve already made
+    int spec_next;                   // next node an idle CTA considers for speculation
+    int pad_i;
+    unsigned long long pad[17];
 };
 
 // Map a CUDA status to an RBFFD code; with RBFFD_DEBUG set in the environment the failing
@@ -132,6 +136,7 @@ struct SolveArgs {
     const signed char* node_ell;
     const signed char* node_m;
     const unsigned char* bc;   // boundary kind per node (0 interior, 1 Dirichlet, 2 Neumann) or null
+    int* spec;                 // per node: 0 none, 1 speculative solve running, 2 made, 3 singular
     const double* nrm;         // unit normals [N][d] of Neumann nodes (or null)
     int N, n, M, K, m, ell;
     int qcap;                  // columns room per stencil

@@ -39,7 +39,8 @@ class rbffd_stats_t(C.Structure):
                 ("n_launches", C.c_int64), ("ms_stencils", C.c_float),
                 ("ms_traversal", C.c_float), ("ms_fallback", C.c_float),
                 ("ms_finalize", C.c_float), ("nnz", C.c_int64), ("plan_bytes", C.c_int64),
-                ("assemble_bytes", C.c_int64), ("n_boundary", C.c_int64)]
+                ("assemble_bytes", C.c_int64), ("n_boundary", C.c_int64),
+                ("n_speculated", C.c_int64), ("n_spec_used", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -58,7 +58,7 @@ def estimate_bytes(N: int, d: int, n: int, delta: float) -> int:
     bounded by the stencil size; the exact figure is known after the plan."""
     ball = 1 if delta >= 1.0 else n
     plan = N * (d * 8 + n * 4 + 8 + 4 + 4 + 8) + (2 * N + 64) * 12 + N * (8 + 8 * d)
-    asm = N * (4 * 5 + 2 + n * 12 + 16) + N * ball * (n * 8 + 9)
+    asm = N * (4 * 6 + 2 + n * 12 + 16) + N * ball * (n * 8 + 9)
     return int(plan + asm + (1 << 20))
 
 
