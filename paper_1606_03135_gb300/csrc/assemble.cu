@@ -719,14 +719,9 @@ __global__ void k_traversal_seed(SolveArgs a) {
 // factorization are independent); the center then only runs the test and publishes.  A node
 // that ends up covered wastes its speculative solve, done while the CTA would have been idle.
 __device__ int pick_spec(const SolveArgs& a) {
-    for (int tries = 0; tries < 8; ++tries) {
-        const int k = atomicAdd(&a.ctr->spec_next, 1);
-        if (k >= a.N) return -1;
-        if (*((volatile int*)&a.state[k]) != kUndecided) continue;
-        if (atomicCAS(&a.spec[k], 0, 1) != 0) continue;
-        return k;
-    }
-    return -1;
+    const int k = atomicAdd(&a.ctr->spec_next, 1);  // one candidate per idle poll
+    if (k >= a.N || *((volatile int*)&a.state[k]) != kUndecided) return -1;
+    return atomicCAS(&a.spec[k], 0, 1) == 0 ? k : -1;
 }
 
 // One CTA per center.  Thread 0 claims the next queue slot and waits (bounded) for it to be
