@@ -123,8 +123,12 @@ typedef struct {
  *   opts    NULL for defaults.
  *   out     receives the plan.
  * Runs the exact kNN search and the retention balls on the device and waits for the
- * stream once (to size the local systems).  Errors: RBFFD_EINVAL, RBFFD_EDUPLICATE,
- * RBFFD_ENOMEM, RBFFD_ECUDA.  On error *out is NULL and nothing leaks. */
+ * stream once (to size the local systems).  Each local system lives in one SM's shared
+ * memory with its right-hand sides: with K = n + M and q the largest retention ball,
+ * about 8 (K (K + 1) / 2 + K q + 7 K) bytes (LU option: 8 K (K + q + 5)) must fit the
+ * device's per-block limit (227 KB on GB300), else RBFFD_EINVAL; e.g. n = 128 with degree 7
+ * fits at delta = 1 but not with balls of 100 nodes.  Errors: RBFFD_EINVAL,
+ * RBFFD_EDUPLICATE, RBFFD_ENOMEM, RBFFD_ECUDA.  On error *out is NULL and nothing leaks. */
 int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
                const rbffd_opts* opts, void* stream, rbffd_plan_t* out);
 

@@ -370,3 +370,22 @@ def test_mixed_entry_with_uniform_parameters_equals_the_uniform_plan():
     b = gpu_run_mixed(X, np.full(N, 12), np.full(N, 2), np.full(N, 3), 0.5)
     for key in ("row_ptr", "col", "val", "owner", "nbr", "ball_len", "lam_row"):
         assert np.array_equal(a[key], b[key]), key
+
+
+# ------------------------------------------------------------------ the largest stencils
+def test_largest_stencil_size_matches_the_oracle():
+    """n = 128 (the limit), K = 134: one 512-thread team per system."""
+    X = NS.jittered_grid(40, 2, seed=21)
+    g, _ = compare(X, 128, 2, 3, 1.0)
+    assert g["stats"]["K"] == 134
+
+
+def test_systems_too_large_for_shared_memory_are_rejected():
+    """n = 128 with degree 7 (K = 164) fits at delta = 1 but not with balls of ~110 nodes
+    (right-hand sides beside the system): the plan says RBFFD_EINVAL."""
+    X = torch.from_numpy(NS.jittered_grid(40, 2, seed=21)).cuda()
+    with R.Plan(X, 128, 7, 7, 1.0) as p:
+        assert p.stats()["K"] == 164
+    with pytest.raises(R.RbffdError) as e:
+        R.Plan(X, 128, 7, 7, 0.05)
+    assert e.value.code == R.EINVAL
