@@ -360,6 +360,8 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
     const int W = knn_words(n);
     unsigned long long* wk = knn_smem + (size_t)wib * W;
     int* wi = reinterpret_cast<int*>(knn_smem + (size_t)wpb * W) + (size_t)wib * W;
+    int* soff = reinterpret_cast<int*>(knn_smem + (size_t)wpb * W) + (size_t)wpb * W + wib * 64;
+    int* sbeg = soff + 32;
     const GridParams g = *gp;
 
     for (int q = blockIdx.x * wpb + wib; q < N; q += gridDim.x * wpb) {
@@ -379,29 +381,55 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
             cnt = 0;
             const int ny = chi[1] - clo[1] + 1;
             const int nz = (D == 3) ? chi[2] - clo[2] + 1 : 1;
-            for (int rz = 0; rz < nz && cnt <= kCollect; ++rz)
-                for (int ry = 0; ry < ny && cnt <= kCollect; ++ry) {
+            const int nrows = ny * nz;
+            // The box's cell rows (contiguous ranges of the cell-sorted nodes) are packed into
+            // full batches of 32 candidates: an FP64 warp instruction costs the same with idle
+            // lanes, and a row holds only a few nodes.  Lane l takes row g0 + l, the rows'
+            // offsets are scanned, and each candidate finds its row by binary search.
+            for (int g0 = 0; g0 < nrows && cnt <= kCollect; g0 += 32) {
+                const int R = g0 + lane;
+                int beg = 0, len = 0;
+                if (R < nrows) {
+                    const int rz = R / ny, ry = R - rz * ny;
                     int cc[3] = {clo[0], clo[1] + ry, (D == 3) ? clo[2] + rz : 0};
                     const int row0 = cell_index<D>(g, cc);
-                    const int beg = cell_start[row0];
-                    const int end = cell_start[row0 + (chi[0] - clo[0]) + 1];
-                    for (int b0 = beg; b0 < end && cnt <= kCollect; b0 += 32) {
-                        const int p = b0 + lane;
-                        unsigned long long key = ~0ull;
-                        int id = 0;
-                        if (p < end) {
-                            double xp[3];
-                            for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)p * D + a];
-                            key = dkey(sqdist_rn<D>(xq, xp));
-                            id = sorted_idx[p];
-                        }
-                        const bool in = p < end && key < bkey;
-                        const unsigned bal = __ballot_sync(0xffffffffu, in);
-                        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-                        if (in && pos < kCollect) { wk[pos] = key; wi[pos] = id; }
-                        cnt += __popc(bal);
-                    }
+                    beg = cell_start[row0];
+                    len = cell_start[row0 + (chi[0] - clo[0]) + 1] - beg;
                 }
+                int incl = len;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int total = __shfl_sync(0xffffffffu, incl, 31);
+                soff[lane] = incl - len;
+                sbeg[lane] = beg;
+                __syncwarp();
+                for (int b0 = 0; b0 < total && cnt <= kCollect; b0 += 32) {
+                    const int e = b0 + lane;
+                    unsigned long long key = ~0ull;
+                    int id = 0;
+                    if (e < total) {
+                        int lo = 0, hi = 31;  // the last row whose offset is <= e (non-empty)
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (soff[mid] <= e) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const int p = sbeg[lo] + (e - soff[lo]);
+                        double xp[3];
+                        for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)p * D + a];
+                        key = dkey(sqdist_rn<D>(xq, xp));
+                        id = sorted_idx[p];
+                    }
+                    const bool in = e < total && key < bkey;
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                    if (in && pos < kCollect) { wk[pos] = key; wi[pos] = id; }
+                    cnt += __popc(bal);
+                }
+                __syncwarp();  // soff/sbeg are rewritten by the next group
+            }
             if (cnt > kCollect || cnt >= n || all) break;
             ++r;
         }
@@ -516,7 +544,7 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     k_cell_fill<D><<<nb, tb, 0, s>>>(X, N, cell_of, start, cursor, sorted_idx, sorted_X);
     const int wpb = 8;
     const int words = knn_words(n);
-    size_t smem = (size_t)wpb * words * (sizeof(unsigned long long) + sizeof(int));
+    size_t smem = (size_t)wpb * (words * (sizeof(unsigned long long) + sizeof(int)) + 64 * sizeof(int));
     if (smem > 48 * 1024 &&
         (rc = RB_CUDA(cudaFuncSetAttribute(k_knn<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem))))
