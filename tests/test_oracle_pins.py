@@ -221,8 +221,10 @@ def _acc(X, nbr, bl, j, ell, m):
 
 
 @pytest.mark.parametrize("mode", [O.STAB_SEQ, O.STAB_OFF, O.STAB_FALLBACK])
-@pytest.mark.parametrize("delta", [0.25, 0.5, 0.8])
+@pytest.mark.parametrize("delta", [1e-9, 0.25, 0.5, 0.8])
 def test_traversal_satisfies_its_unique_characterisation(mode, delta):
+    # delta -> 0: every ball is the whole stencil, so a center's retained set is the
+    # uncovered part of its stencil (§4.1).
     # The index-order traversal is the unique assignment in which node k is a center iff no
     # earlier center keeps it, and each kept row belongs to the earliest center keeping it.
     X = NS.disk2d(300, seed=21)
@@ -270,6 +272,50 @@ def test_delta_one_is_standard_rbffd():
     r = O.assemble(X, 12, 2, 3, 1.0)
     assert np.all(r["is_center"] == 1) and np.array_equal(r["owner"], np.arange(400))
     assert r["stats"]["n_centers"] == 400 and r["stats"]["n_decisions"] == 0
+
+
+def test_delta_one_matches_a_separately_coded_standard_rbffd():
+    """Every row at delta = 1 is standard RBF-FD: the Laplacian weights of the node's own
+    stencil, here from a separate numpy/LAPACK construction of the local system."""
+    from tests.hp_reference import lapack_weights
+    X = NS.disk2d(400, seed=5)
+    n, ell, m = 12, 2, 3
+    r = O.assemble(X, n, ell, m, 1.0)
+    for i in range(0, 400, 7):
+        idx = r["nbr"][i]
+        w = lapack_weights(X, idx, ell, m, X[i]).ravel()
+        order = np.argsort(idx)
+        sl = slice(r["row_ptr"][i], r["row_ptr"][i + 1])
+        assert np.abs(r["val"][sl] - w[order]).max() <= 1e-10 * np.abs(w).max()
+
+
+def test_multi_rhs_columns_equal_single_rhs_solves():
+    """The overlapped solve (§4.1): each column of a multi-right-hand-side solve is the
+    single-right-hand-side solve at that point, bit for bit (one factorization serves all)."""
+    X = NS.disk2d(300, seed=6)
+    nbr, _ = O.knn(X, 20)
+    idx = nbr[17]
+    Y = X[idx[:9]]
+    W, lam = O.local_weights(X, idx, 3, 5, Y)
+    for e in range(9):
+        w1, l1 = O.local_weights(X, idx, 3, 5, Y[e:e + 1])
+        assert np.array_equal(W[:, e], w1[:, 0]) and lam[e] == l1[0]
+
+
+@pytest.mark.parametrize("delta", [1.0, 0.5])
+def test_gershgorin_radius_is_the_local_lebesgue_value(delta):
+    """§4.2: the Gershgorin radius of row i of L is its local Lebesgue value (in the units of
+    L) minus the diagonal magnitude: sum_{j != i} |L_ij| = Lambda_i / rho_owner^2 - |L_ii|."""
+    X = NS.disk2d(500, seed=8)
+    r = O.assemble(X, 12, 2, 3, delta)
+    rho2 = r["d2"][:, -1]
+    for i in range(500):
+        sl = slice(r["row_ptr"][i], r["row_ptr"][i + 1])
+        cols, vals = r["col"][sl], r["val"][sl]
+        diag = abs(vals[cols == i][0])
+        g = np.abs(vals[cols != i]).sum()
+        lam = r["lam_row"][i] / rho2[r["owner"][i]]
+        assert abs(g - (lam - diag)) <= 1e-12 * lam
 
 
 def test_stabilization_is_active_on_small_stencils():
