@@ -67,6 +67,14 @@ typedef struct {
                            32 (one warp per stencil), 64, 96, 128 or 512 to force one (used
                            by the schedule autotuner); 32, 64 and 96 need RBFFD_FACTOR_LDLT,
                            else RBFFD_EINVAL */
+    int rhs_chunk;      /* right-hand sides carried through one factorization (RBFFD_FACTOR_LDLT):
+                           a center with more columns solves the rest afterwards, this many at
+                           a time, with the stored factors (same results, bit for bit).  0 = all
+                           columns of the largest retention ball when that system fits shared
+                           memory, else the largest count that fits; k >= 1 = at most k (fewer
+                           columns per CTA can keep more stencils resident per SM: a tuning
+                           knob, see autotune).  Values < 0, or > 0 with RBFFD_FACTOR_LU, give
+                           RBFFD_EINVAL */
 } rbffd_opts;
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */
@@ -108,6 +116,8 @@ typedef struct {
     int64_t n_boundary;      /* boundary rows (rbffd_set_boundary) */
     int64_t n_speculated;    /* solves made ahead by CTAs that found no ready center */
     int64_t n_spec_used;     /* centers whose solve had been made ahead */
+    int64_t rhs_chunk;       /* right-hand sides carried per factorization (opts.rhs_chunk as
+                                chosen by rbffd_plan) */
 } rbffd_stats_t;
 
 /* rbffd_plan -- build the stencils of §4.1 for one node set.
@@ -124,10 +134,11 @@ typedef struct {
  *   out     receives the plan.
  * Runs the exact kNN search and the retention balls on the device and waits for the
  * stream once (to size the local systems).  Each local system lives in one SM's shared
- * memory with its right-hand sides: with K = n + M and q the largest retention ball,
- * about 8 (K (K + 1) / 2 + K q + 7 K) bytes (LU option: 8 K (K + q + 5)) must fit the
- * device's per-block limit (227 KB on GB300), else RBFFD_EINVAL; e.g. n = 128 with degree 7
- * fits at delta = 1 but not with balls of 100 nodes.  Errors: RBFFD_EINVAL,
+ * memory with q of its right-hand sides: with K = n + M, about 8 (K (K + 1) / 2 + K q + 7 K)
+ * bytes (LU option: 8 K (K + q + 5)) must fit the device's per-block limit (227 KB on GB300).
+ * LU carries every column (q = the largest retention ball); LDL^T carries opts->rhs_chunk
+ * columns and solves the rest in chunks of that many, so its limit is q = 1: in 3D,
+ * n = 128 with degree 7 (K = 248) is too large.  Else RBFFD_EINVAL.  Errors: RBFFD_EINVAL,
  * RBFFD_EDUPLICATE, RBFFD_ENOMEM, RBFFD_ECUDA.  On error *out is NULL and nothing leaks. */
 int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
                const rbffd_opts* opts, void* stream, rbffd_plan_t* out);

@@ -342,13 +342,14 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
             K_max = nk + Mk > K_max ? nk + Mk : K_max;
         }
     }
-    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0};
+    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0, 0};
     if (opts) o = *opts;
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
         (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0 ||
         (o.team != 0 && o.team != 32 && o.team != 64 && o.team != 96 && o.team != 128 &&
          o.team != 512) ||
-        (o.factor == RBFFD_FACTOR_LU && o.team != 0 && o.team != 128 && o.team != 512))
+        (o.factor == RBFFD_FACTOR_LU && o.team != 0 && o.team != 128 && o.team != 512) ||
+        o.rhs_chunk < 0 || (o.factor == RBFFD_FACTOR_LU && o.rhs_chunk > 0))
         return RBFFD_EINVAL;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
 
@@ -358,7 +359,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
     p->N = N; p->d = d; p->n = n; p->ell = ell; p->m = m; p->M = K_max - n; p->K = K_max;
     p->delta = delta; p->opts = o; p->last = s; p->mixed = mixed;
     cudaGetDevice(&p->device);
-    int rc = RBFFD_OK;
+    int rc = RBFFD_OK, qmax = 1;  // qmax: columns of the largest retention ball
     void* scratch = nullptr;
     const int Ni = (int)N;
     const int ncell_max = 2 * Ni + 64;
@@ -456,13 +457,23 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         c.add<double>(Nz * nz); c.add<double>(Nz); c.add<unsigned char>(Nz); c.add<int>(Nz);
         p->asm_bytes = c.bytes;
     }
-    p->qcap = p->max_ball < 1 ? 1 : p->max_ball;
+    // right-hand-side columns carried through one factorization: every column of the largest
+    // ball (LU always), or with LDL^T fewer, opts.rhs_chunk or as many as shared memory holds
+    // (the rest are solved in chunks of that many)
+    qmax = p->max_ball < 1 ? 1 : (int)p->max_ball;
+    p->qcap = qmax;
+    if (o.rhs_chunk > 0 && o.rhs_chunk < p->qcap) p->qcap = o.rhs_chunk;
     {
-        int stride = 0;
-        const size_t per_cta = solve_smem_per_cta(n, p->K, p->qcap, d,
-                                                  o.factor == RBFFD_FACTOR_LDLT, &stride) +
-                               basis_smem_bytes((int)basis_count);
+        const bool ldlt = o.factor == RBFFD_FACTOR_LDLT;
         const size_t avail = (size_t)max_optin_smem() - 64;
+        int stride = 0;
+        size_t per_cta = 0;
+        for (;;) {
+            per_cta = solve_smem_per_cta(n, p->K, p->qcap, qmax, d, ldlt, &stride) +
+                      basis_smem_bytes((int)basis_count);
+            if (per_cta <= avail || !ldlt || p->qcap == 1) break;
+            --p->qcap;
+        }
         p->stride = stride;
         if (per_cta > avail) { rc = RBFFD_EINVAL; goto fail; }
         // fallback classes: one per degree in use (per-node stencils) or one for all nodes
@@ -484,7 +495,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
                 }
         }
         p->lp.force_nt = o.team;
-        rc = prepare_solve_kernels(d, o.factor == RBFFD_FACTOR_LDLT, n, p->K, p->qcap,
+        rc = prepare_solve_kernels(d, o.factor == RBFFD_FACTOR_LDLT, n, p->K, p->qcap, qmax,
                                    (int)basis_count, &p->lp);
         if (rc) goto fail;
     }
@@ -556,6 +567,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.nrm = p->nrm;
     a.N = (int)p->N; a.n = p->n; a.M = p->M; a.K = p->K; a.m = p->m; a.ell = p->ell;
     a.qcap = p->qcap; a.stride = p->stride; a.mode = p->opts.stab_mode;
+    a.qmax = p->max_ball < 1 ? 1 : (int)p->max_ball;
     a.coef = (double)(p->m * (p->m + p->d - 2));
     a.timeout_ns = (unsigned long long)p->opts.timeout_ms * 1000000ull;
     a.state = p->state; a.pending = p->pending; a.owner = p->owner; a.queue = p->queue;
@@ -655,6 +667,7 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
     const DevCounters& c = p->h_ctr;
     out->n_nodes = p->N;
     out->max_ball = p->max_ball;
+    out->rhs_chunk = p->qcap;
     out->n = p->n; out->M = p->M; out->K = p->K; out->d = p->d;
     out->n_launches = p->launches;
     out->plan_bytes = (int64_t)p->plan_bytes;

@@ -65,10 +65,10 @@ struct StencilSmem {
     int* perm;      // K  original unknown held by each row (symmetric pivoting)
     int* rowof;     // K  row holding each original unknown
     unsigned char* pk;  // K  1: 1x1 pivot, 2: first row of a 2x2 pivot, 0: its second row
-    double* lam;    // qcap Lebesgue values of the solved columns
-    int* cols;      // qcap ball position of each solved column
+    double* lam;    // qmax Lebesgue values of the solved columns (all chunks)
+    int* cols;      // qmax ball position of each solved column
     int* colof;     // n column of each ball position, or -1
-    unsigned char* keep;  // qcap kept-for-coverage flags
+    unsigned char* keep;  // qmax kept-for-coverage flags
 };
 
 __host__ __device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
@@ -109,21 +109,22 @@ __device__ __forceinline__ Shape shape_of(const SolveArgs& a, const short* sbasi
 }
 
 // Bytes of one CTA's local system; *stride_out is S (full) or xs (packed).
-size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride_out) {
+size_t solve_smem_per_cta(int n, int K, int qcap, int qmax, int D, int packed,
+                          int* stride_out) {
     int stride = packed ? qcap : K + qcap;
     if ((stride & 1) == 0) ++stride;  // odd row stride: column walks hit distinct banks
     if (stride_out) *stride_out = stride;
     const size_t mat = packed ? ((size_t)tri(K) + 1) / 2 * 2 + (size_t)K * stride
                               : (size_t)K * stride;
-    size_t b = mat * 8 + (size_t)n * D * 8 + (size_t)K * 5 * 8 + (size_t)qcap * 8 +
-               (size_t)(qcap + n) * 4 + (size_t)K * 2 * 4 + (size_t)K + (size_t)qcap;
+    size_t b = mat * 8 + (size_t)n * D * 8 + (size_t)K * 5 * 8 + (size_t)qmax * 8 +
+               (size_t)(qmax + n) * 4 + (size_t)K * 2 * 4 + (size_t)K + (size_t)qmax;
     return (b + 15) & ~size_t(15);
 }
 
 size_t basis_smem_bytes(int count) { return ((size_t)count * sizeof(short) + 15) & ~size_t(15); }
 
 template <int D, bool PACKED>
-__device__ __forceinline__ void carve(char* p, int n, int K, int qcap, int S, StencilSmem& sm) {
+__device__ __forceinline__ void carve(char* p, int n, int K, int qmax, int S, StencilSmem& sm) {
     if (PACKED) {
         sm.A = nullptr;
         sm.T = reinterpret_cast<double*>(p);
@@ -151,9 +152,9 @@ __device__ __forceinline__ void carve(char* p, int n, int K, int qcap, int S, St
     sm.wv2 = reinterpret_cast<double*>(p);
     p += (size_t)K * 8;
     sm.lam = reinterpret_cast<double*>(p);
-    p += (size_t)qcap * 8;
+    p += (size_t)qmax * 8;
     sm.cols = reinterpret_cast<int*>(p);
-    p += (size_t)qcap * 4;
+    p += (size_t)qmax * 4;
     sm.colof = reinterpret_cast<int*>(p);
     p += (size_t)n * 4;
     sm.perm = reinterpret_cast<int*>(p);
@@ -238,8 +239,8 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
                     sm.A[rb * xs + ra] = pm;
                 }
                 const int ca = sm.colof[ra], cb = sm.colof[rb];
-                if (cb >= 0) X[ra * xs + cb] = __dmul_rn(sh.coef, pm2);
-                if (ca >= 0) X[rb * xs + ca] = __dmul_rn(sh.coef, pm2);
+                if (cb >= 0 && cb < q) X[ra * xs + cb] = __dmul_rn(sh.coef, pm2);
+                if (ca >= 0 && ca < q) X[rb * xs + ca] = __dmul_rn(sh.coef, pm2);
             }
             pr += di;
             off += dj;
@@ -364,6 +365,80 @@ __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
         __syncthreads();
     }
     return true;
+}
+
+// D solve and back substitution of the right-hand-side columns 0 .. q-1 held in sm.X, after
+// the forward substitution (carried through the factorization, or forward_subst).
+template <int NT>
+__device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem& sm) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int xs = sm.xs;
+    double* T = sm.T;
+    double* X = sm.X;
+    // D solve: 1x1 rows scale by the reciprocal pivot, 2x2 blocks multiply by their inverse;
+    // then back substitution with L^T: once x_i is final, x_j -= L[i][j] x_i for j < i.
+    // With at most one column per warp (q <= NW), warp w owns column w and its K sequential
+    // steps need only warp synchronisation; otherwise all threads share every step (the
+    // flattened (row, column) pairs keep the lanes busy) with a barrier per step.  Both do
+    // the same operations on every element.
+    constexpr int NW = NT / 32;
+    if (q <= NW) {
+        if (wid < q) {
+            double* Xc = X + wid;
+            for (int i = lane; i < K; i += 32) {
+                const int k = sm.pk[i];
+                double* Bi = Xc + i * xs;
+                if (k == 1) {
+                    *Bi *= sm.rdiag[i];
+                } else if (k == 2) {  // rows i, i + 1 form a 2x2 block
+                    double* Bn = Bi + xs;
+                    const double y0 = *Bi, y1 = *Bn;
+                    *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
+                    *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
+                }
+            }
+            __syncwarp();
+            for (int i = K - 1; i > 0; --i) {
+                const double* Li = T + tri(i);
+                const double xv = Xc[i * xs];
+                for (int jj = lane; jj < i; jj += 32) Xc[jj * xs] = fma(-Li[jj], xv, Xc[jj * xs]);
+                __syncwarp();
+            }
+        }
+        return;
+    }
+    for (int e = tid; e < K * q; e += NT) {
+        const int i = e / q, c = e - (e / q) * q;
+        const int k = sm.pk[i];
+        double* Bi = X + i * xs + c;
+        if (k == 1) {
+            *Bi *= sm.rdiag[i];
+        } else if (k == 2) {
+            double* Bn = Bi + xs;
+            const double y0 = *Bi, y1 = *Bn;
+            *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
+            *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
+        }
+    }
+    __syncthreads();
+    for (int i = K - 1; i > 0; --i) {
+        const int total = i * q;
+        if (tid < total) {
+            int jj = tid / q, cc = tid - (tid / q) * q;
+            const int dj = NT / q, dc = NT - dj * q;
+            const double* Li = T + tri(i);
+            const double* xi = X + i * xs;
+#pragma unroll 4
+            for (int e = tid; e < total; e += NT) {
+                double* xj = X + jj * xs;
+                xj[cc] = fma(-Li[jj], xi[cc], xj[cc]);
+                jj += dj;
+                cc += dc;
+                if (cc >= q) { cc -= q; ++jj; }
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // Symmetric indefinite LDL^T factorization with Bunch-Kaufman partial pivoting (J. R. Bunch
@@ -545,70 +620,7 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
     }
     // The inverse permutation (read after the caller's next barrier).
     for (int r = tid; r < K; r += NT) sm.rowof[sm.perm[r]] = r;
-    // D solve: 1x1 rows scale by the reciprocal pivot, 2x2 blocks multiply by their inverse;
-    // then back substitution with L^T: once x_i is final, x_j -= L[i][j] x_i for j < i.
-    // With at most one column per warp (q <= NW), warp w owns column w and its K sequential
-    // steps need only warp synchronisation; otherwise all threads share every step (the
-    // flattened (row, column) pairs keep the lanes busy) with a barrier per step.  Both do
-    // the same operations on every element.
-    constexpr int NW = NT / 32;
-    if (q <= NW) {
-        if (wid < q) {
-            double* Xc = X + wid;
-            for (int i = lane; i < K; i += 32) {
-                const int k = sm.pk[i];
-                double* Bi = Xc + i * xs;
-                if (k == 1) {
-                    *Bi *= sm.rdiag[i];
-                } else if (k == 2) {  // rows i, i + 1 form a 2x2 block
-                    double* Bn = Bi + xs;
-                    const double y0 = *Bi, y1 = *Bn;
-                    *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
-                    *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
-                }
-            }
-            __syncwarp();
-            for (int i = K - 1; i > 0; --i) {
-                const double* Li = T + tri(i);
-                const double xv = Xc[i * xs];
-                for (int jj = lane; jj < i; jj += 32) Xc[jj * xs] = fma(-Li[jj], xv, Xc[jj * xs]);
-                __syncwarp();
-            }
-        }
-        return true;
-    }
-    for (int e = tid; e < K * q; e += NT) {
-        const int i = e / q, c = e - (e / q) * q;
-        const int k = sm.pk[i];
-        double* Bi = X + i * xs + c;
-        if (k == 1) {
-            *Bi *= sm.rdiag[i];
-        } else if (k == 2) {
-            double* Bn = Bi + xs;
-            const double y0 = *Bi, y1 = *Bn;
-            *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
-            *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
-        }
-    }
-    __syncthreads();
-    for (int i = K - 1; i > 0; --i) {
-        const int total = i * q;
-        if (tid < total) {
-            int jj = tid / q, cc = tid - (tid / q) * q;
-            const int dj = NT / q, dc = NT - dj * q;
-            const double* Li = T + tri(i);
-            const double* xi = X + i * xs;
-#pragma unroll 4
-            for (int e = tid; e < total; e += NT) {
-                double* xj = X + jj * xs;
-                xj[cc] = fma(-Li[jj], xi[cc], xj[cc]);
-                jj += dj;
-                cc += dc;
-                if (cc >= q) { cc -= q; ++jj; }
-            }
-        }
-        __syncthreads();
-    }
+    ldlt_solve_tail<NT>(K, q, sm);
     return true;
 }
 
@@ -619,11 +631,103 @@ __device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
     return PACKED ? factor_solve_ldlt<NT>(sh.K, q, sm) : factor_solve_lu<NT>(sh.K, q, sm);
 }
 
+// ------------------------------------------------------------------ right-hand sides in chunks
+// The factorization carries at most a.qcap right-hand sides (shared memory is sized for that
+// many); a center with more solves the rest afterwards, a.qcap at a time, with the stored
+// factors.  Every column gets the same operations, in the same order, as it would have had
+// in the first chunk, so the weights do not depend on the chunk a column falls in.
+
+// psi_l(x) by the parent recurrence, multiplied in the order the monomial block is built.
+template <int D>
+__device__ __forceinline__ double mono_value(const Basis& bs, int l, const double* x) {
+    unsigned code = 0;  // the variables from l up to the constant, 2 bits each
+    int depth = 0;
+    while (l > 0) {
+        code = (code << 2) | (unsigned)bs.var[l];
+        ++depth;
+        l = bs.parent[l];
+    }
+    double v = 1.0;
+    for (int i = 0; i < depth; ++i) {
+        v = v * x[code & 3u];
+        code >>= 2;
+    }
+    return v;
+}
+
+// Right-hand sides of columns c0 .. c0+qk-1 into sm.X, rows in the factorization's permuted
+// order (row r holds unknown perm[r]).
+template <int D, int NT>
+__device__ void chunk_rhs(const Shape& sh, int c0, int qk, const StencilSmem& sm) {
+    const int K = sh.K, n = sh.n;
+    for (int e = threadIdx.x; e < K * qk; e += NT) {
+        const int r = e / qk, c = e - (e / qk) * qk;
+        const int u = sm.perm[r];
+        const int t = sm.cols[c0 + c];
+        double v = 0.0;
+        if (u < n) {
+            if (u != t) {  // m (m + D - 2) r^(m-2), as in the pair loop
+                const double r2 = sqdist_rn<D>(sm.xi + u * D, sm.xi + t * D);
+                double pm2 = sqrt_fast(r2);
+                for (int k = 0; k < (sh.m - 3) / 2; ++k) pm2 = __dmul_rn(pm2, r2);
+                v = __dmul_rn(sh.coef, pm2);
+            }
+        } else {  // Laplacian of psi_(u-n) at the column's node
+            const int l = u - n;
+            for (int d = 0; d < D; ++d) {
+                const int ch = sh.bs.lap_child[l * D + d];
+                if (ch >= 0)
+                    v = fma(exact_double(sh.bs.lap_coef[l * D + d]),
+                            mono_value<D>(sh.bs, ch, sm.xi + t * D), v);
+            }
+        }
+        sm.X[r * sm.xs + c] = v;
+    }
+}
+
+// Forward substitution with the unit lower factor, step by step as the factorization applied
+// it to the carried columns (a 2x2 pivot's two columns update a row in one expression).
+template <int NT>
+__device__ void forward_subst(int K, int q, const StencilSmem& sm) {
+    const int xs = sm.xs;
+    for (int p = 0; p < K;) {
+        const int k = sm.pk[p];
+        const int p0 = p + k - 1;
+        const int total = (K - p0 - 1) * q;
+        for (int e = threadIdx.x; e < total; e += NT) {
+            const int r = e / q, c = e - (e / q) * q;
+            const int i = p0 + 1 + r;
+            const double* Ti = sm.T + tri(i);
+            double* dst = sm.X + i * xs + c;
+            if (k == 1) *dst = fma(-Ti[p], sm.X[p * xs + c], *dst);
+            else *dst = fma(-Ti[p + 1], sm.X[(p + 1) * xs + c], fma(-Ti[p], sm.X[p * xs + c], *dst));
+        }
+        __syncthreads();
+        p += k;
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void lebesgue_values(int n, int K, int q, const StencilSmem& sm,
+                                                int off);
+
+// Columns c0 .. c0+qk-1 with the stored LDL^T factors: right-hand sides, forward substitution,
+// D solve, back substitution and Lebesgue values (a chunk after the first of a center).
+template <int D, int NT>
+__device__ __forceinline__ void solve_chunk(const Shape& sh, int c0, int qk, const StencilSmem& sm) {
+    chunk_rhs<D, NT>(sh, c0, qk, sm);
+    __syncthreads();
+    forward_subst<NT>(sh.K, qk, sm);
+    ldlt_solve_tail<NT>(sh.K, qk, sm);
+    lebesgue_values<NT>(sh.n, sh.K, qk, sm, c0);
+}
+
 // Local L-Lebesgue value sum_r |w_r| of every solved column: warp w sums the columns w, w + NW,
 // ... (the columns it back-substituted), over the unknowns u whose original index perm[u] is
 // a stencil node (not a polynomial coefficient).
 template <int NT>
-__device__ __forceinline__ void lebesgue_values(int n, int K, int q, const StencilSmem& sm) {
+__device__ __forceinline__ void lebesgue_values(int n, int K, int q, const StencilSmem& sm,
+                                                int off = 0) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = wid; c < q; c += (NT / 32)) {
         double s = 0.0;
@@ -632,7 +736,7 @@ __device__ __forceinline__ void lebesgue_values(int n, int K, int q, const Stenc
             s += sm.perm[u] < n ? fabs(v) : 0.0;
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) sm.lam[c] = s;
+        if (lane == 0) sm.lam[off + c] = s;
     }
 }
 
@@ -728,14 +832,16 @@ __device__ int pick_spec(const SolveArgs& a) {
 // filled; the CTA then solves the center, tests and writes its columns, and resolves the
 // traversal state of its ball members.
 // Registers are capped per team size (team_min_blocks) so that the CTAs that fit an SM's
-// shared memory also fit its register file.
-template <int D, bool PACKED, int NT>
+// shared memory also fit its register file.  CHUNKED (LDL^T only) is the instantiation for
+// plans whose largest ball has more columns than one factorization carries; the other one
+// has no code for later chunks, so it keeps the registers of the one-chunk path.
+template <int D, bool PACKED, int NT, bool CHUNKED>
 __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
     __shared__ int s_j, s_q, s_rej, s_own, s_k, s_sp;
     const short* sbasis = load_basis(smem, a.basis, a.basis_count);
     StencilSmem sm;
-    carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qcap, a.stride, sm);
+    carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qmax, a.stride, sm);
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int ns = a.n, N = a.N;  // ns: row stride of nbr and of a weight slot
@@ -816,21 +922,68 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
         if (__double_as_longlong(r2c) <= 0) r2c = 1.0;
         const double inv_r2 = rcp_fixed(r2c);
         bool ok = true;
-        if (made) {  // the Lebesgue values of the solve made ahead
+        // The columns pass through the right-hand-side block a.qcap at a time: the first chunk
+        // is carried through the factorization, later ones use the stored factors (LDL^T only;
+        // with LU a.qcap covers every ball).  A center whose solve was made ahead only reads
+        // its Lebesgue values.  A ball always holds its center, so q >= 1.
+        if (made) {
             for (int c = tid; c < q; c += NT) sm.lam[c] = __ldcg(&a.slot_lam[base + sm.cols[c]]);
         } else {
-            ok = solve_local<D, PACKED, NT>(a, sh, j, q, sm);
-            if (ok) lebesgue_values<NT>(n, sh.K, q, sm);
+            const int q1 = CHUNKED ? min(q, a.qcap) : q;
+            ok = solve_local<D, PACKED, NT>(a, sh, j, q1, sm);
+            if (ok) lebesgue_values<NT>(n, sh.K, q1, sm);
         }
         __syncthreads();
-        if (ahead) {  // publish every column, then the node's flag
-            if (ok) {
-                for (int e = tid; e < q * n; e += NT) {
+        const int qc = (CHUNKED && !made) ? min(q, a.qcap) : q;
+        // the solved columns c0 .. c0+qk-1 (held in sm.X as 0 .. qk-1) to the weight slots
+        auto emit = [&](int c0, int qk) {
+            if (ahead) {  // every column goes to the node's own slots
+                if (!ok) return;
+                for (int e = tid; e < qk * n; e += NT) {
                     const int c = e / n, r = e - c * n;
-                    a.slot_w[(base + sm.cols[c]) * ns + r] = sm.X[sm.rowof[r] * sm.xs + c] * inv_r2;
+                    a.slot_w[(base + sm.cols[c0 + c]) * ns + r] = sm.X[sm.rowof[r] * sm.xs + c] * inv_r2;
                 }
-                for (int c = tid; c < q; c += NT) a.slot_lam[base + sm.cols[c]] = sm.lam[c];
+                for (int c = tid; c < qk; c += NT) a.slot_lam[base + sm.cols[c0 + c]] = sm.lam[c0 + c];
+                return;
             }
+            // Lebesgue test (§4.2.1) per column
+            int failed = 0, own = 0;
+            for (int c = c0 + tid; c < c0 + qk; c += NT) {
+                const double lam = ok ? sm.lam[c] : nan;
+                const bool test_ok =
+                    ok && __double_as_longlong(lam) <= __double_as_longlong(sm.lam[0]);
+                bool keep;
+                if (!ok) keep = (c == 0);
+                else if (a.mode != RBFFD_STAB_SEQ) keep = true;
+                else keep = test_ok;
+                sm.keep[c] = keep ? 1 : 0;
+                a.slot_lam[base + sm.cols[c]] = lam;
+                a.slot_pass[base + sm.cols[c]] = (c == 0 || test_ok) ? 1 : 0;
+                failed += c > 0 && !test_ok;
+                own += keep && (a.mode != RBFFD_STAB_FALLBACK || c == 0 || test_ok);
+            }
+            if (failed) atomicAdd_block(&s_rej, failed);
+            if (own) atomicAdd_block(&s_own, own);
+            __syncthreads();
+            for (int e = tid; !made && e < qk * n; e += NT) {  // (made ahead: already in the slots)
+                const int c = e / n, r = e - c * n;
+                if (!sm.keep[c0 + c]) continue;
+                a.slot_w[(base + sm.cols[c0 + c]) * ns + r] =
+                    ok ? sm.X[sm.rowof[r] * sm.xs + c] * inv_r2 : nan;
+            }
+        };
+        emit(0, qc);
+        if constexpr (CHUNKED) {
+            for (int c0 = qc; c0 < q; c0 += qc) {  // later chunks (more columns than a.qcap)
+                const int qk = min(qc, q - c0);
+                __syncthreads();  // sm.X is read until here
+                // (the shape is read again rather than kept in registers)
+                if (ok) solve_chunk<D, NT>(shape_of<D>(a, sbasis, j), c0, qk, sm);
+                __syncthreads();
+                emit(c0, qk);
+            }
+        }
+        if (ahead) {  // publish every column, then the node's flag
             __syncthreads();
             if (tid == 0) {
                 fence_gpu();
@@ -838,31 +991,6 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
                 atomicAdd(&a.ctr->n_spec, 1ull);
             }
             continue;
-        }
-        // Lebesgue test (§4.2.1) per column
-        int failed = 0, own = 0;
-        for (int c = tid; c < q; c += NT) {
-            const double lam = ok ? sm.lam[c] : nan;
-            const bool test_ok =
-                ok && __double_as_longlong(lam) <= __double_as_longlong(sm.lam[0]);
-            bool keep;
-            if (!ok) keep = (c == 0);
-            else if (a.mode != RBFFD_STAB_SEQ) keep = true;
-            else keep = test_ok;
-            sm.keep[c] = keep ? 1 : 0;
-            a.slot_lam[base + sm.cols[c]] = lam;
-            a.slot_pass[base + sm.cols[c]] = (c == 0 || test_ok) ? 1 : 0;
-            failed += c > 0 && !test_ok;
-            own += keep && (a.mode != RBFFD_STAB_FALLBACK || c == 0 || test_ok);
-        }
-        if (failed) atomicAdd_block(&s_rej, failed);
-        if (own) atomicAdd_block(&s_own, own);
-        __syncthreads();
-        for (int e = tid; !made && e < q * n; e += NT) {  // (made ahead: already in the slots)
-            const int c = e / n, r = e - c * n;
-            if (!sm.keep[c]) continue;
-            a.slot_w[(base + sm.cols[c]) * ns + r] =
-                ok ? sm.X[sm.rowof[r] * sm.xs + c] * inv_r2 : nan;
         }
         // ownership: the earliest center keeping a row owns it
         for (int c = tid; c < q; c += NT) {
@@ -1169,18 +1297,30 @@ static cudaError_t occupancy(int* per_sm, const void* kern, int nt, size_t smem)
 
 // Resident CTAs per SM of the traversal kernel at team size nt (0 if nt has no instantiation
 // for this factorization).
-template <int D, bool PACKED>
-static int traversal_occupancy(int nt, size_t smem, int* per_sm) {
-    *per_sm = 0;
-    const void* k = nullptr;
-    switch (nt) {
-        case 32: if constexpr (PACKED) k = (const void*)k_traversal<D, PACKED, 32>; break;
-        case 64: if constexpr (PACKED) k = (const void*)k_traversal<D, PACKED, 64>; break;
-        case 96: if constexpr (PACKED) k = (const void*)k_traversal<D, PACKED, 96>; break;
-        case kNT: k = (const void*)k_traversal<D, PACKED, kNT>; break;
-        case kMaxNT: k = (const void*)k_traversal<D, PACKED, kMaxNT>; break;
-        default: break;
+// The traversal kernel for a team size, or nullptr (teams below 128 and chunked right-hand
+// sides exist for LDL^T only).
+template <int D, bool PACKED, bool CH>
+static const void* traversal_kernel(int nt) {
+    if constexpr (!PACKED && CH) {
+        return nullptr;
+    } else {
+        switch (nt) {
+            case 32: if constexpr (PACKED) return (const void*)k_traversal<D, PACKED, 32, CH>; break;
+            case 64: if constexpr (PACKED) return (const void*)k_traversal<D, PACKED, 64, CH>; break;
+            case 96: if constexpr (PACKED) return (const void*)k_traversal<D, PACKED, 96, CH>; break;
+            case kNT: return (const void*)k_traversal<D, PACKED, kNT, CH>;
+            case kMaxNT: return (const void*)k_traversal<D, PACKED, kMaxNT, CH>;
+            default: break;
+        }
+        return nullptr;
     }
+}
+
+template <int D, bool PACKED>
+static int traversal_occupancy(int nt, size_t smem, bool chunked, int* per_sm) {
+    *per_sm = 0;
+    const void* k = chunked ? traversal_kernel<D, PACKED, true>(nt)
+                            : traversal_kernel<D, PACKED, false>(nt);
     if (!k) return RBFFD_EINVAL;
     if (RB_CUDA(allow_max_smem(k)) ||
         RB_CUDA(occupancy(per_sm, k, nt, smem)) || *per_sm < 1)
@@ -1206,9 +1346,9 @@ static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
 // register-bound): more stencils in flight hide more of each one's serial pivot steps.  A
 // forced size (32, 64 and 96 exist for the LDL^T traversal only) is taken as given.
 template <int D, bool PACKED, bool TRAVERSAL>
-static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out) {
+static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool chunked = false) {
     auto occ = [&](int nt, int* ps) {
-        return TRAVERSAL ? traversal_occupancy<D, PACKED>(nt, smem, ps)
+        return TRAVERSAL ? traversal_occupancy<D, PACKED>(nt, smem, chunked, ps)
                          : fallback_occupancy<D, PACKED>(nt, smem, ps);
     };
     int nt = force, rc;
@@ -1232,17 +1372,19 @@ static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out) {
 // limit, choose team sizes and size the persistent grid from the occupancy.  fb[c] holds the
 // fallback launch of stencil class c.
 template <int D, bool PACKED>
-static int prepare(int n, int K, int qcap, int basis_count, LaunchPlan* lp) {
+static int prepare(int n, int K, int qcap, int qmax, int basis_count, LaunchPlan* lp) {
     int stride = 0;
     const size_t bb = basis_smem_bytes(basis_count);
-    const size_t smem = bb + solve_smem_per_cta(n, K, qcap, D, PACKED, &stride);
+    const size_t smem = bb + solve_smem_per_cta(n, K, qcap, qmax, D, PACKED, &stride);
     int per_sm = 0, rc;
-    if ((rc = pick_team<D, PACKED, true>(smem, lp->force_nt, &lp->nt, &per_sm))) return rc;
+    lp->chunked = PACKED && qcap < qmax;
+    if ((rc = pick_team<D, PACKED, true>(smem, lp->force_nt, &lp->nt, &per_sm, lp->chunked)))
+        return rc;
     lp->grid = per_sm * sm_count();
     lp->smem = smem;
     for (int c = 0; c < lp->n_fb; ++c) {
         FallbackClass& f = lp->fb[c];
-        const size_t fs = bb + solve_smem_per_cta(f.n, f.K, 1, D, PACKED, &f.xs);
+        const size_t fs = bb + solve_smem_per_cta(f.n, f.K, 1, 1, D, PACKED, &f.xs);
         if ((rc = pick_team<D, PACKED, false>(fs, 0, &f.nt, &per_sm))) return rc;
         f.grid = per_sm * sm_count();
         f.smem = fs;
@@ -1250,13 +1392,13 @@ static int prepare(int n, int K, int qcap, int basis_count, LaunchPlan* lp) {
     return RBFFD_OK;
 }
 
-int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count,
+int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int qmax, int basis_count,
                           LaunchPlan* lp) {
     if (D == 2)
-        return packed ? prepare<2, true>(n, K, qcap, basis_count, lp)
-                      : prepare<2, false>(n, K, qcap, basis_count, lp);
-    return packed ? prepare<3, true>(n, K, qcap, basis_count, lp)
-                  : prepare<3, false>(n, K, qcap, basis_count, lp);
+        return packed ? prepare<2, true>(n, K, qcap, qmax, basis_count, lp)
+                      : prepare<2, false>(n, K, qcap, qmax, basis_count, lp);
+    return packed ? prepare<3, true>(n, K, qcap, qmax, basis_count, lp)
+                  : prepare<3, false>(n, K, qcap, qmax, basis_count, lp);
 }
 
 template <int D, bool PACKED>
@@ -1279,26 +1421,17 @@ static int traversal(const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
     // that holds a claimed entry is solved), so progress needs no co-residency, and plans
     // on other streams can run beside this grid.
     if (ev0) cudaEventRecord(ev0, s);
-    const size_t per_cta = lp.smem - basis_bytes;
-    switch (lp.nt) {
-        case 32:
-            if constexpr (PACKED) k_traversal<D, PACKED, 32><<<grid, 32, lp.smem, s>>>(a, per_cta, basis_bytes);
-            break;
-        case 64:
-            if constexpr (PACKED) k_traversal<D, PACKED, 64><<<grid, 64, lp.smem, s>>>(a, per_cta, basis_bytes);
-            break;
-        case 96:
-            if constexpr (PACKED) k_traversal<D, PACKED, 96><<<grid, 96, lp.smem, s>>>(a, per_cta, basis_bytes);
-            break;
-        case kMaxNT:
-            k_traversal<D, PACKED, kMaxNT><<<grid, kMaxNT, lp.smem, s>>>(a, per_cta, basis_bytes);
-            break;
-        default:
-            k_traversal<D, PACKED, kNT><<<grid, kNT, lp.smem, s>>>(a, per_cta, basis_bytes);
-            break;
-    }
+    size_t per_cta = lp.smem - basis_bytes;
+    int bb = basis_bytes;
+    SolveArgs args = a;
+    const void* k = lp.chunked ? traversal_kernel<D, PACKED, true>(lp.nt)
+                               : traversal_kernel<D, PACKED, false>(lp.nt);
+    if (!k) return RBFFD_EINVAL;
+    void* params[] = {&args, &per_cta, &bb};
+    const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(lp.nt), params, lp.smem, s);
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
+    if (e != cudaSuccess) return RB_CUDA(e);
     return RB_LAUNCHED(__func__);
 }
 

@@ -139,7 +139,8 @@ struct SolveArgs {
     int* spec;                 // per node: 0 none, 1 speculative solve running, 2 made, 3 singular
     const double* nrm;         // unit normals [N][d] of Neumann nodes (or null)
     int N, n, M, K, m, ell;
-    int qcap;                  // columns room per stencil
+    int qcap;                  // right-hand-side columns carried per factorization
+    int qmax;                  // columns of the largest ball
     int stride;                // row stride of the full matrix (LU) or of the RHS block (LDL^T)
     int mode;                  // RBFFD_STAB_*
     double coef;               // m (m + D - 2)
@@ -162,7 +163,8 @@ struct SolveArgs {
     DevCounters* ctr;
 };
 
-size_t solve_smem_per_cta(int n, int K, int qcap, int D, int packed, int* stride_out);
+size_t solve_smem_per_cta(int n, int K, int qcap, int qmax, int D, int packed,
+                          int* stride_out);
 size_t basis_smem_bytes(int count);
 
 // Launch geometry decided once per plan.  Fallback re-solves run per stencil class (one
@@ -176,11 +178,12 @@ struct FallbackClass {
 struct LaunchPlan {
     int force_nt = 0;  // 0: choose; 128 or 512: forced team size of the traversal
     int nt = 128, grid = 0;
+    bool chunked = false;  // some balls have more columns than one factorization carries
     size_t smem = 0;
     int n_fb = 0;
     FallbackClass fb[kMaxEll + 1];
 };
-int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int basis_count,
+int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int qmax, int basis_count,
                           LaunchPlan* lp);
 int launch_traversal(int D, const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
                      cudaStream_t s, int* launches, cudaEvent_t ev0, cudaEvent_t ev1);

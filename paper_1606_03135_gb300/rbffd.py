@@ -23,7 +23,7 @@ FACTOR_LDLT, FACTOR_LU = 0, 1
 class rbffd_opts(C.Structure):
     _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
                 ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int),
-                ("max_ctas", C.c_int), ("team", C.c_int)]
+                ("max_ctas", C.c_int), ("team", C.c_int), ("rhs_chunk", C.c_int)]
 
 
 class rbffd_csr(C.Structure):
@@ -40,7 +40,8 @@ class rbffd_stats_t(C.Structure):
                 ("ms_traversal", C.c_float), ("ms_fallback", C.c_float),
                 ("ms_finalize", C.c_float), ("nnz", C.c_int64), ("plan_bytes", C.c_int64),
                 ("assemble_bytes", C.c_int64), ("n_boundary", C.c_int64),
-                ("n_speculated", C.c_int64), ("n_spec_used", C.c_int64)]
+                ("n_speculated", C.c_int64), ("n_spec_used", C.c_int64),
+                ("rhs_chunk", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -180,7 +181,8 @@ class Plan:
     the library inside ``rbffd_plan``)."""
 
     def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
-                 stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0, team=0):
+                 stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0, team=0,
+                 rhs_chunk=0):
         self._plan = None
         self._stream = stream
         if isinstance(nodes, np.ndarray):
@@ -196,7 +198,7 @@ class Plan:
         self.ell, self.m, self.delta, self.mode = ell, m, delta, mode
         self.sync = bool(sync)
         opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor,
-                          max_ctas, team)
+                          max_ctas, team, rhs_chunk)
         if np.ndim(n) == 0:  # one stencil size, degree and exponent for every node
             self.n = int(n)
             rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
@@ -315,8 +317,9 @@ class Plan:
 # ------------------------------------------------------------------ schedule autotuner
 def autotune(nodes, n, ell, m, delta, mode=STAB_SEQ, candidates=None, repeats=2):
     """Pick the traversal schedule for a workload -- warp-per-stencil (32 threads), 64-, 96-, 128-
-    or 512-thread tiles per stencil, and the persistent-grid cap -- by timing assemblies of each
-    candidate on the device (CUDA events, best of `repeats`, after a warm-up assembly).
+    or 512-thread tiles per stencil, the persistent-grid cap, and the right-hand sides carried
+    per factorization (8 or 16 where balls are larger) -- by timing assemblies of each candidate
+    on the device (CUDA events, best of `repeats`, after a warm-up assembly).
     Returns (best kwargs for Plan, {candidate: ms}).  Results do not depend on the schedule
     (the same stencils are solved the same way), only the time does."""
     import torch
@@ -324,6 +327,10 @@ def autotune(nodes, n, ell, m, delta, mode=STAB_SEQ, candidates=None, repeats=2)
     if candidates is None:
         candidates = [dict(team=t) for t in (32, 64, 96, 128, 512)]
         candidates += [dict(team=0, max_ctas=c) for c in (0, 4 * sms)]
+        if np.ndim(n) == 0:
+            with Plan(nodes, n, ell, m, delta, mode=mode) as p:
+                max_ball = p.stats()["max_ball"]
+            candidates += [dict(rhs_chunk=c) for c in (8, 16) if c < max_ball]
     timings = {}
     for cand in candidates:
         try:

@@ -380,12 +380,36 @@ def test_largest_stencil_size_matches_the_oracle():
     assert g["stats"]["K"] == 134
 
 
+def test_balls_too_large_for_one_chunk_match_the_oracle():
+    """n = 128, degree 5, r^5 at delta = 0.05: K = 149 and balls of up to ~126 columns, more
+    right-hand sides than fit in shared memory beside the system, so later columns are solved
+    in chunks with the stored factors."""
+    X = NS.jittered_grid(40, 2, seed=21)
+    g, _ = compare(X, 128, 5, 5, 0.05)
+    assert g["stats"]["K"] == 149 and g["stats"]["max_ball"] > 100
+
+
+@pytest.mark.parametrize("team", [0, 32, 512])
+@pytest.mark.parametrize("chunk", [1, 2, 5])
+def test_forced_chunks_are_bitwise_equal_to_one_chunk(team, chunk):
+    """Columns solved after the factorization get the same operations as the ones carried
+    through it, so any chunk size gives the same bits (2D and 3D, warp and CTA teams)."""
+    for X, n, ell, m in ((NS.disk2d(3000, seed=4), 31, 4, 7),
+                         (NS.ball3d(3000, seed=5), 45, 3, 7)):
+        a = gpu_run(X, n, ell, m, 0.3, team=team)
+        b = gpu_run(X, n, ell, m, 0.3, team=team, rhs_chunk=chunk)
+        for key in ("row_ptr", "col", "val", "owner", "is_center", "lam_row"):
+            assert np.array_equal(a[key], b[key]), (key, n)
+
+
+def test_forced_chunks_match_the_oracle():
+    compare(NS.disk2d(2000, seed=6), 21, 3, 5, 0.3, rhs_chunk=2)
+
+
 def test_systems_too_large_for_shared_memory_are_rejected():
-    """n = 128 with degree 7 (K = 164) fits at delta = 1 but not with balls of ~110 nodes
-    (right-hand sides beside the system): the plan says RBFFD_EINVAL."""
-    X = torch.from_numpy(NS.jittered_grid(40, 2, seed=21)).cuda()
-    with R.Plan(X, 128, 7, 7, 1.0) as p:
-        assert p.stats()["K"] == 164
+    """3D, n = 128 with degree 7: K = 248, whose packed triangle alone (247 KB) is above the
+    227 KB of shared memory a CTA can have; the plan says RBFFD_EINVAL."""
+    X = torch.from_numpy(NS.jittered_grid(12, 3, seed=21)).cuda()
     with pytest.raises(R.RbffdError) as e:
-        R.Plan(X, 128, 7, 7, 0.05)
+        R.Plan(X, 128, 7, 7, 1.0)
     assert e.value.code == R.EINVAL
