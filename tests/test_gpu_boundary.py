@@ -15,8 +15,8 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-9
 
 
-def run_bc(X, bc, nrm, n, ell, m, delta, mode=R.STAB_SEQ):
-    with R.Plan(torch.from_numpy(X).cuda(), n, ell, m, delta, mode=mode) as p:
+def run_bc(X, bc, nrm, n, ell, m, delta, mode=R.STAB_SEQ, **kw):
+    with R.Plan(torch.from_numpy(X).cuda(), n, ell, m, delta, mode=mode, **kw) as p:
         p.set_boundary(bc, nrm)
         p.assemble()
         row_ptr, col, val, owner = p.export()
@@ -26,8 +26,8 @@ def run_bc(X, bc, nrm, n, ell, m, delta, mode=R.STAB_SEQ):
                 stats=st)
 
 
-def compare_bc(X, bc, nrm, n, ell, m, delta, mode=R.STAB_SEQ):
-    g = run_bc(X, bc, nrm, n, ell, m, delta, mode)
+def compare_bc(X, bc, nrm, n, ell, m, delta, mode=R.STAB_SEQ, **kw):
+    g = run_bc(X, bc, nrm, n, ell, m, delta, mode, **kw)
     ref = O.assemble(X, n, ell, m, delta, mode, bc=bc, normals=nrm)
     assert ref["stats"]["n_near_tie"] == 0
     assert np.array_equal(g["owner"], ref["owner"])
@@ -61,6 +61,16 @@ def test_dirichlet_ball_matches_the_oracle():
 def test_boundary_with_fallback_mode():
     X, bc, nrm = NS.disk2d_bc(2000, seed=4)
     compare_bc(X, bc, nrm, 12, 2, 3, 0.3, mode=R.STAB_FALLBACK)
+
+
+@pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
+def test_boundary_with_right_hand_sides_in_chunks(mode):
+    """Chunks of 3 columns: the oracle's rows, and the same bits as one chunk."""
+    X, bc, nrm = NS.disk2d_bc(2000, seed=4)
+    g, _ = compare_bc(X, bc, nrm, 21, 3, 5, 0.3, mode=mode, rhs_chunk=3)
+    assert g["stats"]["rhs_chunk"] == 3
+    h = run_bc(X, bc, nrm, 21, 3, 5, 0.3, mode)
+    assert np.array_equal(g["val"], h["val"]) and np.array_equal(g["lam_row"], h["lam_row"])
 
 
 def test_timestep_matrix_and_clearing_the_boundary():

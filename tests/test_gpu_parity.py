@@ -308,8 +308,9 @@ def test_ball3d_N100000_sampled(delta):
 
 
 # ------------------------------------------------------------------ per-node stencils
-def gpu_run_mixed(X, n_node, ell_node, m_node, delta, mode=R.STAB_SEQ):
-    with R.Plan(torch.from_numpy(X).cuda(), n_node, ell_node, m_node, delta, mode=mode) as p:
+def gpu_run_mixed(X, n_node, ell_node, m_node, delta, mode=R.STAB_SEQ, **kw):
+    with R.Plan(torch.from_numpy(X).cuda(), n_node, ell_node, m_node, delta, mode=mode,
+                **kw) as p:
         p.assemble()
         row_ptr, col, val, owner = p.export()
         nbr, rho2, bl = p.export_stencils()
@@ -402,8 +403,33 @@ def test_forced_chunks_are_bitwise_equal_to_one_chunk(team, chunk):
             assert np.array_equal(a[key], b[key]), (key, n)
 
 
-def test_forced_chunks_match_the_oracle():
-    compare(NS.disk2d(2000, seed=6), 21, 3, 5, 0.3, rhs_chunk=2)
+@pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_OFF, R.STAB_FALLBACK])
+def test_forced_chunks_match_the_oracle(mode):
+    g, _ = compare(NS.disk2d(2000, seed=6), 21, 3, 5, 0.3, mode, rhs_chunk=2)
+    assert g["stats"]["rhs_chunk"] == 2 and g["stats"]["max_ball"] > 2
+
+
+def test_forced_chunks_on_per_node_stencils_are_bitwise_equal():
+    """Per-node degrees 2..5 (K up to 169) with chunks of 4 columns against one chunk."""
+    X = NS.cube3d_clustered(3000, seed=4)
+    params = NS.mixed_degree_params(X)
+    a = gpu_run_mixed(X, *params, 0.3)
+    b = gpu_run_mixed(X, *params, 0.3, rhs_chunk=4)
+    assert b["stats"]["rhs_chunk"] == 4 and a["stats"]["max_ball"] > 4
+    for key in ("row_ptr", "col", "val", "owner", "is_center", "lam_row"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_lu_keeps_every_column_and_refuses_balls_that_do_not_fit():
+    """LU stores K (K + q) entries and has no chunked solve: the large-ball case that LDL^T
+    solves in chunks is RBFFD_EINVAL with LU."""
+    X = torch.from_numpy(NS.jittered_grid(40, 2, seed=21)).cuda()
+    with pytest.raises(R.RbffdError) as e:
+        R.Plan(X, 128, 5, 5, 0.05, factor=R.FACTOR_LU)
+    assert e.value.code == R.EINVAL
+    with R.Plan(X, 12, 2, 3, 0.3, factor=R.FACTOR_LU) as p:
+        st = p.stats()
+        assert st["rhs_chunk"] == st["max_ball"]
 
 
 def test_systems_too_large_for_shared_memory_are_rejected():
