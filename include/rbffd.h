@@ -51,6 +51,14 @@ extern "C" {
 #define RBFFD_FACTOR_LDLT 0
 #define RBFFD_FACTOR_LU 1
 
+/* Reference point of the Lebesgue test (§4.2.1): the stencil's own center (default), or the
+ * stencil node nearest the stencil's centroid (the centroid is the sum of the n stencil nodes
+ * in kNN order divided by n; ties to the nearer kNN position).  With the centroid a retained
+ * node passes iff its value is <= the value at that node, which is solved as one more
+ * right-hand side when it is not a retained node; the center keeps its own row either way. */
+#define RBFFD_LREF_CENTER 0
+#define RBFFD_LREF_CENTROID 1
+
 typedef struct {
     int stab_mode;      /* RBFFD_STAB_* */
     int nodes_on_host;  /* 1: `nodes` is a host pointer, copied to the device by rbffd_plan */
@@ -75,6 +83,8 @@ typedef struct {
                            columns per CTA can keep more stencils resident per SM: a tuning
                            knob, see autotune).  Values < 0, or > 0 with RBFFD_FACTOR_LU, give
                            RBFFD_EINVAL */
+    int lebesgue_ref;   /* RBFFD_LREF_CENTER (default) or RBFFD_LREF_CENTROID; the centroid
+                           reference solves no center ahead of its turn */
 } rbffd_opts;
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */

@@ -21,6 +21,7 @@ LIB = os.path.join(HERE, "_build", "liboracle.so")
 OK, EINVAL, EDUPLICATE, ENOMEM, ESINGULAR = 0, -1, -2, -3, -4
 OP_LAPLACIAN, OP_IDENTITY, OP_NORMAL = 0, 1, 2
 STAB_SEQ, STAB_OFF, STAB_FALLBACK = 0, 1, 2
+LREF_CENTER, LREF_CENTROID = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -68,11 +69,11 @@ def lib():
             L.ora_local_weights_dn.argtypes = [P, C.c_int, P, C.c_int, C.c_int, C.c_int, C.c_int,
                                                P, P, C.c_int, P, P]
             L.ora_assemble_bc.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int,
-                                          C.c_double, C.c_int, P, P, P, P, P, P, P, P, P, P,
-                                          C.POINTER(Stats)]
+                                          C.c_double, C.c_int, C.c_int, P, P, P, P, P, P, P, P,
+                                          P, P, C.POINTER(Stats)]
             L.ora_assemble_mixed.argtypes = [P, C.c_int64, C.c_int, P, P, P, C.c_int,
-                                             C.c_double, C.c_int, P, P, P, P, P, P, P, P,
-                                             C.POINTER(Stats)]
+                                             C.c_double, C.c_int, C.c_int, P, P, P, P, P, P, P,
+                                             P, C.POINTER(Stats)]
             _lib = L
     return _lib
 
@@ -157,10 +158,13 @@ def normal_weights(X, idx, ell, m, nrm):
     return W, lam[0]
 
 
-def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None, bc=None, normals=None):
+def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None, bc=None, normals=None,
+             lref=LREF_CENTER):
     """The whole sequential construction of L.  Returns a dict with CSR arrays (row_ptr, col,
     val), owner, is_center, lam_row, stats and the kNN table used.  bc (uint8 [N]: 0
-    interior, 1 Dirichlet, 2 Neumann) and normals ([N][d]) add the boundary rows of §5."""
+    interior, 1 Dirichlet, 2 Neumann) and normals ([N][d]) add the boundary rows of §5.
+    lref picks the reference point of the Lebesgue test (§4.2.1): the stencil's center, or
+    with LREF_CENTROID the stencil node nearest the stencil's centroid."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     N, d = X.shape
     if nbr is None or d2 is None:
@@ -174,7 +178,7 @@ def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None, bc=None, nor
     st = Stats()
     bcv = None if bc is None else np.ascontiguousarray(bc, dtype=np.uint8)
     nrv = None if normals is None else np.ascontiguousarray(normals, dtype=np.float64)
-    _check(lib().ora_assemble_bc(_ptr(X), N, d, n, ell, m, float(delta), mode, _ptr(bcv),
+    _check(lib().ora_assemble_bc(_ptr(X), N, d, n, ell, m, float(delta), mode, lref, _ptr(bcv),
                                  _ptr(nrv), _ptr(np.ascontiguousarray(nbr, dtype=np.int32)),
                                  _ptr(np.ascontiguousarray(d2, dtype=np.float64)),
                                  _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(owner),
@@ -183,7 +187,8 @@ def assemble(X, n, ell, m, delta, mode=STAB_SEQ, nbr=None, d2=None, bc=None, nor
                 lam_row=lam_row, stats=st.as_dict(), nbr=nbr, d2=d2)
 
 
-def assemble_mixed(X, n_node, ell_node, m_node, delta, mode=STAB_SEQ, nbr=None, d2=None):
+def assemble_mixed(X, n_node, ell_node, m_node, delta, mode=STAB_SEQ, nbr=None, d2=None,
+                   lref=LREF_CENTER):
     """The traversal with per-node stencil size, degree and PHS exponent.  Returns the same
     dict as assemble(); CSR rows have the length of the stencil that produced them."""
     X = np.ascontiguousarray(X, dtype=np.float64)
@@ -202,7 +207,7 @@ def assemble_mixed(X, n_node, ell_node, m_node, delta, mode=STAB_SEQ, nbr=None, 
     lam_row = np.zeros(N, dtype=np.float64)
     st = Stats()
     _check(lib().ora_assemble_mixed(_ptr(X), N, d, _ptr(n_node), _ptr(ell_node), _ptr(m_node),
-                                    n_max, float(delta), mode,
+                                    n_max, float(delta), mode, lref,
                                     _ptr(np.ascontiguousarray(nbr, dtype=np.int32)),
                                     _ptr(np.ascontiguousarray(d2, dtype=np.float64)),
                                     _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(owner),

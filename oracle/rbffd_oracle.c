@@ -347,15 +347,62 @@ static void put_row(int64_t i, int n, const int32_t* stencil_idx, const double* 
     sort_row(col + i * n, val + i * n, n);
 }
 
+/* Position t in stencil I (n nodes) of the node nearest the stencil's centroid (§4.2.1, the
+ * reference point of the Lebesgue test in its centroid reading); ties go to the lower t.
+ * The centroid is (sum of the n nodes) * (1/n), each coordinate's sum taken in one fixed
+ * order: 32 partial sums s_l = x_l + x_(l+32) + ... (from 0.0, in that order), then five
+ * halving steps s_l <- s_l + s_(l xor o) for o = 16, 8, 4, 2, 1. */
+static int centroid_node(const double* X, int d, const int32_t* I, int n) {
+    double c[3] = {0.0, 0.0, 0.0};
+    const double inv_n = 1.0 / (double)n;
+    for (int a = 0; a < d; ++a) {
+        double s[32], u[32];
+        for (int l = 0; l < 32; ++l) {
+            s[l] = 0.0;
+            for (int t = l; t < n; t += 32) s[l] = s[l] + X[(int64_t)I[t] * d + a];
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+            for (int l = 0; l < 32; ++l) u[l] = s[l] + s[l ^ o];
+            memcpy(s, u, sizeof(s));
+        }
+        c[a] = s[0] * inv_n;
+    }
+    int best = 0;
+    double bd = sqdist(X + (int64_t)I[0] * d, c, d);
+    for (int t = 1; t < n; ++t) {
+        double s = sqdist(X + (int64_t)I[t] * d, c, d);
+        if (s < bd) { bd = s; best = t; }
+    }
+    return best;
+}
+
+/* Evaluation points of one center: the q retained members cols[0..q) (cols[0] = 0, the
+ * center) and, with the centroid reference, the reference node appended when it is not one
+ * of them.  Returns the number of points; *e_ref the point whose Lebesgue value the test
+ * uses. */
+static int eval_points(const double* X, int d, const int32_t* I, int n, int lref, int* cols,
+                       int q, int* e_ref) {
+    *e_ref = 0;
+    if (lref != ORA_LREF_CENTROID) return q;
+    const int t_ref = centroid_node(X, d, I, n);
+    for (int e = 0; e < q; ++e)
+        if (cols[e] == t_ref) { *e_ref = e; return q; }
+    cols[q] = t_ref;
+    *e_ref = q;
+    return q + 1;
+}
+
 /* The traversal visits nodes in index order.  A node already given a row is never
  * recomputed (§4.1).  An uncovered node k becomes a center: its retention set R_k is the
  * part of the ball of radius (1-delta) rho_k (closed; the ball is a prefix of the kNN list)
  * not yet covered, k first.  One factorization, one solve per member of R_k.  Then, per
  * mode:
- *   SEQ      (§4.2.1) keep member i iff Lambda(x_i) <= Lambda(x_k), Lambda = ||w||_1 of
+ *   SEQ      (§4.2.1) keep member i iff Lambda(x_i) <= Lambda(x_ref), Lambda = ||w||_1 of
  *            its column; rejected members stay uncovered and are reached later by the
  *            traversal (as a member of a later ball or as a center).  The reference point
- *            of the test is the stencil's own center x_k.
+ *            x_ref of the test is the stencil's own center x_k (ora_assemble), or the
+ *            stencil node nearest the stencil's centroid (ora_assemble_bc with
+ *            ORA_LREF_CENTROID); the center keeps its own row either way.
  *   OFF      keep every member.
  *   FALLBACK coverage as OFF; each member failing the test gets its row from its own
  *            delta = 1 stencil afterwards. */
@@ -363,8 +410,8 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
                  const int32_t* nbr, const double* d2, int64_t* row_ptr, int32_t* col,
                  double* val, int32_t* owner, uint8_t* is_center, double* lam_row,
                  ora_stats* st) {
-    return ora_assemble_bc(X, N, d, n, ell, m, delta, mode, NULL, NULL, nbr, d2, row_ptr, col,
-                           val, owner, is_center, lam_row, st);
+    return ora_assemble_bc(X, N, d, n, ell, m, delta, mode, ORA_LREF_CENTER, NULL, NULL, nbr, d2,
+                           row_ptr, col, val, owner, is_center, lam_row, st);
 }
 
 /* Boundary nodes (§5): bc[i] = 1 (Dirichlet) or 2 (Neumann), 0 for interior nodes.  The
@@ -375,11 +422,11 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
  * the derivative along its unit normal nrm[i] for Neumann.  Boundary rows have is_center
  * = 3 and are their own owners. */
 int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, double delta,
-                    int mode, const uint8_t* bc, const double* nrm, const int32_t* nbr,
+                    int mode, int lref, const uint8_t* bc, const double* nrm, const int32_t* nbr,
                     const double* d2, int64_t* row_ptr, int32_t* col, double* val,
                     int32_t* owner, uint8_t* is_center, double* lam_row, ora_stats* st) {
     if (N < 1 || n < 1 || n > N || (d != 2 && d != 3) || m < 3 || (m % 2) == 0 ||
-        !(delta > 0.0 && delta <= 1.0) || mode < 0 || mode > 2)
+        !(delta > 0.0 && delta <= 1.0) || mode < 0 || mode > 2 || lref < 0 || lref > 1)
         return ORA_EINVAL;
     int M = ora_poly_terms(d, ell, NULL);
     if (M > n) return ORA_EINVAL;
@@ -390,10 +437,10 @@ int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, do
     int32_t* ball = (int32_t*)malloc(sizeof(int32_t) * N);
     uint8_t* covered = (uint8_t*)calloc((size_t)N, 1);
     uint8_t* redo = (uint8_t*)calloc((size_t)N, 1);
-    double* Y = (double*)malloc(sizeof(double) * n * d);
-    double* W = (double*)malloc(sizeof(double) * n * n);
-    double* lam = (double*)malloc(sizeof(double) * n);
-    int* cols = (int*)malloc(sizeof(int) * n);
+    double* Y = (double*)malloc(sizeof(double) * (n + 1) * d);  /* members + reference */
+    double* W = (double*)malloc(sizeof(double) * n * (n + 1));
+    double* lam = (double*)malloc(sizeof(double) * (n + 1));
+    int* cols = (int*)malloc(sizeof(int) * (n + 1));
     int rc = ORA_OK;
     if (!ball || !covered || !redo || !Y || !W || !lam || !cols) { rc = ORA_ENOMEM; goto done; }
     rc = ora_ball_len(d2, N, n, delta, ball);
@@ -411,19 +458,21 @@ int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, do
         int q = 0;
         for (int t = 0; t < ball[k]; ++t) /* t = 0 is k itself, never covered here */
             if (!covered[I[t]] && !(bc && bc[I[t]])) cols[q++] = t;
-        for (int e = 0; e < q; ++e)
+        int e_ref;
+        const int qe = eval_points(X, d, I, n, lref, cols, q, &e_ref);
+        for (int e = 0; e < qe; ++e)
             for (int a = 0; a < d; ++a) Y[e * d + a] = X[(int64_t)I[cols[e]] * d + a];
-        rc = ora_local_weights(X, d, I, n, ell, m, ORA_OP_LAPLACIAN, Y, q, W, lam);
+        rc = ora_local_weights(X, d, I, n, ell, m, ORA_OP_LAPLACIAN, Y, qe, W, lam);
         if (rc != ORA_OK) goto done;
         is_center[k] = 1;
         s0.n_centers++;
-        s0.sum_cols += q;
+        s0.sum_cols += qe;
         for (int e = 0; e < q; ++e) {
             int64_t i = I[cols[e]];
             int pass = 1;
-            if (e > 0) {
-                double margin = (lam[0] - lam[e]) / lam[0];
-                pass = lam[e] <= lam[0];
+            if (e > 0 && e != e_ref) {  /* (the reference node passes its own test) */
+                double margin = (lam[e_ref] - lam[e]) / lam[e_ref];
+                pass = lam[e] <= lam[e_ref];
                 s0.n_decisions++;
                 if (!pass) s0.n_rejected++;
                 if (fabs(margin) < s0.min_abs_margin) s0.min_abs_margin = fabs(margin);
@@ -435,7 +484,7 @@ int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, do
             s0.sum_q++;
             if (lam_row) lam_row[i] = lam[e];
             if (mode == ORA_STAB_FALLBACK && !pass) { redo[i] = 1; continue; }
-            put_row(i, n, I, W + e, q, col, val);
+            put_row(i, n, I, W + e, qe, col, val);
         }
     }
     if (mode == ORA_STAB_FALLBACK) {
@@ -487,11 +536,11 @@ done:
  * stored by row_ptr (N+1), col/val hold up to N*n_max entries. */
 int ora_assemble_mixed(const double* X, int64_t N, int d, const int32_t* n_node,
                        const int32_t* ell_node, const int32_t* m_node, int n_max, double delta,
-                       int mode, const int32_t* nbr, const double* d2, int64_t* row_ptr,
-                       int32_t* col, double* val, int32_t* owner, uint8_t* is_center,
-                       double* lam_row, ora_stats* st) {
+                       int mode, int lref, const int32_t* nbr, const double* d2,
+                       int64_t* row_ptr, int32_t* col, double* val, int32_t* owner,
+                       uint8_t* is_center, double* lam_row, ora_stats* st) {
     if (N < 1 || n_max < 1 || n_max > N || (d != 2 && d != 3) || !(delta > 0.0 && delta <= 1.0) ||
-        mode < 0 || mode > 2)
+        mode < 0 || mode > 2 || lref < 0 || lref > 1)
         return ORA_EINVAL;
     for (int64_t k = 0; k < N; ++k) {
         if (n_node[k] < 1 || n_node[k] > n_max || m_node[k] < 3 || (m_node[k] % 2) == 0 ||
@@ -508,10 +557,10 @@ int ora_assemble_mixed(const double* X, int64_t N, int d, const int32_t* n_node,
     double* rval = (double*)malloc(sizeof(double) * N * n_max);
     uint8_t* covered = (uint8_t*)calloc((size_t)N, 1);
     uint8_t* redo = (uint8_t*)calloc((size_t)N, 1);
-    double* Y = (double*)malloc(sizeof(double) * n_max * d);
-    double* W = (double*)malloc(sizeof(double) * n_max * n_max);
-    double* lam = (double*)malloc(sizeof(double) * n_max);
-    int* cols = (int*)malloc(sizeof(int) * n_max);
+    double* Y = (double*)malloc(sizeof(double) * (n_max + 1) * d);  /* members + reference */
+    double* W = (double*)malloc(sizeof(double) * n_max * (n_max + 1));
+    double* lam = (double*)malloc(sizeof(double) * (n_max + 1));
+    int* cols = (int*)malloc(sizeof(int) * (n_max + 1));
     int rc = ORA_OK;
     if (!ball || !src || !rcol || !rval || !covered || !redo || !Y || !W || !lam || !cols) {
         rc = ORA_ENOMEM;
@@ -534,19 +583,22 @@ int ora_assemble_mixed(const double* X, int64_t N, int d, const int32_t* n_node,
         int q = 0;
         for (int t = 0; t < ball[k]; ++t)
             if (!covered[I[t]]) cols[q++] = t;
-        for (int e = 0; e < q; ++e)
+        int e_ref;
+        const int qe = eval_points(X, d, I, nk, lref, cols, q, &e_ref);
+        for (int e = 0; e < qe; ++e)
             for (int a = 0; a < d; ++a) Y[e * d + a] = X[(int64_t)I[cols[e]] * d + a];
-        rc = ora_local_weights(X, d, I, nk, ell_node[k], m_node[k], ORA_OP_LAPLACIAN, Y, q, W, lam);
+        rc = ora_local_weights(X, d, I, nk, ell_node[k], m_node[k], ORA_OP_LAPLACIAN, Y, qe, W,
+                               lam);
         if (rc != ORA_OK) goto done;
         is_center[k] = 1;
         s0.n_centers++;
-        s0.sum_cols += q;
+        s0.sum_cols += qe;
         for (int e = 0; e < q; ++e) {
             int64_t i = I[cols[e]];
             int pass = 1;
-            if (e > 0) {
-                double margin = (lam[0] - lam[e]) / lam[0];
-                pass = lam[e] <= lam[0];
+            if (e > 0 && e != e_ref) {  /* (the reference node passes its own test) */
+                double margin = (lam[e_ref] - lam[e]) / lam[e_ref];
+                pass = lam[e] <= lam[e_ref];
                 s0.n_decisions++;
                 if (!pass) s0.n_rejected++;
                 if (fabs(margin) < s0.min_abs_margin) s0.min_abs_margin = fabs(margin);
@@ -561,7 +613,7 @@ int ora_assemble_mixed(const double* X, int64_t N, int d, const int32_t* n_node,
             src[i] = (int32_t)k;
             for (int j = 0; j < nk; ++j) {
                 rcol[i * n_max + j] = I[j];
-                rval[i * n_max + j] = W[(int64_t)j * q + e];
+                rval[i * n_max + j] = W[(int64_t)j * qe + e];
             }
         }
     }

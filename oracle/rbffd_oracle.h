@@ -21,16 +21,19 @@ extern "C" {
 enum { ORA_OK = 0, ORA_EINVAL = -1, ORA_EDUPLICATE = -2, ORA_ENOMEM = -3, ORA_ESINGULAR = -4 };
 enum { ORA_OP_LAPLACIAN = 0, ORA_OP_IDENTITY = 1, ORA_OP_NORMAL = 2 };
 enum { ORA_STAB_SEQ = 0, ORA_STAB_OFF = 1, ORA_STAB_FALLBACK = 2 };
+/* Reference point of the Lebesgue test (§4.2.1): the stencil's own center, or the stencil
+ * node nearest the centroid of the stencil. */
+enum { ORA_LREF_CENTER = 0, ORA_LREF_CENTROID = 1 };
 
 typedef struct {
     int64_t n_centers;      /* N_delta: stencils whose weights were kept (fallback stencils excluded) */
     int64_t n_fallback;     /* rows recomputed by their own delta=1 stencil (FALLBACK mode) */
     int64_t n_decisions;    /* Lebesgue tests made for non-center retained nodes */
-    int64_t n_rejected;     /* of which failed  Lambda_i <= Lambda_center */
+    int64_t n_rejected;     /* of which failed  Lambda_i <= Lambda_ref */
     int64_t n_near_tie;     /* of which |margin| <= 1e-9 */
     int64_t sum_q;          /* rows written by centers (== N in SEQ/OFF) */
-    int64_t sum_cols;       /* right-hand sides solved in total */
-    double min_abs_margin;  /* min over decisions of |(L_c - L_i) / L_c| (inf if none) */
+    int64_t sum_cols;       /* right-hand sides solved in total (reference points included) */
+    double min_abs_margin;  /* min over decisions of |(L_ref - L_i) / L_ref| (inf if none) */
     int64_t n_boundary;     /* boundary rows (ora_assemble_bc) */
 } ora_stats;
 
@@ -81,9 +84,12 @@ int ora_assemble(const double* X, int64_t N, int d, int n, int ell, int m, doubl
  * outward normal nrm[i*d..], may be NULL without Neumann nodes).  The overlapped traversal
  * covers the interior only; every boundary node gets its own-stencil row: the identity
  * (Dirichlet) or the normal derivative (Neumann); is_center = 3 for those rows.  bc may be
- * NULL (no boundary: ora_assemble). */
+ * NULL (no boundary: ora_assemble).  lref (ORA_LREF_*) picks the reference point of the
+ * Lebesgue test: with ORA_LREF_CENTROID a retained member passes iff its value is <= the
+ * value at the stencil node nearest the stencil's centroid (solved as one more point when it
+ * is not a retained member); the center itself keeps its row either way. */
 int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, double delta,
-                    int mode, const uint8_t* bc, const double* nrm, const int32_t* nbr,
+                    int mode, int lref, const uint8_t* bc, const double* nrm, const int32_t* nbr,
                     const double* d2, int64_t* row_ptr, int32_t* col, double* val,
                     int32_t* owner, uint8_t* is_center, double* lam_row, ora_stats* stats);
 
@@ -92,7 +98,7 @@ int ora_assemble_bc(const double* X, int64_t N, int d, int n, int ell, int m, do
  * that produced them: row_ptr[N+1], col/val with room for N*n_max entries. */
 int ora_assemble_mixed(const double* X, int64_t N, int d, const int32_t* n_node,
                        const int32_t* ell_node, const int32_t* m_node, int n_max, double delta,
-                       int mode, const int32_t* nbr, const double* d2, int64_t* row_ptr,
+                       int mode, int lref, const int32_t* nbr, const double* d2, int64_t* row_ptr,
                        int32_t* col, double* val, int32_t* owner, uint8_t* is_center,
                        double* lam_row, ora_stats* stats);
 

@@ -36,6 +36,7 @@ struct rbffd_plan_s {
     int Mof[kMaxEll + 1] = {};
     bool mixed = false;      // per-node n, ell, m (rbffd_plan_mixed)
     int* node_n = nullptr;
+    unsigned char* ref_pos = nullptr;  // centroid reference of the Lebesgue test (or none)
     signed char* node_ell = nullptr;
     signed char* node_m = nullptr;
     // boundary nodes (rbffd_set_boundary)
@@ -342,14 +343,15 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
             K_max = nk + Mk > K_max ? nk + Mk : K_max;
         }
     }
-    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0, 0};
+    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0, 0, RBFFD_LREF_CENTER};
     if (opts) o = *opts;
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
         (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0 ||
         (o.team != 0 && o.team != 32 && o.team != 64 && o.team != 96 && o.team != 128 &&
          o.team != 512) ||
         (o.factor == RBFFD_FACTOR_LU && o.team != 0 && o.team != 128 && o.team != 512) ||
-        o.rhs_chunk < 0 || (o.factor == RBFFD_FACTOR_LU && o.rhs_chunk > 0))
+        o.rhs_chunk < 0 || (o.factor == RBFFD_FACTOR_LU && o.rhs_chunk > 0) ||
+        (o.lebesgue_ref != RBFFD_LREF_CENTER && o.lebesgue_ref != RBFFD_LREF_CENTROID))
         return RBFFD_EINVAL;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
 
@@ -387,7 +389,9 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
                      oP = c.add<short>(basis_count), oC = c.add<DevCounters>(1),
                      oNn = c.add<int>(mixed ? (size_t)N : 0),
                      oNl = c.add<signed char>(mixed ? (size_t)N : 0),
-                     oNm = c.add<signed char>(mixed ? (size_t)N : 0);
+                     oNm = c.add<signed char>(mixed ? (size_t)N : 0),
+                     oRp = c.add<unsigned char>(
+                         o.lebesgue_ref == RBFFD_LREF_CENTROID ? (size_t)N : 0);
         if ((rc = pool_alloc(&p->plan_block, c.bytes, p->device, s))) goto fail;
         p->plan_bytes = c.bytes;
         p->X = at<double>(p->plan_block, oX);
@@ -398,6 +402,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         p->slot_off = at<long long>(p->plan_block, oS);
         p->basis = at<short>(p->plan_block, oP);
         p->ctr = at<DevCounters>(p->plan_block, oC);
+        if (o.lebesgue_ref == RBFFD_LREF_CENTROID) p->ref_pos = at<unsigned char>(p->plan_block, oRp);
         if (mixed) {
             p->node_n = at<int>(p->plan_block, oNn);
             p->node_ell = at<signed char>(p->plan_block, oNl);
@@ -432,6 +437,10 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
     if (rc) goto fail;
     rc = launch_scan_i32_to_i64(p->ball_len, p->slot_off, Ni, s, &p->launches);
     if (rc) goto fail;
+    if (p->ref_pos) {
+        rc = launch_centroid_ref(d, p->X, p->nbr, p->node_n, Ni, n, p->ref_pos, s, &p->launches);
+        if (rc) goto fail;
+    }
     cudaEventRecord(p->ev[1], s);
     cudaFreeAsync(scratch, s);
     scratch = nullptr;
@@ -460,7 +469,8 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
     // right-hand-side columns carried through one factorization: every column of the largest
     // ball (LU always), or with LDL^T fewer, opts.rhs_chunk or as many as shared memory holds
     // (the rest are solved in chunks of that many)
-    qmax = p->max_ball < 1 ? 1 : (int)p->max_ball;
+    // columns of the largest ball, plus the Lebesgue reference node when it is not a member
+    qmax = (p->max_ball < 1 ? 1 : (int)p->max_ball) + (o.lebesgue_ref == RBFFD_LREF_CENTROID);
     p->qcap = qmax;
     if (o.rhs_chunk > 0 && o.rhs_chunk < p->qcap) p->qcap = o.rhs_chunk;
     {
@@ -563,11 +573,12 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.node_n = p->node_n; a.node_ell = p->node_ell; a.node_m = p->node_m;
     a.bc = p->n_boundary > 0 ? p->bc : nullptr;
     // speculation only pays where centers wait on each other (retention balls beyond the center)
-    a.spec = p->max_ball > 1 ? p->spec : nullptr;
+    a.spec = (p->max_ball > 1 && p->opts.lebesgue_ref == RBFFD_LREF_CENTER) ? p->spec : nullptr;
     a.nrm = p->nrm;
     a.N = (int)p->N; a.n = p->n; a.M = p->M; a.K = p->K; a.m = p->m; a.ell = p->ell;
     a.qcap = p->qcap; a.stride = p->stride; a.mode = p->opts.stab_mode;
-    a.qmax = p->max_ball < 1 ? 1 : (int)p->max_ball;
+    a.qmax = (p->max_ball < 1 ? 1 : (int)p->max_ball) + (p->ref_pos ? 1 : 0);
+    a.ref_pos = p->ref_pos;
     a.coef = (double)(p->m * (p->m + p->d - 2));
     a.timeout_ns = (unsigned long long)p->opts.timeout_ms * 1000000ull;
     a.state = p->state; a.pending = p->pending; a.owner = p->owner; a.queue = p->queue;

@@ -828,6 +828,45 @@ __device__ int pick_spec(const SolveArgs& a) {
     return atomicCAS(&a.spec[k], 0, 1) == 0 ? k : -1;
 }
 
+// Reference point of the Lebesgue test in its centroid reading (§4.2.1): for every node j,
+// the position in its stencil (n_j nodes) of the node nearest the stencil's centroid; one warp
+// per node.  The centroid is (sum of the nodes) * (1/n_j) with each coordinate's sum in one
+// fixed order (lane l adds nodes l, l + 32, ... from 0.0, then a xor butterfly; IEEE addition
+// commutes, so every lane holds the same sum); ties go to the lower position.  It depends on
+// the stencil only, so it runs once per plan, before the traversal.
+template <int D>
+__global__ void k_centroid_ref(const double* X, const int* nbr, const int* node_n, int N, int ns,
+                               unsigned char* ref_pos) {
+    const int lane = threadIdx.x & 31;
+    const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (j >= N) return;  // (warp-uniform)
+    const int n = node_n ? node_n[j] : ns;
+    const int* nb = nbr + (size_t)j * ns;
+    const double inv_n = __ddiv_rn(1.0, exact_double(n));
+    double c[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        double s = 0.0;
+        for (int t = lane; t < n; t += 32) s = __dadd_rn(s, __ldg(&X[(size_t)nb[t] * D + d]));
+        for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+        c[d] = __dmul_rn(s, inv_n);
+    }
+    unsigned long long best = ~0ull;  // this lane's smallest squared distance (bits; r2 >= 0)
+    int tb = 0x7fffffff;              // and its lowest position
+    for (int t = lane; t < n; t += 32) {
+        const unsigned long long k =
+            (unsigned long long)__double_as_longlong(sqdist_rn<D>(X + (size_t)nb[t] * D, c));
+        if (k < best) { best = k; tb = t; }
+    }
+    unsigned long long m = best;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v < m ? v : m;
+    }
+    const unsigned t = __reduce_min_sync(0xffffffffu, best == m ? (unsigned)tb : 0x7fffffffu);
+    if (lane == 0) ref_pos[j] = (unsigned char)t;
+}
+
 // One CTA per center.  Thread 0 claims the next queue slot and waits (bounded) for it to be
 // filled; the CTA then solves the center, tests and writes its columns, and resolves the
 // traversal state of its ball members.
@@ -838,7 +877,7 @@ __device__ int pick_spec(const SolveArgs& a) {
 template <int D, bool PACKED, int NT, bool CHUNKED>
 __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs a, size_t per_cta, int basis_bytes) {
     extern __shared__ __align__(16) char smem[];
-    __shared__ int s_j, s_q, s_rej, s_own, s_k, s_sp;
+    __shared__ int s_j, s_q, s_rej, s_own, s_k, s_sp, s_ref, s_refonly;
     const short* sbasis = load_basis(smem, a.basis, a.basis_count);
     StencilSmem sm;
     carve<D, PACKED>(smem + basis_bytes, a.n, a.K, a.qmax, a.stride, sm);
@@ -893,7 +932,10 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
         const Shape sh = shape_of<D>(a, sbasis, j);
         const int n = sh.n;
 
-        // columns: the center and every later ball member not already kept by an earlier center
+        // columns: the center and every later ball member not already kept by an earlier center.
+        // With the centroid reference of the Lebesgue test, the reference node's column goes to
+        // position 1 (after the center), and is solved as one more column when it is not such
+        // a member (reference only: never kept).
         const int L = a.ball_len[j];
         if (wid == 0) {
             int q = 0;
@@ -913,7 +955,24 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
                 if (t < n) sm.colof[t] = inc ? pos : -1;
                 q += __popc(bal);
             }
-            if (lane == 0) s_q = q;
+            __syncwarp();
+            if (lane == 0) {
+                int ref = 0, only = 0;
+                if (a.ref_pos) {
+                    const int tref = a.ref_pos[j];
+                    if (tref > 0) {  // the reference column to position 1
+                        int p = sm.colof[tref];
+                        if (p < 0) { p = q++; sm.cols[p] = tref; only = 1; }
+                        const int t1 = sm.cols[1];
+                        sm.cols[1] = tref; sm.colof[tref] = 1;
+                        sm.cols[p] = t1; sm.colof[t1] = p;
+                        ref = 1;
+                    }
+                }
+                s_q = q;
+                s_ref = ref;
+                s_refonly = only;
+            }
         }
         __syncthreads();
         const int q = s_q;
@@ -937,21 +996,26 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
         const int qc = (CHUNKED && !made) ? min(q, a.qcap) : q;
         // the solved columns c0 .. c0+qk-1 (held in sm.X as 0 .. qk-1) to the weight slots
         auto emit = [&](int c0, int qk) {
+            const int cref = s_ref;                       // the test's reference column
+            const int conly = s_refonly ? cref : -1;      // a reference-only column
             if (ahead) {  // every column goes to the node's own slots
                 if (!ok) return;
                 for (int e = tid; e < qk * n; e += NT) {
                     const int c = e / n, r = e - c * n;
+                    if (c0 + c == conly) continue;
                     a.slot_w[(base + sm.cols[c0 + c]) * ns + r] = sm.X[sm.rowof[r] * sm.xs + c] * inv_r2;
                 }
-                for (int c = tid; c < qk; c += NT) a.slot_lam[base + sm.cols[c0 + c]] = sm.lam[c0 + c];
+                for (int c = tid; c < qk; c += NT)
+                    if (c0 + c != conly) a.slot_lam[base + sm.cols[c0 + c]] = sm.lam[c0 + c];
                 return;
             }
-            // Lebesgue test (§4.2.1) per column
+            // Lebesgue test (§4.2.1) per column; the center keeps its own row
             int failed = 0, own = 0;
             for (int c = c0 + tid; c < c0 + qk; c += NT) {
+                if (c == conly) { sm.keep[c] = 0; continue; }
                 const double lam = ok ? sm.lam[c] : nan;
                 const bool test_ok =
-                    ok && __double_as_longlong(lam) <= __double_as_longlong(sm.lam[0]);
+                    ok && (c == 0 || __double_as_longlong(lam) <= __double_as_longlong(sm.lam[cref]));
                 bool keep;
                 if (!ok) keep = (c == 0);
                 else if (a.mode != RBFFD_STAB_SEQ) keep = true;
@@ -1433,6 +1497,15 @@ static int traversal(const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
     if (ev1) cudaEventRecord(ev1, s);
     ++*launches;
     if (e != cudaSuccess) return RB_CUDA(e);
+    return RB_LAUNCHED(__func__);
+}
+
+int launch_centroid_ref(int D, const double* X, const int* nbr, const int* node_n, int N, int ns,
+                        unsigned char* ref_pos, cudaStream_t s, int* launches) {
+    const int tb = 256, nb = (int)(((size_t)N * 32 + tb - 1) / tb);
+    if (D == 2) k_centroid_ref<2><<<nb, tb, 0, s>>>(X, nbr, node_n, N, ns, ref_pos);
+    else k_centroid_ref<3><<<nb, tb, 0, s>>>(X, nbr, node_n, N, ns, ref_pos);
+    ++*launches;
     return RB_LAUNCHED(__func__);
 }
 

@@ -143,6 +143,8 @@ struct SolveArgs {
     int qmax;                  // columns of the largest ball
     int stride;                // row stride of the full matrix (LU) or of the RHS block (LDL^T)
     int mode;                  // RBFFD_STAB_*
+    const unsigned char* ref_pos;  // centroid reference of the Lebesgue test: its stencil
+                                   // position per node (nullptr: the stencil's center)
     double coef;               // m (m + D - 2)
     int no_seed;               // fault injection: push no initial center (waits run out)
     int factor;                // RBFFD_FACTOR_LDLT (packed layout) or RBFFD_FACTOR_LU (full)
@@ -185,6 +187,8 @@ struct LaunchPlan {
 };
 int prepare_solve_kernels(int D, int packed, int n, int K, int qcap, int qmax, int basis_count,
                           LaunchPlan* lp);
+int launch_centroid_ref(int D, const double* X, const int* nbr, const int* node_n, int N, int ns,
+                        unsigned char* ref_pos, cudaStream_t s, int* launches);
 int launch_traversal(int D, const SolveArgs& a, const LaunchPlan& lp, const int* indeg,
                      cudaStream_t s, int* launches, cudaEvent_t ev0, cudaEvent_t ev1);
 int launch_fallback(int D, const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s,

@@ -18,12 +18,14 @@ from . import build as _build
 OK, EINVAL, EDUPLICATE, ENOMEM, ESINGULAR, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 STAB_SEQ, STAB_OFF, STAB_FALLBACK = 0, 1, 2
 FACTOR_LDLT, FACTOR_LU = 0, 1
+LREF_CENTER, LREF_CENTROID = 0, 1  # reference point of the Lebesgue test (rbffd_opts.lebesgue_ref)
 
 
 class rbffd_opts(C.Structure):
     _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
                 ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int),
-                ("max_ctas", C.c_int), ("team", C.c_int), ("rhs_chunk", C.c_int)]
+                ("max_ctas", C.c_int), ("team", C.c_int), ("rhs_chunk", C.c_int),
+                ("lebesgue_ref", C.c_int)]
 
 
 class rbffd_csr(C.Structure):
@@ -182,7 +184,7 @@ class Plan:
 
     def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
                  stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0, team=0,
-                 rhs_chunk=0):
+                 rhs_chunk=0, lebesgue_ref=0):
         self._plan = None
         self._stream = stream
         if isinstance(nodes, np.ndarray):
@@ -198,7 +200,7 @@ class Plan:
         self.ell, self.m, self.delta, self.mode = ell, m, delta, mode
         self.sync = bool(sync)
         opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor,
-                          max_ctas, team, rhs_chunk)
+                          max_ctas, team, rhs_chunk, lebesgue_ref)
         if np.ndim(n) == 0:  # one stencil size, degree and exponent for every node
             self.n = int(n)
             rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,

@@ -54,6 +54,8 @@ def test_strerror_and_argument_checks_need_no_gpu():
     assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, neg_chunk)[0] == R.EINVAL
     lu_chunk = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LU, 0, 0, 4)
     assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, lu_chunk)[0] == R.EINVAL
+    bad_ref = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LDLT, 0, 0, 0, 2)
+    assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, bad_ref)[0] == R.EINVAL
 
 
 def test_struct_layouts_match_the_header(tmp_path):

@@ -28,7 +28,8 @@ def run_bc(X, bc, nrm, n, ell, m, delta, mode=R.STAB_SEQ, **kw):
 
 def compare_bc(X, bc, nrm, n, ell, m, delta, mode=R.STAB_SEQ, **kw):
     g = run_bc(X, bc, nrm, n, ell, m, delta, mode, **kw)
-    ref = O.assemble(X, n, ell, m, delta, mode, bc=bc, normals=nrm)
+    ref = O.assemble(X, n, ell, m, delta, mode, bc=bc, normals=nrm,
+                     lref=kw.get("lebesgue_ref", O.LREF_CENTER))
     assert ref["stats"]["n_near_tie"] == 0
     assert np.array_equal(g["owner"], ref["owner"])
     assert np.array_equal(g["is_center"], ref["is_center"])
@@ -107,3 +108,10 @@ def test_boundary_argument_errors():
             p.set_boundary(bc, None)  # Neumann nodes need normals
         with pytest.raises(R.RbffdError):
             p.timestep_matrix(0.1, out=torch.empty(10, dtype=torch.float64, device="cuda"))
+
+
+def test_boundary_with_the_centroid_reference():
+    """Stencils next to the boundary have their centroids shifted inwards: the reference node
+    is often not the center, and may be a boundary node (solved as a reference only)."""
+    X, bc, nrm = NS.disk2d_bc(2000, seed=4)
+    compare_bc(X, bc, nrm, 21, 3, 5, 0.3, lebesgue_ref=R.LREF_CENTROID)

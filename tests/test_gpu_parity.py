@@ -320,18 +320,8 @@ def gpu_run_mixed(X, n_node, ell_node, m_node, delta, mode=R.STAB_SEQ, **kw):
                 ball_len=bl, lam_row=lam, is_center=isc, stats=st)
 
 
-@pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
-def test_mixed_degrees_3d_match_the_mixed_oracle(mode):
-    X = NS.cube3d_clustered(3000, seed=4)
-    n_node, ell_node, m_node = NS.mixed_degree_params(X)
-    g = gpu_run_mixed(X, n_node, ell_node, m_node, 0.3, mode)
-    ref = O.assemble_mixed(X, n_node, ell_node, m_node, 0.3, mode)
-    assert ref["stats"]["n_near_tie"] == 0
-    assert np.array_equal(g["nbr"], ref["nbr"])
-    assert np.array_equal(g["owner"], ref["owner"])
-    assert np.array_equal(g["is_center"], ref["is_center"])
-    assert np.array_equal(g["row_ptr"], ref["row_ptr"])
-    assert np.array_equal(g["col"], ref["col"])
+def check_mixed_rows(X, g, ref, n_node, ell_node, m_node):
+    """Weights of the mixed-degree workload against the mixed oracle."""
     # Degree-5 stencils here (K = 169 on clustered nodes) have condition numbers near 5e10:
     # two correct FP64 solvers (the oracle's LU, LAPACK) already differ by up to ~2e-7 on
     # them, and the symmetric Bunch-Kaufman factorization the GPU uses is a few times less
@@ -358,6 +348,21 @@ def test_mixed_degrees_3d_match_the_mixed_oracle(mode):
         e_gpu = np.abs(g["val"][sl] - w[order]).max() / scale
         e_ora = np.abs(ref["val"][sl] - w[order]).max() / scale
         assert e_gpu <= max(TOL, 10 * e_ora), (i, e_gpu, e_ora)
+
+
+@pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
+def test_mixed_degrees_3d_match_the_mixed_oracle(mode):
+    X = NS.cube3d_clustered(3000, seed=4)
+    n_node, ell_node, m_node = NS.mixed_degree_params(X)
+    g = gpu_run_mixed(X, n_node, ell_node, m_node, 0.3, mode)
+    ref = O.assemble_mixed(X, n_node, ell_node, m_node, 0.3, mode)
+    assert ref["stats"]["n_near_tie"] == 0
+    assert np.array_equal(g["nbr"], ref["nbr"])
+    assert np.array_equal(g["owner"], ref["owner"])
+    assert np.array_equal(g["is_center"], ref["is_center"])
+    assert np.array_equal(g["row_ptr"], ref["row_ptr"])
+    assert np.array_equal(g["col"], ref["col"])
+    check_mixed_rows(X, g, ref, n_node, ell_node, m_node)
     lam_err = np.abs(g["lam_row"] - ref["lam_row"]) / ref["lam_row"]
     assert np.quantile(lam_err, 0.8) <= TOL and lam_err.max() <= 1e-5
     assert g["stats"]["n_fallback"] == ref["stats"]["n_fallback"]
@@ -439,3 +444,40 @@ def test_systems_too_large_for_shared_memory_are_rejected():
     with pytest.raises(R.RbffdError) as e:
         R.Plan(X, 128, 7, 7, 1.0)
     assert e.value.code == R.EINVAL
+
+
+# ------------------------------------------------------------------ centroid reference (§4.2.1)
+@pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_OFF, R.STAB_FALLBACK])
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_centroid_reference_matches_the_oracle(mode, case):
+    """The Lebesgue test against the stencil node nearest the stencil's centroid: reference
+    positions from the per-plan pre-pass, the reference solved as one more column when it is
+    not a retained node, the center always kept."""
+    if case == "2d":
+        X, n, ell, m = NS.disk2d(2000, seed=6), 21, 3, 5
+    else:
+        X, n, ell, m = NS.ball3d(3000, seed=5), 45, 3, 7
+    ref = O.assemble(X, n, ell, m, 0.3, mode, lref=O.LREF_CENTROID)
+    compare(X, n, ell, m, 0.3, mode, ref=ref, lebesgue_ref=R.LREF_CENTROID)
+    # (solved-column counts may differ: the dataflow can solve a member that a center before
+    # it, finishing later, keeps; the oracle solves each center's columns in index order)
+
+
+@pytest.mark.parametrize("team,chunk", [(0, 1), (0, 2), (32, 0), (512, 3)])
+def test_centroid_reference_in_chunks_and_teams_is_bitwise_equal(team, chunk):
+    X = NS.disk2d(3000, seed=4)
+    a = gpu_run(X, 31, 4, 7, 0.3, lebesgue_ref=R.LREF_CENTROID)
+    b = gpu_run(X, 31, 4, 7, 0.3, lebesgue_ref=R.LREF_CENTROID, team=team, rhs_chunk=chunk)
+    for key in ("row_ptr", "col", "val", "owner", "is_center", "lam_row"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_centroid_reference_on_per_node_stencils_matches_the_mixed_oracle():
+    X = NS.cube3d_clustered(3000, seed=4)
+    params = NS.mixed_degree_params(X)
+    g = gpu_run_mixed(X, *params, 0.3, lebesgue_ref=R.LREF_CENTROID)
+    ref = O.assemble_mixed(X, *params, 0.3, lref=O.LREF_CENTROID)
+    assert ref["stats"]["n_near_tie"] == 0
+    for key in ("owner", "is_center", "row_ptr", "col"):
+        assert np.array_equal(g[key], ref[key]), key
+    check_mixed_rows(X, g, ref, *params)

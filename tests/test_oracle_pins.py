@@ -230,11 +230,17 @@ def test_traversal_satisfies_its_unique_characterisation(mode, delta):
     X = NS.disk2d(300, seed=21)
     n, ell, m = 12, 2, 3
     r = O.assemble(X, n, ell, m, delta, mode=mode)
-    nbr, d2 = r["nbr"], r["d2"]
-    bl = O.ball_len(d2, delta)
+    bl = O.ball_len(r["d2"], delta)
+    acc = {j: _acc(X, r["nbr"], bl, j, ell, m) for j in np.flatnonzero(r["is_center"] == 1)}
+    _check_characterisation(X, r, bl, acc, mode, ell, m)
+
+
+def _check_characterisation(X, r, bl, acc, mode, ell, m):
+    """The index-order traversal's unique assignment, given each center's acceptance flags
+    acc[j] = (W, lam, ok) over its ball (computed by the caller)."""
+    nbr = r["nbr"]
     N = X.shape[0]
     centers = np.flatnonzero(r["is_center"] == 1)
-    acc = {j: _acc(X, nbr, bl, j, ell, m) for j in centers}
     keep = lambda j, t: bool(acc[j][2][t]) if mode == O.STAB_SEQ else True
     first = np.full(N, -1)
     for j in centers:  # ascending
@@ -265,6 +271,57 @@ def test_traversal_satisfies_its_unique_characterisation(mode, delta):
         assert np.array_equal(r["col"][sl], src_cols[o])
         assert np.array_equal(r["val"][sl], src_w[o])
     assert r["stats"]["n_fallback"] == n_fb
+
+
+def _centroid_ref(X, idx):
+    """Stencil position of the node nearest the centroid of the stencil (numpy mean), and the
+    relative gap to the second nearest, so that a test can rule out a near tie."""
+    P = X[idx]
+    dd = ((P - P.mean(axis=0)) ** 2).sum(axis=1)
+    o = np.argsort(dd, kind="stable")
+    return int(o[0]), (dd[o[1]] - dd[o[0]]) / max(dd[o[1]], 1e-300)
+
+
+@pytest.mark.parametrize("mode", [O.STAB_SEQ, O.STAB_FALLBACK])
+@pytest.mark.parametrize("delta", [0.25, 0.5])
+def test_centroid_reference_traversal_satisfies_its_characterisation(mode, delta):
+    """§4.2.1 with the test's reference point at the stencil node nearest the stencil's
+    centroid: a retained node is kept iff its Lebesgue value is <= the value at that node
+    (found here with numpy, evaluated as a separate point of the same stencil); the center
+    always keeps its own row; the traversal is otherwise the unique index-order assignment."""
+    X = NS.disk2d(300, seed=21)
+    n, ell, m = 12, 2, 3
+    r = O.assemble(X, n, ell, m, delta, mode=mode, lref=O.LREF_CENTROID)
+    bl = O.ball_len(r["d2"], delta)
+    acc, moved = {}, 0
+    for j in np.flatnonzero(r["is_center"] == 1):
+        idx = r["nbr"][j]
+        tref, gap = _centroid_ref(X, idx)
+        assert gap > 1e-9
+        moved += tref != 0
+        W, lam = O.local_weights(X, idx, ell, m, X[idx[:bl[j]]])
+        _, lam_ref = O.local_weights(X, idx, ell, m, X[idx[tref]][None, :])
+        ok = lam <= lam_ref[0]
+        ok[0] = True
+        acc[j] = (W, lam, ok)
+    assert moved > 0  # the two readings differ on this node set
+    _check_characterisation(X, r, bl, acc, mode, ell, m)
+    ref = O.assemble(X, n, ell, m, delta, mode=mode)
+    assert not np.array_equal(ref["owner"], r["owner"]) or mode != O.STAB_SEQ
+
+
+def test_centroid_reference_equals_center_reference_when_centroids_are_centers():
+    """Nodes evenly spaced on a circle: every stencil (a node and its nearest neighbours on
+    both sides) has its centroid on the center's radius, nearest to the center itself, so the
+    centroid reading of the test is the center reading and the matrices agree bit for bit."""
+    a = 2 * np.pi * np.arange(64) / 64
+    X = np.stack([np.cos(a), np.sin(a)], axis=1)
+    r0 = O.assemble(X, 5, 1, 3, 0.4)
+    assert all(_centroid_ref(X, r0["nbr"][j])[0] == 0 for j in range(64))
+    r1 = O.assemble(X, 5, 1, 3, 0.4, lref=O.LREF_CENTROID)
+    for key in ("owner", "is_center", "col", "val", "lam_row"):
+        assert np.array_equal(r0[key], r1[key]), key
+    assert r0["stats"]["n_decisions"] > 0
 
 
 def test_delta_one_is_standard_rbffd():
