@@ -13,43 +13,69 @@
 namespace rbffd {
 
 // ------------------------------------------------------------------ exclusive scans
-// Single-CTA exclusive scan in one pass: thread t owns a contiguous chunk of the input, sums
-// it, takes the block-wide exclusive scan of the chunk sums and writes its chunk.
-// out[0..count] with out[count] = total.  When count_dev is given the element count is
-// min(count, *count_dev), read on the device (the number of grid cells in use is only known
-// there).  Used for cell offsets, weight-slot offsets and row pointers.
+// Single-CTA exclusive scan, out[0..count] with out[count] = total.  The input is walked in
+// tiles of 1024 x kScanCh elements: each tile is loaded and stored coalesced through shared
+// memory, where thread t scans its kScanCh contiguous elements; the block-wide scan of the
+// thread sums and the running total of earlier tiles give the offsets.  When count_dev is
+// given the element count is min(count, *count_dev), read on the device (the number of grid
+// cells in use is only known there).  Used for cell offsets and weight-slot offsets.
+constexpr int kScanCh = 4;
+constexpr int kScanTile = 1024 * kScanCh;
+__device__ __forceinline__ int scan_pad(int e) { return e + (e >> 5); }  // fewer bank conflicts
+
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(1024) k_scan(const TI* __restrict__ in, TO* __restrict__ out,
                                                int count, const int* __restrict__ count_dev) {
+    __shared__ TO tile[kScanTile + kScanTile / 32];
     __shared__ TO warp_tot[32];
     if (count_dev) count = min(count, *count_dev);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int chunk = (count + 1023) / 1024;
-    const int b = min(tid * chunk, count), e = min(b + chunk, count);
-    TO s = 0;
-    for (int i = b; i < e; ++i) s += (TO)in[i];
-    TO incl = s;  // inclusive warp scan of the chunk sums
-    for (int o = 1; o < 32; o <<= 1) {
-        const TO t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_tot[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        TO w = warp_tot[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const TO t = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += t;
+    TO carry = 0;  // total of the earlier tiles (the same in every thread)
+    for (int base = 0; base < count; base += kScanTile) {
+#pragma unroll
+        for (int k = 0; k < kScanCh; ++k) {
+            const int e = k * 1024 + tid, g = base + e;
+            tile[scan_pad(e)] = g < count ? (TO)in[g] : (TO)0;
         }
-        warp_tot[lane] = w;  // inclusive over warps
+        __syncthreads();
+        TO v[kScanCh], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanCh; ++k) {
+            v[k] = tile[scan_pad(tid * kScanCh + k)];
+            sum += v[k];
+        }
+        TO incl = sum;  // inclusive warp scan of the thread sums
+        for (int o = 1; o < 32; o <<= 1) {
+            const TO t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_tot[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            TO w = warp_tot[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const TO t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            warp_tot[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        TO run = carry + (wid > 0 ? warp_tot[wid - 1] : (TO)0) + (incl - sum);
+#pragma unroll
+        for (int k = 0; k < kScanCh; ++k) {
+            tile[scan_pad(tid * kScanCh + k)] = run;
+            run += v[k];
+        }
+        carry += warp_tot[31];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kScanCh; ++k) {
+            const int e = k * 1024 + tid, g = base + e;
+            if (g < count) out[g] = tile[scan_pad(e)];
+        }
+        __syncthreads();  // the next tile reuses tile[] and warp_tot[]
     }
-    __syncthreads();
-    TO run = (wid > 0 ? warp_tot[wid - 1] : (TO)0) + (incl - s);
-    for (int i = b; i < e; ++i) {
-        out[i] = run;
-        run += (TO)in[i];
-    }
-    if (tid == 0) out[count] = warp_tot[31];
+    if (tid == 0) out[count] = carry;
 }
 
 int launch_scan_i32_to_i64(const int* in, long long* out, int count, cudaStream_t s,
