@@ -481,3 +481,10 @@ def test_centroid_reference_on_per_node_stencils_matches_the_mixed_oracle():
     for key in ("owner", "is_center", "row_ptr", "col"):
         assert np.array_equal(g[key], ref[key]), key
     check_mixed_rows(X, g, ref, *params)
+
+
+def test_centroid_reference_at_the_largest_stencil_size():
+    """n = 128: the reference pre-pass walks four lanes' worth of nodes per warp lane."""
+    X = NS.jittered_grid(40, 2, seed=21)
+    ref = O.assemble(X, 128, 2, 3, 0.5, lref=O.LREF_CENTROID)
+    compare(X, 128, 2, 3, 0.5, ref=ref, lebesgue_ref=R.LREF_CENTROID)
