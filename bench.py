@@ -200,6 +200,7 @@ def run_gpu(args):
     ts_buf = {delta: torch.empty(N * n, dtype=torch.float64, device=dev) for delta in deltas} \
         if bcw is not None else None
     stream = torch.cuda.current_stream(dev)
+    copy_stream = torch.cuda.Stream(dev)
 
     def one_step(detail=None, nodes=None, host_out=False):
         # The sweep keeps its plans (and their CSR) on the device until every delta is
@@ -216,11 +217,12 @@ def run_gpu(args):
             if bcw is not None:
                 p.timestep_matrix(w["timestep_c"], out=ts_buf[delta])
             plans.append((delta, p))
-        for delta, p in plans:
-            if host_out:  # into pinned host buffers allocated once
-                row_ptr, col, val, owner = p.export(out=host_out[delta])
+        if host_out:  # into pinned host buffers allocated once, on a copy stream: one delta's
+            for delta, p in plans:  # copies overlap the next deltas' assembly
+                row_ptr, col, val, owner = p.export_async(host_out[delta], copy_stream)
                 d2h += row_ptr.nbytes + col.nbytes + val.nbytes + owner.nbytes
-            st = p.stats()
+        for delta, p in plans:
+            st = p.stats()  # (waits for the plan's copies too)
             if st["status"] != 0:
                 raise RuntimeError(f"delta {delta}: {R.rbffd_strerror(st['status'])}")
             launches += st["n_launches"]

@@ -186,6 +186,17 @@ int rbffd_stats(rbffd_plan_t plan, rbffd_stats_t* out);
 int rbffd_export(rbffd_plan_t plan, int64_t* row_ptr, int32_t* col, double* val,
                  int32_t* owner);
 
+/* rbffd_export_async -- rbffd_export enqueued on `stream` (a CUDA stream, NULL for the legacy
+ * default stream) without waiting: the copies start once the plan's last assembly has
+ * finished and are complete when `stream` reaches them, so one plan's copies can overlap
+ * another plan's assembly (host buffers should be pinned for that).  Later work on the plan
+ * (an assembly, rbffd_stats, rbffd_destroy) waits for the copies.  nnz must be known without
+ * waiting: always for uniform stencils (N n); for per-node stencils assembled with
+ * opts.sync = 0, only once rbffd_stats has been called after the assembly, else
+ * RBFFD_ESTATE.  Other errors: RBFFD_EINVAL, RBFFD_ECUDA. */
+int rbffd_export_async(rbffd_plan_t plan, int64_t* row_ptr, int32_t* col, double* val,
+                       int32_t* owner, void* stream);
+
 /* rbffd_export_stencils -- copy the kNN stencils to host memory: nbr [N][n] (nbr[k][0] ==
  * k, ordered by (squared distance, index); n is the largest stencil size of the plan), rho2
  * [N] (squared stencil width), ball_len [N]

@@ -723,6 +723,28 @@ int rbffd_export(rbffd_plan_t p, int64_t* row_ptr, int32_t* col, double* val, in
     return bad(cudaStreamSynchronize(s));
 }
 
+int rbffd_export_async(rbffd_plan_t p, int64_t* row_ptr, int32_t* col, double* val,
+                       int32_t* owner, void* stream) {
+    if (!p) return RBFFD_EINVAL;
+    if (!p->assembled) return RBFFD_ESTATE;
+    if (p->mixed && !p->counters_fresh) return RBFFD_ESTATE;
+    const size_t N = (size_t)p->N;
+    const size_t nnz = p->mixed ? (size_t)p->nnz : N * (size_t)p->n;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool other = s != p->last;
+    int rc = RBFFD_OK;
+    if (other && (rc = bad(cudaStreamWaitEvent(s, p->ev[6], 0)))) return rc;  // the assembly
+    if (row_ptr && (rc = bad(cudaMemcpyAsync(row_ptr, p->row_ptr, (N + 1) * 8, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (col && (rc = bad(cudaMemcpyAsync(col, p->col, nnz * 4, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (val && (rc = bad(cudaMemcpyAsync(val, p->val, nnz * 8, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (owner && (rc = bad(cudaMemcpyAsync(owner, p->owner, N * 4, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (other) {  // the plan's next work waits for the copies
+        if ((rc = bad(cudaEventRecord(p->ev[7], s)))) return rc;
+        if ((rc = bad(cudaStreamWaitEvent(p->last, p->ev[7], 0)))) return rc;
+    }
+    return RBFFD_OK;
+}
+
 int rbffd_export_stencils(rbffd_plan_t p, int32_t* nbr, double* rho2, int32_t* ball_len) {
     if (!p) return RBFFD_EINVAL;
     cudaStream_t s = p->last;

@@ -65,6 +65,8 @@ _SIGS = {
     "rbffd_timestep_matrix": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
     "rbffd_stats": (C.c_int, [C.c_void_p, C.POINTER(rbffd_stats_t)]),
     "rbffd_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbffd_export_async": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]),
     "rbffd_export_stencils": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_export_lambda": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_stencils_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_double,
@@ -143,6 +145,10 @@ def rbffd_stats(plan):
 
 def rbffd_export(plan, row_ptr, col, val, owner):
     return load().rbffd_export(plan, _p(row_ptr), _p(col), _p(val), _p(owner))
+
+
+def rbffd_export_async(plan, row_ptr, col, val, owner, stream):
+    return load().rbffd_export_async(plan, _p(row_ptr), _p(col), _p(val), _p(owner), stream)
 
 
 def rbffd_export_stencils(plan, nbr, rho2, ball_len):
@@ -282,6 +288,22 @@ class Plan:
             if a.dtype != dt or not a.flags.c_contiguous or a.size < size:
                 raise ValueError("export buffers: wrong dtype, layout or size")
         _check(rbffd_export(self._plan, row_ptr, col, val, owner), "rbffd_export")
+        return row_ptr[:N + 1], col[:nnz], val[:nnz], owner[:N]
+
+    def export_async(self, out, stream):
+        """export() into caller buffers `out` (pinned host arrays, as for export) enqueued on
+        the torch CUDA stream `stream` without waiting; the arrays are filled once the stream
+        has reached the copies.  Returns the views of the parts that will be filled."""
+        N = self.N
+        # per-node stencils: nnz from the counters (rbffd_stats waits for the assembly)
+        nnz = self.stats()["nnz"] if hasattr(self, "_node_params") else N * self.n
+        row_ptr, col, val, owner = out
+        for a, dt, size in ((row_ptr, np.int64, N + 1), (col, np.int32, nnz),
+                            (val, np.float64, nnz), (owner, np.int32, N)):
+            if a.dtype != dt or not a.flags.c_contiguous or a.size < size:
+                raise ValueError("export buffers: wrong dtype, layout or size")
+        _check(rbffd_export_async(self._plan, row_ptr, col, val, owner,
+                                  _stream_handle(stream)), "rbffd_export_async")
         return row_ptr[:N + 1], col[:nnz], val[:nnz], owner[:N]
 
     def export_stencils(self):

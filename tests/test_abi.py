@@ -48,6 +48,7 @@ def test_strerror_and_argument_checks_need_no_gpu():
     assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, lu_warp)[0] == R.EINVAL
     assert R.load().rbffd_set_boundary(None, None, None) == R.EINVAL
     assert R.load().rbffd_timestep_matrix(None, 0.5, None, None) == R.EINVAL
+    assert R.rbffd_export_async(None, None, None, None, None, None) == R.EINVAL
     neg_cap = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LDLT, -1, 0)
     assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, neg_cap)[0] == R.EINVAL
     neg_chunk = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LDLT, 0, 0, -1)
