@@ -220,7 +220,12 @@ class Plan:
             _check(rc, "rbffd_plan_mixed")
         self._plan = plan
 
-    def assemble(self):
+    def assemble(self, stream=None):
+        """Form L on the device (``rbffd_assemble``).  `stream` (a torch CUDA stream) moves the
+        plan to another stream from here on, e.g. assemble on the compute stream while the next
+        plan is built on a side stream."""
+        if stream is not None:
+            self._stream = stream
         rc, csr = rbffd_assemble(self._plan, _stream_handle(self._stream))
         _check(rc, "rbffd_assemble")
         return csr
