@@ -166,12 +166,45 @@ def test_ill_conditioned_stencils_are_as_accurate_as_the_oracle():
 # ------------------------------------------------------------------ full-size 2D workload
 @pytest.mark.slow
 def test_square2d_N40000_full_oracle_all_deltas():
+    """The benchmark's workload in the benchmark's launch configuration: the three plans
+    built on a side stream from pinned host nodes, assembled asynchronously in order on the
+    compute stream, each CSR copied back on a copy stream (rbffd_export_async)."""
     X = NS.square2d(40000, seed=2)
     nbr, d2 = O.knn(X, 31)
+    refs = {}
     for delta in (1.0, 0.5, 0.3):
         ref = O.assemble(X, 31, 4, 7, delta, O.STAB_SEQ, nbr, d2)
         ref["nbr"], ref["d2"] = nbr, d2
-        compare(X, 31, 4, 7, delta, ref=ref)
+        refs[delta] = ref
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    Xp = pin(X.shape, torch.float64)
+    Xp[...] = X
+    side, copy = torch.cuda.Stream(), torch.cuda.Stream()
+    compute = torch.cuda.current_stream()
+    side.wait_stream(compute)
+    plans, outs = [], {}
+    for delta in refs:
+        p = R.Plan(Xp, 31, 4, 7, delta, sync=False, stream=side)
+        p.assemble(stream=compute)
+        plans.append((delta, p))
+    N = X.shape[0]
+    for delta, p in plans:
+        outs[delta] = p.export_async((pin(N + 1, torch.int64), pin(N * 31, torch.int32),
+                                      pin(N * 31, torch.float64), pin(N, torch.int32)), copy)
+    for delta, p in plans:
+        st = p.stats()
+        assert st["status"] == 0 and st["n_centers"] == refs[delta]["stats"]["n_centers"]
+        row_ptr, col, val, owner = outs[delta]
+        ref = refs[delta]
+        assert np.array_equal(owner, ref["owner"])
+        assert np.array_equal(row_ptr, ref["row_ptr"]) and np.array_equal(col, ref["col"])
+        check_rows(dict(row_ptr=row_ptr, val=val), ref, 31)
+        nb, rho2, bl = p.export_stencils()
+        assert np.array_equal(nb, nbr) and np.array_equal(rho2, d2[:, -1])
+        lam, isc = p.export_lambda()
+        assert np.array_equal(isc, ref["is_center"])
+        np.testing.assert_allclose(lam, ref["lam_row"], rtol=TOL, atol=0)
+        p.close()
 
 
 # ------------------------------------------------------------------ apply, repeatability, API
