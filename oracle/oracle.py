@@ -16,7 +16,10 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "rbffd_oracle.c")
-LIB = os.path.join(HERE, "_build", "liboracle.so")
+# RBFFD_ORACLE_TEST_LIB: a prebuilt copy of the oracle with a planted mistake, used by the test
+# that checks every such mistake fails a pin (never set otherwise)
+_TEST_LIB = os.environ.get("RBFFD_ORACLE_TEST_LIB")
+LIB = _TEST_LIB or os.path.join(HERE, "_build", "liboracle.so")
 
 OK, EINVAL, EDUPLICATE, ENOMEM, ESINGULAR = 0, -1, -2, -3, -4
 OP_LAPLACIAN, OP_IDENTITY, OP_NORMAL = 0, 1, 2
@@ -29,6 +32,8 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (plain C, FP64, no FMA contraction)."""
+    if _TEST_LIB:
+        return LIB
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
     stale = (not os.path.exists(LIB)) or os.path.getmtime(LIB) < max(
         os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "rbffd_oracle.h")))
