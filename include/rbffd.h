@@ -71,7 +71,8 @@ typedef struct {
     int max_ctas;       /* cap on the persistent traversal grid, so that plans assembled
                            concurrently on several streams share the GPU; 0 = fill the GPU */
     int team;           /* threads per stencil team: 0 = chosen from the shared-memory
-                           footprint (128 when several stencils fit an SM, else 512), or
+                           footprint (96 for LDL^T, or 128 if that keeps more stencils
+                           resident, when more than 4 fit an SM; else 512), or
                            32 (one warp per stencil), 64, 96, 128 or 512 to force one (used
                            by the schedule autotuner); 32, 64 and 96 need RBFFD_FACTOR_LDLT,
                            else RBFFD_EINVAL */

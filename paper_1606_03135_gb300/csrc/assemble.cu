@@ -1405,10 +1405,11 @@ static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
 
 // Team size for a launch when none is forced: 128 threads when several stencils fit an SM's
 // shared memory, else 512 so that the one or few resident stencils still keep enough warps
-// busy.  The LDL^T traversal takes 96 threads instead of 128 when that keeps more stencils
-// resident (small systems, where 128-thread teams are register-bound): more stencils in
-// flight hide more of each one's serial pivot steps, even one more out of a dozen (2D,
-// K = 46, 13 columns: 13 stencils of 96 threads beat 12 of 128 by 7%).  A
+// busy.  The LDL^T traversal takes 96 threads instead of 128 unless that keeps fewer stencils
+// resident: more stencils in flight hide more of each one's serial pivot steps (2D, K = 46,
+// 13 columns: 13 stencils of 96 threads beat 12 of 128 by 7%), and at equal residency the
+// smaller team wastes fewer lanes in its short steps (2D, 21 columns: 1.11 against 1.17 ms;
+// 3D, K = 65, one column: 15.5 against 15.7 ms).  A
 // forced size (32, 64 and 96 exist for the LDL^T traversal only) is taken as given.
 template <int D, bool PACKED, bool TRAVERSAL>
 static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool chunked = false) {
@@ -1424,7 +1425,7 @@ static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool 
         if (TRAVERSAL && PACKED && nt == kNT) {
             int p96 = 0;
             if ((rc = occ(96, &p96))) return rc;
-            if (p96 > per_sm) nt = 96;
+            if (p96 >= per_sm) nt = 96;
         }
     }
     if ((rc = occ(nt, per_sm_out))) return rc;

@@ -346,9 +346,10 @@ class Plan:
 # ------------------------------------------------------------------ schedule autotuner
 def autotune(nodes, n, ell, m, delta, mode=STAB_SEQ, candidates=None, repeats=2):
     """Pick the traversal schedule for a workload -- warp-per-stencil (32 threads), 64-, 96-, 128-
-    or 512-thread tiles per stencil, the persistent-grid cap, and the right-hand sides carried
-    per factorization (8 or 16 where balls are larger) -- by timing assemblies of each candidate
-    on the device (CUDA events, best of `repeats`, after a warm-up assembly).
+    or 512-thread tiles per stencil, the persistent-grid cap, and, with 96- or 128-thread tiles,
+    fewer right-hand sides per factorization (about 0.3, 0.45 and 0.6 of the largest ball:
+    more stencils fit an SM, later columns take extra passes) -- by timing assemblies of each
+    candidate on the device (CUDA events, best of `repeats`, after a warm-up assembly).
     Returns (best kwargs for Plan, {candidate: ms}).  Results do not depend on the schedule
     (the same stencils are solved the same way), only the time does."""
     import torch
@@ -359,7 +360,9 @@ def autotune(nodes, n, ell, m, delta, mode=STAB_SEQ, candidates=None, repeats=2)
         if np.ndim(n) == 0:
             with Plan(nodes, n, ell, m, delta, mode=mode) as p:
                 max_ball = p.stats()["max_ball"]
-            candidates += [dict(rhs_chunk=c) for c in (8, 16) if c < max_ball]
+            chunks = sorted({max(4, round(max_ball * f)) for f in (0.3, 0.45, 0.6)})
+            candidates += [dict(team=t, rhs_chunk=c) for t in (96, 128) for c in chunks
+                           if c < max_ball]
     timings = {}
     for cand in candidates:
         try:
