@@ -2,6 +2,7 @@
 // (stream-ordered allocations), the launch sequence and error reporting.  No call throws,
 // traps, asserts or exits; every CUDA error becomes an RBFFD_* code.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -285,6 +286,15 @@ int refresh_counters(rbffd_plan_s* p) {
     return RBFFD_OK;
 }
 
+// A named host range for profilers (nsys timelines, ncu --nvtx filters): the span of the call
+// that enqueues a phase.  Without an attached tool the push and pop cost a few nanoseconds.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 int max_optin_smem() {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
@@ -523,12 +533,14 @@ extern "C" {
 
 int rbffd_plan(const double* nodes, int64_t N, int d, int n, int ell, int m, double delta,
                const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
+    NvtxRange r("rbffd_plan");
     return plan_impl(nodes, N, d, n, ell, m, nullptr, nullptr, nullptr, delta, opts, stream, out);
 }
 
 int rbffd_plan_mixed(const double* nodes, int64_t N, int d, const int32_t* n_node,
                      const int32_t* ell_node, const int32_t* m_node, double delta,
                      const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
+    NvtxRange r("rbffd_plan_mixed");
     if (!out) return RBFFD_EINVAL;
     *out = nullptr;
     if (!n_node || !ell_node || !m_node || N < 1) return RBFFD_EINVAL;
@@ -539,6 +551,7 @@ int rbffd_plan_mixed(const double* nodes, int64_t N, int d, const int32_t* n_nod
 }
 
 int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
+    NvtxRange r("rbffd_assemble");
     if (!p) return RBFFD_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     p->last = s;
@@ -589,10 +602,14 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.max_ctas = p->opts.max_ctas;
 
     if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
-    rc = launch_traversal(p->d, a, p->lp, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
+    {
+        NvtxRange t("traversal");
+        rc = launch_traversal(p->d, a, p->lp, p->indeg, s, &p->launches, p->ev[2], p->ev[3]);
+    }
     if (rc) return rc;
     cudaEventRecord(p->ev[4], s);
     if (p->opts.stab_mode == RBFFD_STAB_FALLBACK || p->n_boundary > 0) {
+        NvtxRange f("fallback and boundary rows");
         rc = launch_fallback(p->d, a, p->lp, s, &p->launches);
         if (rc) return rc;
     }
@@ -664,6 +681,7 @@ int rbffd_timestep_matrix(rbffd_plan_t p, double c, double* val_out, void* strea
 }
 
 int rbffd_apply(rbffd_plan_t p, const double* u, double* y, void* stream) {
+    NvtxRange r("rbffd_apply");
     if (!p || !u || !y) return RBFFD_EINVAL;
     if (!p->assembled) return RBFFD_ESTATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -708,6 +726,7 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
 }
 
 int rbffd_export(rbffd_plan_t p, int64_t* row_ptr, int32_t* col, double* val, int32_t* owner) {
+    NvtxRange r("rbffd_export");
     if (!p) return RBFFD_EINVAL;
     if (!p->assembled) return RBFFD_ESTATE;
     cudaStream_t s = p->last;
@@ -725,6 +744,7 @@ int rbffd_export(rbffd_plan_t p, int64_t* row_ptr, int32_t* col, double* val, in
 
 int rbffd_export_async(rbffd_plan_t p, int64_t* row_ptr, int32_t* col, double* val,
                        int32_t* owner, void* stream) {
+    NvtxRange r("rbffd_export_async");
     if (!p) return RBFFD_EINVAL;
     if (!p->assembled) return RBFFD_ESTATE;
     if (p->mixed && !p->counters_fresh) return RBFFD_ESTATE;
