@@ -61,3 +61,17 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["unit"] == "rows/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["workload"] == bench.WORKLOAD
+
+
+def test_kernel_source_hash_ignores_comments_only(tmp_path):
+    """The DRAM-traffic record is keyed by the kernel source without comments: a comment edit
+    keeps it, a code edit invalidates it."""
+    a = tmp_path / "a.cu"
+    a.write_text("// one\n__global__ void k(int* x) {\n    x[0] = 1;  // set\n}\n")
+    b = tmp_path / "b.cu"
+    b.write_text("/* two */\n__global__ void k(int* x) {\n\n    x[0] = 1;\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("__global__ void k(int* x) {\n    x[0] = 2;\n}\n")
+    assert bench.kernel_source_hash(str(a)) == bench.kernel_source_hash(str(b))
+    assert bench.kernel_source_hash(str(a)) != bench.kernel_source_hash(str(c))
+
