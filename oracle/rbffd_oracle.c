@@ -349,23 +349,14 @@ static void put_row(int64_t i, int n, const int32_t* stencil_idx, const double* 
 
 /* Position t in stencil I (n nodes) of the node nearest the stencil's centroid (§4.2.1, the
  * reference point of the Lebesgue test in its centroid reading); ties go to the lower t.
- * The centroid is (sum of the n nodes) * (1/n), each coordinate's sum taken in one fixed
- * order: 32 partial sums s_l = x_l + x_(l+32) + ... (from 0.0, in that order), then five
- * halving steps s_l <- s_l + s_(l xor o) for o = 16, 8, 4, 2, 1. */
+ * The centroid is the mean of the n nodes: each coordinate summed over the stencil in kNN
+ * order starting from 0.0, then divided by n. */
 static int centroid_node(const double* X, int d, const int32_t* I, int n) {
     double c[3] = {0.0, 0.0, 0.0};
-    const double inv_n = 1.0 / (double)n;
     for (int a = 0; a < d; ++a) {
-        double s[32], u[32];
-        for (int l = 0; l < 32; ++l) {
-            s[l] = 0.0;
-            for (int t = l; t < n; t += 32) s[l] = s[l] + X[(int64_t)I[t] * d + a];
-        }
-        for (int o = 16; o >= 1; o >>= 1) {
-            for (int l = 0; l < 32; ++l) u[l] = s[l] + s[l ^ o];
-            memcpy(s, u, sizeof(s));
-        }
-        c[a] = s[0] * inv_n;
+        double s = 0.0;
+        for (int t = 0; t < n; ++t) s = s + X[(int64_t)I[t] * d + a];
+        c[a] = s / (double)n;
     }
     int best = 0;
     double bd = sqdist(X + (int64_t)I[0] * d, c, d);

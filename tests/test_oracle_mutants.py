@@ -34,8 +34,9 @@ MUTANTS = [
      "pass = lam[e] < 0.95 * lam[e_ref];"),
     ("centroid reference ignored", "pass = lam[e] <= lam[e_ref];",
      "pass = lam[e] <= lam[0];"),
-    ("centroid divided by n - 1", "const double inv_n = 1.0 / (double)n;",
-     "const double inv_n = 1.0 / (double)(n - 1);"),
+    ("centroid divided by n - 1", "c[a] = s / (double)n;", "c[a] = s / (double)(n - 1);"),
+    ("centroid sum skips the center", "for (int t = 0; t < n; ++t) s = s + X[(int64_t)I[t] * d + a];",
+     "for (int t = 1; t < n; ++t) s = s + X[(int64_t)I[t] * d + a];"),
 ]
 
 
