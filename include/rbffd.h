@@ -75,7 +75,8 @@ typedef struct {
                            resident, when more than 4 fit an SM; else 512), or
                            32 (one warp per stencil), 64, 96, 128 or 512 to force one (used
                            by the schedule autotuner); 32, 64 and 96 need RBFFD_FACTOR_LDLT,
-                           else RBFFD_EINVAL */
+                           else RBFFD_EINVAL; 96 and 128 are refused for plans that refine
+                           (see refine) */
     int rhs_chunk;      /* right-hand sides carried through one factorization (RBFFD_FACTOR_LDLT):
                            a center with more columns solves the rest afterwards, this many at
                            a time, with the stored factors (same results, bit for bit).  0 = all
@@ -86,7 +87,27 @@ typedef struct {
                            RBFFD_EINVAL */
     int lebesgue_ref;   /* RBFFD_LREF_CENTER (default) or RBFFD_LREF_CENTROID; the centroid
                            reference solves no center ahead of its turn */
+    int refine;         /* one step of iterative refinement of the LDL^T local solves of plans
+                           whose largest system has K >= RBFFD_REFINE_MIN_K (degree-4 and -5
+                           stencils in 3D reach condition numbers near 1e10, where the first
+                           solution's error is dominated by the symmetric-pivoting
+                           factorization): RBFFD_REFINE_AUTO (default) refines a system when its
+                           pivots span at least 2^16 (max |d| / min |d| over the D blocks, a
+                           lower bound of its condition number); RBFFD_REFINE_ALL refines every
+                           system of every plan; RBFFD_REFINE_NONE none.  The residual b - A x0 is formed
+                           in FP64 with the assembled system (copied to the plan's assembly
+                           memory before the factorization: one full K x K copy per resident
+                           CTA) and the correction is solved with
+                           the stored factors (about 4 K^2 flops per refined column).  The
+                           traversal's 96- and 128-thread teams have no refinement step, so
+                           forcing them (opts.team) on a plan that refines is RBFFD_EINVAL.
+                           RBFFD_FACTOR_LU is never refined.  Other values: RBFFD_EINVAL */
 } rbffd_opts;
+
+#define RBFFD_REFINE_AUTO 0
+#define RBFFD_REFINE_ALL 1
+#define RBFFD_REFINE_NONE 2
+#define RBFFD_REFINE_MIN_K 100
 
 typedef struct rbffd_plan_s* rbffd_plan_t; /* opaque; owned by the library */
 
@@ -129,6 +150,12 @@ typedef struct {
     int64_t n_spec_used;     /* centers whose solve had been made ahead */
     int64_t rhs_chunk;       /* right-hand sides carried per factorization (opts.rhs_chunk as
                                 chosen by rbffd_plan) */
+    double sum_k3;           /* sum over factored stencils of K^3 */
+    double sum_k2_cols;      /* sum over factored stencils of K^2 q_k, q_k = the columns the
+                                result needed (every retained node solved, kept or not) */
+    double flops_refine;     /* refinement work executed: 4 K^2 per refined column */
+    int32_t refine_min_K;    /* systems with K >= this are refined (INT32_MAX: none) */
+    int32_t pad0;
 } rbffd_stats_t;
 
 /* rbffd_plan -- build the stencils of §4.1 for one node set.

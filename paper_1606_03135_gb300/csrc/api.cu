@@ -55,6 +55,10 @@ struct rbffd_plan_s {
     long long total_slots = 0;
     int qcap = 0, stride = 0;
     LaunchPlan lp;
+    int refine_min_K = 0x7fffffff;  // systems with K >= this are refined
+    long long rs_doubles = 0, rs_stride = 0;  // refinement scratch: size, per traversal CTA
+    int rs_x0 = 0;                  // offset of the first solution within a slot
+    double* rs = nullptr;
     // traversal and results
     bool have_asm = false, assembled = false;
     int* state = nullptr;
@@ -353,7 +357,8 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
             K_max = nk + Mk > K_max ? nk + Mk : K_max;
         }
     }
-    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0, 0, RBFFD_LREF_CENTER};
+    rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0, 0, RBFFD_LREF_CENTER,
+                 RBFFD_REFINE_AUTO};
     if (opts) o = *opts;
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
         (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0 ||
@@ -361,7 +366,8 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
          o.team != 512) ||
         (o.factor == RBFFD_FACTOR_LU && o.team != 0 && o.team != 128 && o.team != 512) ||
         o.rhs_chunk < 0 || (o.factor == RBFFD_FACTOR_LU && o.rhs_chunk > 0) ||
-        (o.lebesgue_ref != RBFFD_LREF_CENTER && o.lebesgue_ref != RBFFD_LREF_CENTROID))
+        (o.lebesgue_ref != RBFFD_LREF_CENTER && o.lebesgue_ref != RBFFD_LREF_CENTROID) ||
+        o.refine < RBFFD_REFINE_AUTO || o.refine > RBFFD_REFINE_NONE)
         return RBFFD_EINVAL;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
 
@@ -515,9 +521,32 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
                 }
         }
         p->lp.force_nt = o.team;
+        p->refine_min_K = (!ldlt || o.refine == RBFFD_REFINE_NONE) ? 0x7fffffff
+                          : o.refine == RBFFD_REFINE_ALL           ? 0
+                                                                   : RBFFD_REFINE_MIN_K;
+        p->lp.refine_min_K = p->refine_min_K;
         rc = prepare_solve_kernels(d, o.factor == RBFFD_FACTOR_LDLT, n, p->K, p->qcap, qmax,
                                    (int)basis_count, &p->lp);
         if (rc) goto fail;
+        // refinement scratch: one slot per CTA of every launch that refines (the traversal when
+        // its largest system qualifies, the fallback classes that do), each the lower triangle
+        // of the largest system plus its first solution of one chunk of columns
+        if (p->K >= p->refine_min_K) {  // the largest over the traversal and fallback launches
+            // per CTA: the full K x K matrix, then x0 and 4 partial sums per (unknown, column)
+            auto sq32 = [](long long K) { return (K * K + 31) / 32 * 32; };
+            const long long K = p->K;
+            p->rs_x0 = (int)sq32(K);
+            p->rs_stride = (p->rs_x0 + 5 * K * p->qcap + 31) / 32 * 32;
+            long long doubles = (long long)p->lp.grid * p->rs_stride;
+            for (int c = 0; c < p->lp.n_fb; ++c) {
+                FallbackClass& f = p->lp.fb[c];
+                f.rs_x0 = (int)sq32(f.K);
+                f.rs_stride = (f.rs_x0 + 5 * f.K + 31) / 32 * 32;
+                if ((long long)f.grid * f.rs_stride > doubles) doubles = (long long)f.grid * f.rs_stride;
+            }
+            p->rs_doubles = doubles;
+            p->asm_bytes += ((size_t)doubles * 8 + 255) & ~size_t(255);
+        }
     }
     *out = p;
     return RBFFD_OK;
@@ -566,7 +595,8 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
                      o_sl = c.add<double>(S), o_sp = c.add<unsigned char>(S),
                      o_rp = c.add<long long>(N + 1), o_col = c.add<int>(N * n),
                      o_val = c.add<double>(N * n), o_lam = c.add<double>(N),
-                     o_isc = c.add<unsigned char>(N), o_spec = c.add<int>(N);
+                     o_isc = c.add<unsigned char>(N), o_spec = c.add<int>(N),
+                     o_rs = c.add<double>((size_t)p->rs_doubles);
         if ((rc = pool_alloc(&p->asm_block, c.bytes, p->device, s))) return rc;
         void* b = p->asm_block;
         p->state = at<int>(b, o_state); p->pending = at<int>(b, o_pend);
@@ -577,6 +607,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
         p->col = at<int>(b, o_col); p->val = at<double>(b, o_val);
         p->lam_row = at<double>(b, o_lam); p->is_center = at<unsigned char>(b, o_isc);
         p->spec = at<int>(b, o_spec);
+        p->rs = p->rs_doubles > 0 ? at<double>(b, o_rs) : nullptr;
         p->have_asm = true;
     }
     SolveArgs a{};
@@ -600,6 +631,11 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.no_seed = p->opts.fault_inject == 1;
     a.factor = p->opts.factor;
     a.max_ctas = p->opts.max_ctas;
+    a.rs = p->rs;
+    a.rs_stride = p->rs_stride;
+    a.rs_x0 = p->rs_x0;
+    a.refine_min_K = p->refine_min_K;
+    a.refine_all = p->opts.refine == RBFFD_REFINE_ALL ? 1 : 0;
 
     if ((rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s)))) return rc;
     {
@@ -697,6 +733,7 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
     out->n_nodes = p->N;
     out->max_ball = p->max_ball;
     out->rhs_chunk = p->qcap;
+    out->refine_min_K = p->refine_min_K;
     out->n = p->n; out->M = p->M; out->K = p->K; out->d = p->d;
     out->n_launches = p->launches;
     out->plan_bytes = (int64_t)p->plan_bytes;
@@ -716,6 +753,9 @@ int rbffd_stats(rbffd_plan_t p, rbffd_stats_t* out) {
         // (1/3) K^3 (LDL^T) or (2/3) K^3 (LU) per factorization, 2 K^2 per owned row's solve
         const double c3 = p->opts.factor == RBFFD_FACTOR_LU ? 2.0 / 3.0 : 1.0 / 3.0;
         out->alg_flops = c3 * (double)c.sum_k3 + 2.0 * (double)c.sum_k2q;
+        out->sum_k3 = (double)c.sum_k3;
+        out->sum_k2_cols = (double)c.sum_k2c;
+        out->flops_refine = 4.0 * (double)c.sum_k2r;
         out->nnz = p->nnz;
         if (cudaEventElapsedTime(&ms, p->ev[2], p->ev[3]) == cudaSuccess) out->ms_traversal = ms;
         if (cudaEventElapsedTime(&ms, p->ev[4], p->ev[5]) == cudaSuccess) out->ms_fallback = ms;

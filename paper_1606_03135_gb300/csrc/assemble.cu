@@ -448,13 +448,24 @@ __device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem&
 // and 2x2 pivots with alpha = (1 + sqrt(17)) / 8; symmetric swaps are tracked in sm.perm.
 // Returns false (uniformly) on an exactly singular pivot column.  On success sm.rowof[u] is
 // the row of the right-hand-side block that holds unknown u.
-template <int NT>
+// Pivot ratio of the factorization, written by factor_solve_ldlt<NT, true>: floor(log2) of
+// max |D block entry| times floor(log2) of max |D^-1 block entry|, i.e. an estimate (within a
+// factor 4) of log2 of max |d| / min |d| over the pivots, a lower bound of the system's
+// condition number.  Read after a barrier.
+__shared__ int s_pivot_log2_ratio;
+constexpr int kRefinePivotLog2 = 16;  // refine systems whose pivots span at least 2^16
+
+// Biased IEEE exponent of |v| (an integer-pipe floor(log2 |v|) + 1023).
+__device__ __forceinline__ int exp_bits(double v) { return (int)((abs_bits(v) >> 52) & 0x7ff); }
+
+template <int NT, bool TRACK = false>
 __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
     __shared__ int s_ok, s_kind;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int xs = sm.xs;
     double* T = sm.T;
     double* X = sm.X;
+    int e_d = 0, e_r = 0;  // (thread 0, TRACK) largest exponents of |D| and |D^-1| entries
     for (int r = tid; r < K; r += NT) sm.perm[r] = r;
     __syncthreads();
     int p = 0;
@@ -536,6 +547,10 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
             if (ok) {
                 if (kind == 1 && swap_a == swap_b && !slow) {  // the usual step: all in registers
                     if (lane == 0) { sm.rdiag[p] = rcp_p; sm.pk[p] = 1; }
+                    if (TRACK && lane == 0) {
+                        e_d = max(e_d, exp_bits(dpp));
+                        e_r = max(e_r, exp_bits(rcp_p));
+                    }
                     const double s0 = w0 * rcp_p, s1 = w1 * rcp_p;
                     if (i0 < K) { sm.wv[i0] = w0; T[tri(i0) + p] = s0; }
                     if (i1 < K) { sm.wv[i1] = w1; T[tri(i1) + p] = s1; }
@@ -547,6 +562,10 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
                 } else if (kind == 1) {  // after a swap (or an extreme pivot): reload
                     const double rcp = rcp_fixed(T[tri(p) + p]);
                     if (lane == 0) { sm.rdiag[p] = rcp; sm.pk[p] = 1; }
+                    if (TRACK && lane == 0) {
+                        e_d = max(e_d, exp_bits(T[tri(p) + p]));
+                        e_r = max(e_r, exp_bits(rcp));
+                    }
                     for (int i = p + 1 + lane; i < K; i += 32) {
                         const double w = T[tri(i) + p];
                         sm.wv[i] = w;
@@ -560,6 +579,10 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
                         sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.dinv2[p] = i11;
                         sm.pk[p] = 2; sm.pk[p + 1] = 0;
                         T[tri(p + 1) + p] = 0.0;  // L has no entry inside a 2x2 pivot block
+                        if (TRACK) {
+                            e_d = max(e_d, max(exp_bits(d0), max(exp_bits(d1), exp_bits(d2))));
+                            e_r = max(e_r, max(exp_bits(i00), max(exp_bits(i01), exp_bits(i11))));
+                        }
                     }
                     for (int i = p + 2 + lane; i < K; i += 32) {
                         const double w1 = T[tri(i) + p], w2 = T[tri(i) + p + 1];
@@ -620,15 +643,9 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
     }
     // The inverse permutation (read after the caller's next barrier).
     for (int r = tid; r < K; r += NT) sm.rowof[sm.perm[r]] = r;
+    if (TRACK && tid == 0) s_pivot_log2_ratio = e_d + e_r - 2 * 1023;
     ldlt_solve_tail<NT>(K, q, sm);
     return true;
-}
-
-template <int D, bool PACKED, int NT>
-__device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
-                            const StencilSmem& sm) {
-    assemble_local<D, PACKED, NT>(a, sh, j, q, sm);
-    return PACKED ? factor_solve_ldlt<NT>(sh.K, q, sm) : factor_solve_lu<NT>(sh.K, q, sm);
 }
 
 // ------------------------------------------------------------------ right-hand sides in chunks
@@ -655,33 +672,39 @@ __device__ __forceinline__ double mono_value(const Basis& bs, int l, const doubl
     return v;
 }
 
+// Right-hand-side entry of unknown u for the column of stencil position t: m (m + D - 2)
+// r^(m-2) (as in the pair loop) for a stencil node, the Laplacian of psi_(u-n) at node t for a
+// monomial.
+template <int D>
+__device__ __forceinline__ double rhs_entry(const Shape& sh, int u, int t, const StencilSmem& sm) {
+    const int n = sh.n;
+    double v = 0.0;
+    if (u < n) {
+        if (u != t) {
+            const double r2 = sqdist_rn<D>(sm.xi + u * D, sm.xi + t * D);
+            double pm2 = sqrt_fast(r2);
+            for (int k = 0; k < (sh.m - 3) / 2; ++k) pm2 = __dmul_rn(pm2, r2);
+            v = __dmul_rn(sh.coef, pm2);
+        }
+    } else {
+        const int l = u - n;
+        for (int d = 0; d < D; ++d) {
+            const int ch = sh.bs.lap_child[l * D + d];
+            if (ch >= 0)
+                v = fma(exact_double(sh.bs.lap_coef[l * D + d]), mono_value<D>(sh.bs, ch, sm.xi + t * D), v);
+        }
+    }
+    return v;
+}
+
 // Right-hand sides of columns c0 .. c0+qk-1 into sm.X, rows in the factorization's permuted
 // order (row r holds unknown perm[r]).
 template <int D, int NT>
 __device__ void chunk_rhs(const Shape& sh, int c0, int qk, const StencilSmem& sm) {
-    const int K = sh.K, n = sh.n;
+    const int K = sh.K;
     for (int e = threadIdx.x; e < K * qk; e += NT) {
         const int r = e / qk, c = e - (e / qk) * qk;
-        const int u = sm.perm[r];
-        const int t = sm.cols[c0 + c];
-        double v = 0.0;
-        if (u < n) {
-            if (u != t) {  // m (m + D - 2) r^(m-2), as in the pair loop
-                const double r2 = sqdist_rn<D>(sm.xi + u * D, sm.xi + t * D);
-                double pm2 = sqrt_fast(r2);
-                for (int k = 0; k < (sh.m - 3) / 2; ++k) pm2 = __dmul_rn(pm2, r2);
-                v = __dmul_rn(sh.coef, pm2);
-            }
-        } else {  // Laplacian of psi_(u-n) at the column's node
-            const int l = u - n;
-            for (int d = 0; d < D; ++d) {
-                const int ch = sh.bs.lap_child[l * D + d];
-                if (ch >= 0)
-                    v = fma(exact_double(sh.bs.lap_coef[l * D + d]),
-                            mono_value<D>(sh.bs, ch, sm.xi + t * D), v);
-            }
-        }
-        sm.X[r * sm.xs + c] = v;
+        sm.X[r * sm.xs + c] = rhs_entry<D>(sh, sm.perm[r], sm.cols[c0 + c], sm);
     }
 }
 
@@ -709,17 +732,189 @@ __device__ void forward_subst(int K, int q, const StencilSmem& sm) {
 
 template <int NT>
 __device__ __forceinline__ void lebesgue_values(int n, int K, int q, const StencilSmem& sm,
-                                                int off);
+                                                int off = 0);
+
+// Right-hand side of the normal derivative at the stencil center (the origin of the scaled
+// coordinates) for unknown u of node i's own stencil (§5, a Neumann row): d/dn ||y - xi_u||^m
+// at y = 0 is -m ||xi_u||^(m-2) (xi_u . n), and of the monomials only the linear ones have a
+// nonzero gradient there (d/dn xi_a = n_a).
+template <int D>
+__device__ __forceinline__ double neumann_value(const SolveArgs& a, const Shape& sh, int i, int u,
+                                                const StencilSmem& sm) {
+    const double* nv = a.nrm + (size_t)i * D;
+    if (u < sh.n) {
+        const double mm = exact_double(sh.m);
+        const double* xj = sm.xi + u * D;
+        double r2 = xj[0] * xj[0], dot = xj[0] * nv[0];
+        for (int c = 1; c < D; ++c) {
+            r2 = fma(xj[c], xj[c], r2);
+            dot = fma(xj[c], nv[c], dot);
+        }
+        double pm2 = sqrt_fast(r2);  // r^(m-2), m odd
+        for (int t = 0; t < (sh.m - 3) / 2; ++t) pm2 *= r2;
+        return -mm * pm2 * dot;
+    }
+    const int l = u - sh.n;
+    return (l > 0 && sh.bs.parent[l] == 0) ? nv[sh.bs.var[l]] : 0.0;
+}
+
+// Team sizes whose traversal kernels carry the refinement step: the 96- and 128-thread teams
+// run with 40 registers for small systems (many per SM), and the planner gives plans that
+// refine (largest system K >= 100, at most a few per SM) 512-thread teams, or 32 or 64 when
+// forced.  The fallback kernel carries it at every team size (ALL_TEAMS).
+__host__ __device__ constexpr bool team_refines(int nt) { return nt != 96 && nt != 128; }
+
+// Per-CTA scratch of the refinement step of this launch, or nullptr when the plan refines
+// nothing.  (Whether a system is refined is decided after its factorization.)
+template <int NT, bool ALL_TEAMS = false>
+__device__ __forceinline__ double* refine_scratch(const SolveArgs& a) {
+    if constexpr (!ALL_TEAMS && !team_refines(NT)) {
+        return nullptr;
+    } else {
+        return a.rs != nullptr ? a.rs + (size_t)blockIdx.x * a.rs_stride : nullptr;
+    }
+}
+
+// The residual's dot products sum_v A_uv x0_v are split into kRefineSegs fixed ranges of v
+// (the same for every team size), summed in order within a range and then combined in a
+// fixed order, so every thread of a team has short independent chains and the bits do not
+// depend on the team.
+constexpr int kRefineSegs = 4;
+
+// Partial sum over v in segment g of A_uv x0_v: gA is the full assembled matrix (row v at
+// v K, so the threads of a warp, holding consecutive u, read one contiguous row), gX0 holds
+// x0 by unknown (unknown v of column c at v qk + c: one address for the whole warp).
+__device__ __forceinline__ double residual_part(int u, int c, int g, int K, int qk,
+                                                const double* __restrict__ gA,
+                                                const double* __restrict__ gX0) {
+    const int len = (K + kRefineSegs - 1) / kRefineSegs;
+    const int v0 = g * len, v1 = min(K, v0 + len);
+    double s = 0.0;
+#pragma unroll 8
+    for (int v = v0; v < v1; ++v) s = fma(__ldcg(gA + (size_t)v * K + u), __ldcg(gX0 + v * qk + c), s);
+    return s;
+}
+
+// One step of iterative refinement (J. H. Wilkinson, "Rounding Errors in Algebraic Processes",
+// 1963) of the columns c0 .. c0+qk-1 held in sm.X after their LDL^T solve:
+// x1 = x0 + (L D L^T)^-1 (b - A x0), the residual formed in FP64 with the assembled matrix A
+// (gA, copied in full before the factorization overwrote it) and the right-hand sides rebuilt
+// bit for bit.  On the ill-conditioned systems of large stencils (condition
+// numbers up to ~1e10) the first solution's forward error is dominated by the symmetric-
+// pivoting factorization; one step brings it down to that of the assembled system itself.
+// Only systems whose pivot ratio (s_pivot_log2_ratio) reaches 2^kRefinePivotLog2 are refined,
+// unless a.refine_all: the well-conditioned majority keeps its first solution.  kind: 0 the
+// Laplacian right-hand sides of the columns in sm.cols, 2 the normal derivative at the center
+// of node i (one column).  gX0 holds x0 (K x qk).  With at most one column per warp each warp
+// forward-substitutes its own column; the arithmetic of an entry is the same either way, so
+// every team size gives the same bits.
+template <int D, int NT>
+__device__ void refine_columns(const SolveArgs& a, const Shape& sh, int c0, int qk,
+                               const StencilSmem& sm, const double* __restrict__ gA,
+                               double* __restrict__ gX0, int kind, int i) {
+    constexpr int NW = NT / 32;
+    const int K = sh.K, xs = sm.xs, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    double* gP = gX0 + (size_t)K * qk;  // kRefineSegs partial sums per entry
+    __syncthreads();  // (the last solve steps may have been warp-synchronous)
+    // adaptive: only systems whose pivots span at least 2^16 (unless every system is refined)
+    if (a.refine_all == 0 && s_pivot_log2_ratio < kRefinePivotLog2) return;
+    for (int e = tid; e < K * qk; e += NT) {  // x0 by unknown
+        const int r = e / qk, c = e - r * qk;
+        gX0[sm.perm[r] * qk + c] = sm.X[r * xs + c];
+    }
+    if (kind == 2) {
+        for (int r = tid; r < K; r += NT) sm.X[r * xs] = neumann_value<D>(a, sh, i, sm.perm[r], sm);
+    } else {
+        chunk_rhs<D, NT>(sh, c0, qk, sm);
+    }
+    __syncthreads();
+    for (int e = tid; e < K * qk * kRefineSegs; e += NT) {  // (unknown, column, segment) items
+        const int g = e / (K * qk), uc = e - g * (K * qk);
+        const int u = uc / qk, c = uc - u * qk;
+        gP[e] = residual_part(u, c, g, K, qk, gA, gX0);
+    }
+    __syncthreads();
+    for (int e = tid; e < K * qk; e += NT) {  // r = b - ((p0 + p1) + (p2 + p3)), rows permuted
+        const int r = e / qk, c = e - r * qk;
+        const int uc = sm.perm[r] * qk + c;
+        const double* P = gP + uc;
+        const size_t st = (size_t)K * qk;
+        sm.X[r * xs + c] = sm.X[r * xs + c] - ((__ldcg(P) + __ldcg(P + st)) + (__ldcg(P + 2 * st) + __ldcg(P + 3 * st)));
+    }
+    __syncthreads();
+    if (qk <= NW) {  // forward substitution, a warp per column with warp synchronisation only
+        if (wid < qk) {
+            double* Xc = sm.X + wid;
+            for (int p = 0; p < K;) {
+                const int k = sm.pk[p];
+                const int p0 = p + k - 1;
+                const double xp = Xc[p * xs], xq = k == 2 ? Xc[(p + 1) * xs] : 0.0;
+                for (int r = p0 + 1 + lane; r < K; r += 32) {
+                    const double* Tr = sm.T + tri(r);
+                    double* dst = Xc + r * xs;
+                    if (k == 1) *dst = fma(-Tr[p], xp, *dst);
+                    else *dst = fma(-Tr[p + 1], xq, fma(-Tr[p], xp, *dst));
+                }
+                __syncwarp();
+                p += k;
+            }
+        }
+    } else {
+        forward_subst<NT>(K, qk, sm);
+    }
+    ldlt_solve_tail<NT>(K, qk, sm);
+    __syncthreads();
+    for (int e = tid; e < K * qk; e += NT) {
+        const int r = e / qk, c = e - r * qk;
+        sm.X[r * xs + c] += __ldcg(gX0 + sm.perm[r] * qk + c);
+    }
+    if (tid == 0) atomicAdd(&a.ctr->sum_k2r, (unsigned long long)K * K * qk);
+    __syncthreads();
+}
+
+// The assembled symmetric matrix (packed lower triangle in shared memory) to gA in full,
+// row-major K x K, before the factorization overwrites it.
+template <int NT>
+__device__ __forceinline__ void copy_full_matrix(int K, const StencilSmem& sm, double* __restrict__ gA) {
+    for (int e = threadIdx.x; e < K * K; e += NT) {
+        const int r = e / K, c = e - r * K;
+        gA[e] = r >= c ? sm.T[tri(r) + c] : sm.T[tri(c) + r];
+    }
+}
 
 // Columns c0 .. c0+qk-1 with the stored LDL^T factors: right-hand sides, forward substitution,
-// D solve, back substitution and Lebesgue values (a chunk after the first of a center).
+// D solve, back substitution (refined like the first chunk) and Lebesgue values (a chunk after
+// the first of a center).
 template <int D, int NT>
-__device__ __forceinline__ void solve_chunk(const Shape& sh, int c0, int qk, const StencilSmem& sm) {
+__device__ __forceinline__ void solve_chunk(const SolveArgs& a, const Shape& sh, int c0, int qk,
+                                            const StencilSmem& sm, int j) {
     chunk_rhs<D, NT>(sh, c0, qk, sm);
     __syncthreads();
     forward_subst<NT>(sh.K, qk, sm);
     ldlt_solve_tail<NT>(sh.K, qk, sm);
+    if constexpr (team_refines(NT)) {
+        if (double* gA = refine_scratch<NT>(a))
+            refine_columns<D, NT>(a, sh, c0, qk, sm, gA, gA + a.rs_x0, 0, j);
+    }
     lebesgue_values<NT>(sh.n, sh.K, qk, sm, c0);
+}
+
+// Assemble, factor and solve the first q columns of stencil j (refined when its shape asks).
+template <int D, bool PACKED, int NT>
+__device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
+                            const StencilSmem& sm) {
+    assemble_local<D, PACKED, NT>(a, sh, j, q, sm);
+    if constexpr (!PACKED) {
+        return factor_solve_lu<NT>(sh.K, q, sm);
+    } else {
+        double* gA = refine_scratch<NT>(a);
+        if (gA) copy_full_matrix<NT>(sh.K, sm, gA);
+        if (!factor_solve_ldlt<NT, team_refines(NT)>(sh.K, q, sm)) return false;
+        if constexpr (team_refines(NT)) {
+            if (gA) refine_columns<D, NT>(a, sh, 0, q, sm, gA, gA + a.rs_x0, 0, j);
+        }
+        return true;
+    }
 }
 
 // Local L-Lebesgue value sum_r |w_r| of every solved column: warp w sums the columns w, w + NW,
@@ -727,7 +922,7 @@ __device__ __forceinline__ void solve_chunk(const Shape& sh, int c0, int qk, con
 // a stencil node (not a polynomial coefficient).
 template <int NT>
 __device__ __forceinline__ void lebesgue_values(int n, int K, int q, const StencilSmem& sm,
-                                                int off = 0) {
+                                                int off) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int c = wid; c < q; c += (NT / 32)) {
         double s = 0.0;
@@ -830,10 +1025,10 @@ __device__ int pick_spec(const SolveArgs& a) {
 
 // Reference point of the Lebesgue test in its centroid reading (§4.2.1): for every node j,
 // the position in its stencil (n_j nodes) of the node nearest the stencil's centroid; one warp
-// per node.  The centroid is (sum of the nodes) * (1/n_j) with each coordinate's sum in one
-// fixed order (lane l adds nodes l, l + 32, ... from 0.0, then a xor butterfly; IEEE addition
-// commutes, so every lane holds the same sum); ties go to the lower position.  It depends on
-// the stencil only, so it runs once per plan, before the traversal.
+// per node.  The centroid is the mean of the stencil's nodes: lane 0 sums each coordinate in
+// kNN order from 0.0 and divides by n_j (at most 128 additions per coordinate, once per plan),
+// then broadcasts it; ties in the distance go to the lower position.  It depends on the
+// stencil only, so it runs once per plan, before the traversal.
 template <int D>
 __global__ void k_centroid_ref(const double* X, const int* nbr, const int* node_n, int N, int ns,
                                unsigned char* ref_pos) {
@@ -842,14 +1037,15 @@ __global__ void k_centroid_ref(const double* X, const int* nbr, const int* node_
     if (j >= N) return;  // (warp-uniform)
     const int n = node_n ? node_n[j] : ns;
     const int* nb = nbr + (size_t)j * ns;
-    const double inv_n = __ddiv_rn(1.0, exact_double(n));
     double c[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
         double s = 0.0;
-        for (int t = lane; t < n; t += 32) s = __dadd_rn(s, __ldg(&X[(size_t)nb[t] * D + d]));
-        for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
-        c[d] = __dmul_rn(s, inv_n);
+        if (lane == 0) {
+            for (int t = 0; t < n; ++t) s = __dadd_rn(s, __ldg(&X[(size_t)nb[t] * D + d]));
+            s = __ddiv_rn(s, exact_double(n));
+        }
+        c[d] = __shfl_sync(0xffffffffu, s, 0);
     }
     unsigned long long best = ~0ull;  // this lane's smallest squared distance (bits; r2 >= 0)
     int tb = 0x7fffffff;              // and its lowest position
@@ -1042,7 +1238,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
                 const int qk = min(qc, q - c0);
                 __syncthreads();  // sm.X is read until here
                 // (the shape is read again rather than kept in registers)
-                if (ok) solve_chunk<D, NT>(shape_of<D>(a, sbasis, j), c0, qk, sm);
+                if (ok) solve_chunk<D, NT>(a, shape_of<D>(a, sbasis, j), c0, qk, sm, j);
                 __syncthreads();
                 emit(c0, qk);
             }
@@ -1081,6 +1277,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
             const unsigned long long K = (unsigned long long)sh.K;
             atomicAdd(&a.ctr->sum_k3, K * K * K);
             atomicAdd(&a.ctr->sum_k2q, K * K * (unsigned long long)s_own);
+            atomicAdd(&a.ctr->sum_k2c, K * K * (unsigned long long)q);
             atomicAdd(&a.ctr->n_centers, 1ull);
             atomicAdd(&a.ctr->sum_cols, (unsigned long long)q);
             atomicAdd(&a.ctr->n_rejected, (unsigned long long)s_rej);
@@ -1109,32 +1306,11 @@ __global__ void k_fallback_collect(SolveArgs a) {
     }
 }
 
-// Right-hand side of the normal derivative at the stencil center (the origin of the scaled
-// coordinates), replacing column 0 of the right-hand-side block: d/dn ||y - xi_j||^m at y = 0
-// is -m ||xi_j||^(m-2) (xi_j . n), and of the monomials only the linear ones have a nonzero
-// gradient there (d/dn xi_a = n_a).
+// Normal-derivative right-hand side of node i's own stencil, replacing column 0 of the
+// right-hand-side block (unknowns in index order, before the factorization).
 template <int D, int NT>
 __device__ void neumann_rhs(const SolveArgs& a, const Shape& sh, int i, const StencilSmem& sm) {
-    const double* nv = a.nrm + (size_t)i * D;
-    const double mm = exact_double(sh.m);
-    for (int j = threadIdx.x; j < sh.n + sh.M; j += NT) {
-        double v;
-        if (j < sh.n) {
-            const double* xj = sm.xi + j * D;
-            double r2 = xj[0] * xj[0], dot = xj[0] * nv[0];
-            for (int c = 1; c < D; ++c) {
-                r2 = fma(xj[c], xj[c], r2);
-                dot = fma(xj[c], nv[c], dot);
-            }
-            double pm2 = sqrt_fast(r2);  // r^(m-2), m odd
-            for (int t = 0; t < (sh.m - 3) / 2; ++t) pm2 *= r2;
-            v = -mm * pm2 * dot;
-        } else {
-            const int l = j - sh.n;
-            v = (l > 0 && sh.bs.parent[l] == 0) ? nv[sh.bs.var[l]] : 0.0;
-        }
-        sm.X[j * sm.xs] = v;
-    }
+    for (int j = threadIdx.x; j < sh.n + sh.M; j += NT) sm.X[j * sm.xs] = neumann_value<D>(a, sh, i, j, sm);
 }
 
 // FALLBACK re-solves (one right-hand side each), one launch per stencil class: `cls` is the
@@ -1171,7 +1347,15 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
             neumann_rhs<D, NT>(a, sh, i, sm);
             __syncthreads();
         }
-        const bool ok = PACKED ? factor_solve_ldlt<NT>(sh.K, 1, sm) : factor_solve_lu<NT>(sh.K, 1, sm);
+        bool ok;
+        if constexpr (PACKED) {
+            double* gA = refine_scratch<NT, true>(a);
+            if (gA) copy_full_matrix<NT>(sh.K, sm, gA);
+            ok = factor_solve_ldlt<NT, true>(sh.K, 1, sm);
+            if (ok && gA) refine_columns<D, NT>(a, sh, 0, 1, sm, gA, gA + a.rs_x0, kind, i);
+        } else {
+            ok = factor_solve_lu<NT>(sh.K, 1, sm);
+        }
         if (ok) lebesgue_values<NT>(sh.n, sh.K, 1, sm);
         __syncthreads();
         double r2c = a.rho2[i];
@@ -1189,6 +1373,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_fallback_solve(Solv
             const unsigned long long K = (unsigned long long)sh.K;
             atomicAdd(&a.ctr->sum_k3, K * K * K);
             atomicAdd(&a.ctr->sum_k2q, K * K);
+            atomicAdd(&a.ctr->sum_k2c, K * K);
             if (kind == 0) atomicAdd(&a.ctr->n_fallback, 1ull);
             atomicAdd(&a.ctr->sum_cols, 1ull);
         }
@@ -1412,16 +1597,18 @@ static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
 // 3D, K = 65, one column: 15.5 against 15.7 ms).  A
 // forced size (32, 64 and 96 exist for the LDL^T traversal only) is taken as given.
 template <int D, bool PACKED, bool TRAVERSAL>
-static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool chunked = false) {
+static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool chunked = false,
+                     bool refined = false) {
     auto occ = [&](int nt, int* ps) {
         return TRAVERSAL ? traversal_occupancy<D, PACKED>(nt, smem, chunked, ps)
                          : fallback_occupancy<D, PACKED>(nt, smem, ps);
     };
     int nt = force, rc;
+    if (refined && nt != 0 && !team_refines(nt)) return RBFFD_EINVAL;  // no refinement step there
     if (nt == 0) {
         int per_sm = 0;
         if ((rc = occ(kNT, &per_sm))) return rc;
-        nt = per_sm <= 4 ? kMaxNT : kNT;
+        nt = (per_sm <= 4 || refined) ? kMaxNT : kNT;
         if (TRAVERSAL && PACKED && nt == kNT) {
             int p96 = 0;
             if ((rc = occ(96, &p96))) return rc;
@@ -1444,7 +1631,8 @@ static int prepare(int n, int K, int qcap, int qmax, int basis_count, LaunchPlan
     const size_t smem = bb + solve_smem_per_cta(n, K, qcap, qmax, D, PACKED, &stride);
     int per_sm = 0, rc;
     lp->chunked = PACKED && qcap < qmax;
-    if ((rc = pick_team<D, PACKED, true>(smem, lp->force_nt, &lp->nt, &per_sm, lp->chunked)))
+    if ((rc = pick_team<D, PACKED, true>(smem, lp->force_nt, &lp->nt, &per_sm, lp->chunked,
+                                         PACKED && K >= lp->refine_min_K)))
         return rc;
     lp->grid = per_sm * sm_count();
     lp->smem = smem;
@@ -1530,10 +1718,13 @@ static int fallback(const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s, in
     const int basis_bytes = (int)basis_smem_bytes(a.basis_count);
     for (int c = 0; c < lp.n_fb; ++c) {
         const FallbackClass& f = lp.fb[c];
+        SolveArgs af = a;  // refinement scratch laid out for this class's systems
+        af.rs_stride = f.rs_stride;
+        af.rs_x0 = f.rs_x0;
         if (f.nt == kMaxNT)
-            k_fallback_solve<D, PACKED, kMaxNT><<<f.grid, kMaxNT, f.smem, s>>>(a, f.cls, f.n, f.K, f.xs, basis_bytes);
+            k_fallback_solve<D, PACKED, kMaxNT><<<f.grid, kMaxNT, f.smem, s>>>(af, f.cls, f.n, f.K, f.xs, basis_bytes);
         else
-            k_fallback_solve<D, PACKED, kNT><<<f.grid, kNT, f.smem, s>>>(a, f.cls, f.n, f.K, f.xs, basis_bytes);
+            k_fallback_solve<D, PACKED, kNT><<<f.grid, kNT, f.smem, s>>>(af, f.cls, f.n, f.K, f.xs, basis_bytes);
         ++*launches;
     }
     return RB_LAUNCHED(__func__);

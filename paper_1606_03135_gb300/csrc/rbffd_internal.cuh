@@ -68,7 +68,9 @@ struct DevCounters {
     unsigned long long n_spec_used;  // centers that found their solve already made
     int spec_next;                   // next node an idle CTA considers for speculation
     int pad_i;
-    unsigned long long pad[17];
+    unsigned long long sum_k2c;      // sum over factored stencils of K^2 (columns solved)
+    unsigned long long sum_k2r;      // sum over refined solves of K^2 (columns refined)
+    unsigned long long pad[15];
 };
 
 // Map a CUDA status to an RBFFD code; with RBFFD_DEBUG set in the environment the failing
@@ -149,6 +151,17 @@ struct SolveArgs {
     int no_seed;               // fault injection: push no initial center (waits run out)
     int factor;                // RBFFD_FACTOR_LDLT (packed layout) or RBFFD_FACTOR_LU (full)
     int max_ctas;              // cap on the persistent grid (0 = fill the GPU)
+    // One step of iterative refinement of ill-conditioned LDL^T local solves, in plans whose
+    // largest system has K >= refine_min_K: per-CTA scratch of rs_stride doubles at
+    // rs + blockIdx.x rs_stride holding the assembled matrix in full (K x K) and, from offset
+    // rs_x0, the first solution of a chunk of right-hand sides and the residual's partial sums
+    // (K x q each, 5 in all; rs == nullptr: the plan refines nothing).
+    double* rs;
+    long long rs_stride;
+    int rs_x0;
+    int refine_min_K;
+    int refine_all;            // 1: refine every system; 0: only those whose pivot ratio
+                               // max |d| / min |d| reaches 2^16 (ill-conditioned)
 
     unsigned long long timeout_ns;
     // traversal state
@@ -176,9 +189,12 @@ struct FallbackClass {
     int n, K, xs;   // largest stencil / system of the class, right-hand-side stride
     int nt, grid;
     size_t smem;
+    long long rs_stride;  // refinement scratch per CTA of this class's launch (doubles)
+    int rs_x0;
 };
 struct LaunchPlan {
-    int force_nt = 0;  // 0: choose; 128 or 512: forced team size of the traversal
+    int force_nt = 0;  // 0: choose; 32 .. 512: forced team size of the traversal
+    int refine_min_K = 0x7fffffff;  // systems this large are refined (their teams carry the step)
     int nt = 128, grid = 0;
     bool chunked = false;  // some balls have more columns than one factorization carries
     size_t smem = 0;

@@ -19,13 +19,15 @@ OK, EINVAL, EDUPLICATE, ENOMEM, ESINGULAR, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, 
 STAB_SEQ, STAB_OFF, STAB_FALLBACK = 0, 1, 2
 FACTOR_LDLT, FACTOR_LU = 0, 1
 LREF_CENTER, LREF_CENTROID = 0, 1  # reference point of the Lebesgue test (rbffd_opts.lebesgue_ref)
+REFINE_AUTO, REFINE_ALL, REFINE_NONE = 0, 1, 2  # iterative refinement (rbffd_opts.refine)
+REFINE_MIN_K = 100  # RBFFD_REFINE_MIN_K: systems at least this large are refined by default
 
 
 class rbffd_opts(C.Structure):
     _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
                 ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int),
                 ("max_ctas", C.c_int), ("team", C.c_int), ("rhs_chunk", C.c_int),
-                ("lebesgue_ref", C.c_int)]
+                ("lebesgue_ref", C.c_int), ("refine", C.c_int)]
 
 
 class rbffd_csr(C.Structure):
@@ -43,7 +45,8 @@ class rbffd_stats_t(C.Structure):
                 ("ms_finalize", C.c_float), ("nnz", C.c_int64), ("plan_bytes", C.c_int64),
                 ("assemble_bytes", C.c_int64), ("n_boundary", C.c_int64),
                 ("n_speculated", C.c_int64), ("n_spec_used", C.c_int64),
-                ("rhs_chunk", C.c_int64)]
+                ("rhs_chunk", C.c_int64), ("sum_k3", C.c_double), ("sum_k2_cols", C.c_double),
+                ("flops_refine", C.c_double), ("refine_min_K", C.c_int32), ("pad0", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -190,7 +193,7 @@ class Plan:
 
     def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
                  stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0, team=0,
-                 rhs_chunk=0, lebesgue_ref=0):
+                 rhs_chunk=0, lebesgue_ref=0, refine=REFINE_AUTO):
         self._plan = None
         self._stream = stream
         if isinstance(nodes, np.ndarray):
@@ -206,7 +209,7 @@ class Plan:
         self.ell, self.m, self.delta, self.mode = ell, m, delta, mode
         self.sync = bool(sync)
         opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor,
-                          max_ctas, team, rhs_chunk, lebesgue_ref)
+                          max_ctas, team, rhs_chunk, lebesgue_ref, refine)
         if np.ndim(n) == 0:  # one stencil size, degree and exponent for every node
             self.n = int(n)
             rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,

@@ -53,17 +53,27 @@ class Result:
         return self.t_done - self.t_arrival
 
 
-def estimate_bytes(N: int, d: int, n: int, delta: float) -> int:
-    """Device bytes a job needs (plan + traversal + CSR), with the retention-ball sizes
-    bounded by the stencil size; the exact figure is known after the plan."""
+def estimate_bytes(N: int, d: int, n: int, delta: float, ell: int = None) -> int:
+    """Upper bound of the device bytes a uniform-stencil job holds at once: the plan's stencil
+    arrays, the cell-grid scratch of its kNN step, and the traversal and CSR arrays of its
+    assembly, with every retention ball bounded by the stencil size (one node at delta = 1),
+    plus 1 MB for alignment and small tables.  Plans of K = n + C(ell + d, d) >= 100 unknowns
+    refine ill-conditioned solves by default, and their assembly then keeps, per resident CTA,
+    the full K x K system, its first solutions and the residual's partial sums: at most 5 times
+    the CTA's shared-memory system, so under 200 MB on a 152-SM GB300 (228 KB of shared memory
+    per SM); without `ell` that is assumed.  The exact figure is known after the plan (rbffd_stats: plan_bytes
+    + assemble_bytes) and never exceeds this."""
     ball = 1 if delta >= 1.0 else n
     plan = N * (d * 8 + n * 4 + 8 + 4 + 4 + 8) + (2 * N + 64) * 12 + N * (8 + 8 * d)
     asm = N * (4 * 6 + 2 + n * 12 + 16) + N * ball * (n * 8 + 9)
-    return int(plan + asm + (1 << 20))
+    refined = ell is None or n + math.comb(ell + d, d) >= 100
+    return int(plan + asm + (1 << 20) + ((200 << 20) if refined else 0))
 
 
 class Budget:
-    """Admission control: slots and device bytes, FIFO."""
+    """Admission control: slots and device bytes, FIFO.  A reservation is taken before a job
+    allocates anything, so the budget holds at allocation time; nothing waits while it holds
+    a slot (a reservation that would have to grow beyond the budget fails the job)."""
 
     def __init__(self, slots: int, budget_bytes: int):
         self.slots = slots
@@ -74,20 +84,25 @@ class Budget:
         self.cv = threading.Condition()
 
     def admit(self, need: int):
+        """Wait for a free slot and `need` bytes (jobs that can never fit raise MemoryError)."""
+        if need > self.budget:
+            raise MemoryError(f"job needs {need} bytes > budget {self.budget}")
         with self.cv:
             while self.free_slots == 0 or self.in_use + need > self.budget:
-                if need > self.budget:
-                    raise MemoryError(f"job needs {need} bytes > budget {self.budget}")
                 self.cv.wait()
             self.free_slots -= 1
             self.in_use += need
             self.peak = max(self.peak, self.in_use)
 
     def resize(self, old: int, new: int):
-        """Correct a reservation once the exact size is known (waits if it grew)."""
+        """Correct a held reservation once the exact size is known.  Shrinking always works;
+        growing never waits (the job holds a slot, and two growing jobs could wait on each
+        other): it succeeds if the budget has room now, else raises MemoryError and the
+        reservation stays `old`."""
         with self.cv:
-            while new > old and self.in_use - old + new > self.budget:
-                self.cv.wait()
+            if new > old and self.in_use - old + new > self.budget:
+                raise MemoryError(f"exact size {new} bytes does not fit the budget "
+                                  f"({self.in_use - old} of {self.budget} in use by others)")
             self.in_use += new - old
             self.peak = max(self.peak, self.in_use)
             self.cv.notify_all()
@@ -119,21 +134,24 @@ class Server:
 
     def _run_one(self, job: Job, stream, t0: float, res: Result, reserved: int):
         R = self.R
+        p = None
         try:
             with self.torch.cuda.stream(stream):
                 p = R.Plan(job.nodes, job.n, job.ell, job.m, job.delta, mode=job.mode,
                            stream=stream, max_ctas=self.max_ctas)
                 st = p.stats()
                 exact = st["plan_bytes"] + st["assemble_bytes"]
-                self.budget.resize(reserved, exact)
+                self.budget.resize(reserved, exact)  # (raises rather than wait)
                 reserved = exact
                 p.assemble()
                 if self.keep:
                     res.row_ptr, res.col, res.val, res.owner = p.export()
                 res.stats = p.stats()
-                p.close()
         except Exception as e:  # a failed job is reported, never the process
             res.error = f"{type(e).__name__}: {e}"
+        finally:
+            if p is not None:
+                p.close()
         res.t_done = time.perf_counter() - t0
         return reserved
 
@@ -160,13 +178,18 @@ class Server:
             if job.arrival > now:
                 time.sleep(job.arrival - now)
             N, d = job.nodes.shape
-            need = estimate_bytes(N, d, job.n, job.delta)
-            need = min(need, self.budget.budget)
-            self.budget.admit(need)  # blocks until a slot and the memory are free
+            need = estimate_bytes(N, d, job.n, job.delta, ell=job.ell)
+            res = Result(job.rid, N, job.arrival, 0.0, 0.0)
+            results[job.rid] = res
+            try:
+                self.budget.admit(need)  # blocks until a slot and the memory are free
+            except MemoryError as e:  # can never fit: reported, the trace goes on
+                res.t_admit = res.t_done = time.perf_counter() - t0
+                res.error = f"MemoryError: {e}"
+                continue
+            res.t_admit = time.perf_counter() - t0
             with free_lock:
                 slot = free.pop()
-            res = Result(job.rid, N, job.arrival, time.perf_counter() - t0, 0.0)
-            results[job.rid] = res
             th = threading.Thread(target=worker, args=(job, slot, need, res), daemon=True)
             th.start()
             threads.append(th)

@@ -5,6 +5,7 @@ structure bit-exact; weights within 1e-9 of the row's largest weight (the tolera
 method's specification states); Lebesgue values within 1e-9 relative.  Structural parity is
 asserted where the oracle saw no Lebesgue decision within 1e-9 of a tie.
 """
+import math
 import time
 
 import numpy as np
@@ -353,34 +354,75 @@ def gpu_run_mixed(X, n_node, ell_node, m_node, delta, mode=R.STAB_SEQ, **kw):
                 ball_len=bl, lam_row=lam, is_center=isc, stats=st)
 
 
-def check_mixed_rows(X, g, ref, n_node, ell_node, m_node):
-    """Weights of the mixed-degree workload against the mixed oracle."""
-    # Degree-5 stencils here (K = 169 on clustered nodes) have condition numbers near 5e10:
-    # two correct FP64 solvers (the oracle's LU, LAPACK) already differ by up to ~2e-7 on
-    # them, and the symmetric Bunch-Kaufman factorization the GPU uses is a few times less
-    # accurate than partial-pivot LU there.  Rows must match to 1e-9, except where the
-    # stencil's rounding error allows more: then the GPU must stay within 1e-6, and on the
-    # worst rows, against a 30-digit solve, within 10x the oracle's own error.
-    from tests.hp_reference import mp_weights
-    errs = []
-    for i in range(X.shape[0]):
-        sl = slice(ref["row_ptr"][i], ref["row_ptr"][i + 1])
-        a, b = g["val"][sl], ref["val"][sl]
-        errs.append(np.abs(a - b).max() / np.abs(b).max())
-    errs = np.array(errs)
-    assert np.mean(errs > TOL) <= 0.2 and errs.max() <= 1e-6
-    for i in np.argsort(errs)[::-1][:2]:
-        if errs[i] <= TOL:
-            break
-        o = ref["owner"][i]
-        idx = ref["nbr"][o, :n_node[o]]
-        w = mp_weights(X, idx, int(ell_node[o]), int(m_node[o]), X[i:i + 1], dps=30)[:, 0]
+def forward_errors(X, g, ref, n_node, ell_node, m_node, rows, rho2):
+    """Forward errors of the GPU's and the oracle's rows (and scaled Lebesgue values) against
+    a double-double solve of each row's stencil (tests/hp_reference.py), relative to the row's
+    largest exact weight.  Rows sharing a stencil share its factorization."""
+    from tests.hp_reference import dd_weights
+    src = np.where(ref["is_center"] >= 2, np.arange(X.shape[0]), ref["owner"])
+    out = {}
+    for s_ in np.unique(src[rows]):
+        rs = [i for i in rows if src[i] == s_]
+        idx = ref["nbr"][s_, :n_node[s_]]
+        W = dd_weights(X, idx, int(ell_node[s_]), int(m_node[s_]), X[rs])
         order = np.argsort(idx)
-        sl = slice(ref["row_ptr"][i], ref["row_ptr"][i + 1])
-        scale = np.abs(w).max()
-        e_gpu = np.abs(g["val"][sl] - w[order]).max() / scale
-        e_ora = np.abs(ref["val"][sl] - w[order]).max() / scale
-        assert e_gpu <= max(TOL, 10 * e_ora), (i, e_gpu, e_ora)
+        for k, i in enumerate(rs):
+            sl = slice(ref["row_ptr"][i], ref["row_ptr"][i + 1])
+            w = W[order, k]
+            sc = np.abs(w).max()
+            lam = np.abs(w).sum() * rho2[s_]  # the scaled local Lebesgue value of the row
+            lg = abs(g["lam_row"][i] - lam) / lam if "lam_row" in g else 0.0
+            out[i] = (np.abs(g["val"][sl] - w).max() / sc, np.abs(ref["val"][sl] - w).max() / sc,
+                      lg, abs(ref["lam_row"][i] - lam) / lam)
+    return out
+
+
+def check_mixed_rows(X, g, ref, n_node, ell_node, m_node, per_class=25, seed=99, max_bad=None,
+                     min_rows=100):
+    """Weights of per-node (or ill-conditioned uniform) stencils against the oracle.
+
+    Rows within 1e-9 of the oracle pass as they are.  The degree-4 and degree-5 stencils of
+    the clustered cube (K = 106 and 169) reach condition numbers near 3e10, where any FP64
+    solver is up to ~3e-7 from the exact weights (the oracle's LU, LAPACK and the library
+    alike), so 1e-9 between two FP64 solvers is not attainable there.  Every row above 1e-9
+    (with max_bad: that many, the worst first), and a stratified sample of `per_class` rows of
+    every degree, is measured against a double-double (~32-digit) solve of its stencil, and
+    the GPU's forward errors must meet the bar of tests/hp_reference.accuracy_failures against
+    the oracle's (which LAPACK meets too), for the weights and for the Lebesgue values (when g
+    has them).  Returns the per-degree summary of the sampled forward errors."""
+    from tests.hp_reference import accuracy_failures
+    N = X.shape[0]
+    rp = ref["row_ptr"]
+    errs = np.array([np.abs(g["val"][rp[i]:rp[i + 1]] - ref["val"][rp[i]:rp[i + 1]]).max() /
+                     np.abs(ref["val"][rp[i]:rp[i + 1]]).max() for i in range(N)])
+    src = np.where(ref["is_center"] >= 2, np.arange(N), ref["owner"])
+    cls = ell_node[src]
+    perm = NS.permutation(seed, N)
+    bad = np.nonzero(errs > TOL)[0]
+    if max_bad is not None:
+        bad = bad[np.argsort(errs[bad])[::-1][:max_bad]]
+    rows = set(bad.tolist())
+    for c in np.unique(cls):
+        rows.update([int(i) for i in perm if cls[i] == c][:per_class])
+    rows = sorted(rows)
+    rho2 = ref["d2"][np.arange(N), n_node - 1]
+    fe = forward_errors(X, g, ref, n_node, ell_node, m_node, rows, rho2)
+    v = np.array([fe[i] for i in rows])
+    c_rows = cls[rows]
+    fails = accuracy_failures(v[:, 0], v[:, 1], c_rows)
+    if "lam_row" in g:
+        fails += ["Lebesgue " + f for f in accuracy_failures(v[:, 2], v[:, 3], c_rows, v[:, 0])]
+    summary = {}
+    for c in np.unique(cls):
+        w = v[c_rows == c]
+        summary[int(c)] = dict(rows=int(w.shape[0]), above_1e9=int((errs[cls == c] > TOL).sum()),
+                               gpu_max=float(w[:, 0].max()), gpu_median=float(np.median(w[:, 0])),
+                               oracle_max=float(w[:, 1].max()),
+                               oracle_median=float(np.median(w[:, 1])))
+    print("forward errors per degree:", summary)
+    assert not fails, fails[:10]
+    assert len(rows) >= min_rows
+    return summary
 
 
 @pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
@@ -396,10 +438,41 @@ def test_mixed_degrees_3d_match_the_mixed_oracle(mode):
     assert np.array_equal(g["row_ptr"], ref["row_ptr"])
     assert np.array_equal(g["col"], ref["col"])
     check_mixed_rows(X, g, ref, n_node, ell_node, m_node)
-    lam_err = np.abs(g["lam_row"] - ref["lam_row"]) / ref["lam_row"]
-    assert np.quantile(lam_err, 0.8) <= TOL and lam_err.max() <= 1e-5
     assert g["stats"]["n_fallback"] == ref["stats"]["n_fallback"]
     assert g["stats"]["nnz"] == ref["row_ptr"][-1]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
+def test_mixed_degrees_3d_N20000_match_the_mixed_oracle(mode):
+    """The same at N = 20,000 (the clustered cube's recipe, degree 2..5 by x-slab)."""
+    X = NS.cube3d_clustered(20000, seed=4)
+    n_node, ell_node, m_node = NS.mixed_degree_params(X)
+    g = gpu_run_mixed(X, n_node, ell_node, m_node, 0.3, mode)
+    ref = O.assemble_mixed(X, n_node, ell_node, m_node, 0.3, mode)
+    assert ref["stats"]["n_near_tie"] == 0
+    for key in ("nbr", "owner", "is_center", "row_ptr", "col"):
+        assert np.array_equal(g[key], ref[key]), key
+    check_mixed_rows(X, g, ref, n_node, ell_node, m_node)
+    assert g["stats"]["n_fallback"] == ref["stats"]["n_fallback"]
+    assert g["stats"]["refine_min_K"] == R.REFINE_MIN_K
+
+
+def test_refinement_options_on_per_node_stencils():
+    """Refinement changes weights only (rounding), never the structure: with every system
+    refined, only the ill-conditioned ones (the default) or none, the matrices share their
+    structure; the default refines a part of what refining everything does."""
+    X = NS.cube3d_clustered(3000, seed=4)
+    params = NS.mixed_degree_params(X)
+    runs = {r: gpu_run_mixed(X, *params, 0.3, refine=r)
+            for r in (R.REFINE_AUTO, R.REFINE_ALL, R.REFINE_NONE)}
+    for r, g in runs.items():
+        for key in ("owner", "is_center", "row_ptr", "col"):
+            assert np.array_equal(g[key], runs[R.REFINE_AUTO][key]), (r, key)
+        assert g["stats"]["refine_min_K"] == {R.REFINE_NONE: 0x7fffffff, R.REFINE_ALL: 0,
+                                              R.REFINE_AUTO: R.REFINE_MIN_K}[r]
+    fr = {r: g["stats"]["flops_refine"] for r, g in runs.items()}
+    assert fr[R.REFINE_NONE] == 0 < fr[R.REFINE_AUTO] < fr[R.REFINE_ALL]
 
 
 def test_mixed_entry_with_uniform_parameters_equals_the_uniform_plan():
@@ -521,3 +594,26 @@ def test_centroid_reference_at_the_largest_stencil_size():
     X = NS.jittered_grid(40, 2, seed=21)
     ref = O.assemble(X, 128, 2, 3, 0.5, lref=O.LREF_CENTROID)
     compare(X, 128, 2, 3, 0.5, ref=ref, lebesgue_ref=R.LREF_CENTROID)
+
+
+@pytest.mark.parametrize("team,chunk", [(32, 0), (64, 3), (512, 0), (512, 2)])
+def test_refined_schedules_are_bitwise_equal(team, chunk):
+    """The refinement step does the same arithmetic on every entry whatever the team size or
+    chunk (a warp per column or per residual entry), so refined results agree bit for bit."""
+    X = NS.cube3d_clustered(3000, seed=4)
+    params = NS.mixed_degree_params(X)
+    a = gpu_run_mixed(X, *params, 0.3)
+    b = gpu_run_mixed(X, *params, 0.3, team=team, rhs_chunk=chunk)
+    for key in ("row_ptr", "col", "val", "owner", "is_center", "lam_row"):
+        assert np.array_equal(a[key], b[key]), key
+
+
+def test_teams_without_the_refinement_step_are_refused_for_refined_systems():
+    X = torch.from_numpy(NS.cube3d_clustered(3000, seed=4)).cuda()
+    params = NS.mixed_degree_params(X.cpu().numpy())
+    for team in (96, 128):
+        with pytest.raises(R.RbffdError) as e:
+            R.Plan(X, *params, 0.3, team=team)
+        assert e.value.code == R.EINVAL
+        with R.Plan(X, *params, 0.3, team=team, refine=R.REFINE_NONE) as p:
+            p.assemble()

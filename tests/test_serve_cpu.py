@@ -36,29 +36,38 @@ def test_budget_never_exceeds_slots_or_bytes():
     assert b.in_use == 0 and b.free_slots == 3
 
 
-def test_budget_resize_waits_for_room():
+def test_budget_resize_shrinks_and_grows_only_into_free_room():
     b = S.Budget(slots=2, budget_bytes=100)
     b.admit(60)
     b.admit(30)
-    done = []
+    b.resize(30, 20)  # the exact size is smaller: room is handed back at once
+    assert b.in_use == 80
+    b.resize(20, 40)  # grows into free room without waiting
+    assert b.in_use == 100 and b.peak == 100
 
-    def grow():
-        b.resize(30, 50)  # needs 60 + 50 > 100 until the first job leaves
-        done.append(time.perf_counter())
 
-    t = threading.Thread(target=grow)
-    t.start()
-    time.sleep(0.05)
-    assert not done
-    b.release(60)
-    t.join(5)
-    assert done and b.in_use == 50
+def test_budget_resize_never_waits_while_holding_a_slot():
+    # two running jobs that both need to grow beyond the budget: each fails at once (the job
+    # is reported as failed) instead of waiting for the other
+    b = S.Budget(slots=2, budget_bytes=100)
+    b.admit(50)
+    b.admit(40)
+    t0 = time.perf_counter()
+    for old, new in ((50, 70), (40, 60)):
+        with pytest.raises(MemoryError):
+            b.resize(old, new)
+    assert time.perf_counter() - t0 < 1.0
+    assert b.in_use == 90  # the failed resizes left the reservations as they were
+    b.release(50)
+    b.release(40)
+    assert b.in_use == 0 and b.free_slots == 2
 
 
 def test_oversized_job_is_refused():
     b = S.Budget(slots=1, budget_bytes=10)
     with pytest.raises(MemoryError):
         b.admit(11)
+    assert b.free_slots == 1 and b.in_use == 0
 
 
 def test_serving_mix_follows_its_recipe():
