@@ -1,16 +1,21 @@
 """Benchmark: forming the sparse FP64 Laplacian differentiation matrix with overlapped RBF-FD.
 
-One step = the delta sweep of the 2D workload: for each delta in (1.0, 0.5, 0.3), plan the
-stencils (kNN, retention balls) and assemble L (traversal with Lebesgue stabilization, one
-factorization per center, multi-RHS solves, CSR) for N = 40,000 jittered nodes in the unit
-square, PHS r^7, degree-4 polynomials (M = 15), n = 31.  Metric: matrix rows per second.
+The headline step is the delta sweep of the largest sweep workload: for each delta in
+(1.0, 0.4, 0.2), plan the stencils (kNN, retention balls) and assemble L (traversal with
+Lebesgue stabilization, one factorization per center, multi-RHS solves, CSR) for N = 100,000
+quasi-uniform nodes in the unit ball, PHS r^7, degree-3 polynomials (M = 20), n = 45.
+Metric: matrix rows per second.  The same JSON line carries, under "configs", the 2D square
+sweep (N = 40,000), the clustered mixed-degree cube (N = 500,000, eager and replayed from a
+captured CUDA graph) and the serving trace (256 jobs: 1 slot against 4 slots on the same
+arrival traces), each with its own roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--headline-only] [--workload NAME | serve]
 
-Under torchrun (N > 1) every rank forms its own copy of the workload (independent replicas:
-the method has no exchange step on this path) and rank 0 prints one JSON line with the
-aggregate rows/s over the max-over-ranks time.  ``--impl reference`` times the CPU oracle
-(the plain sequential restatement of the method) instead, one delta of the sweep per step.
+Under torchrun (N > 1) every rank forms its own copy of the headline workload (independent
+replicas: the method has no exchange step on this path) and rank 0 prints one JSON line with
+the aggregate rows/s over the max-over-ranks time.  ``--impl reference`` times the CPU oracle
+(the plain sequential restatement of the method) on bounded samples instead.
 """
 from __future__ import annotations
 
@@ -19,6 +24,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -29,11 +35,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "square2d_N40000_l4_n31_r7"
+WORKLOAD = "ball3d_N100000_l3_n45_r7"      # headline: the largest delta-sweep workload
+SWEEP_2D = "square2d_N40000_l4_n31_r7"
+MIXED = "cube3d_N500000_mixed_l2to5"
 METRIC = "diff-matrix rows/s (FP64, delta sweep)"
 UNIT = "rows/s"
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no FP64 entry in the measured peaks)
+# The FP64 pipe of a GB300: 152 SMs x 2 DFMA per clock x 2 flops x 2.07 GHz = 1.259 TFLOP/s;
+# the profiling recipe's nominal figure is 1.25 (the measured peaks file has no FP64 entry).
+FP64_PEAK_TFLOPS = 1.25
+PEAK_DERIVATION = ("nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.259 "
+                   "TFLOP/s, quoted as 1.25 (profiling recipe); MEASURED_PEAKS.json has no "
+                   "FP64 entry")
 L2_FLUSH_BYTES = 256 << 20
+# bounded oracle sample for the CPU baseline and the reference arm: the headline's recipe and
+# stencil parameters at a fifth of its size (the oracle's brute-force kNN is quadratic in N)
+ORACLE_SAMPLE_N = 20000
 
 
 def _env_rank():
@@ -115,15 +131,15 @@ def kernel_source_hash(path):
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
-def _traffic_entry():
-    """DRAM traffic of the traversal kernel from the committed ncu summary, if the kernel
-    source is unchanged since it was captured."""
+def _traffic_entry(workload):
+    """DRAM traffic of the traversal kernel on `workload` from the committed ncu summary, if
+    the kernel source is unchanged since it was captured."""
     path = os.path.join(ROOT, "profiles", "traversal_traffic.json")
     src = os.path.join(ROOT, "paper_1606_03135_gb300", "csrc", "assemble.cu")
     try:
         rec = json.load(open(path))
         h = kernel_source_hash(src)
-        if rec.get("assemble_cu_code_sha256_16") == h:
+        if rec.get("assemble_cu_code_sha256_16") == h and rec.get("workload") == workload:
             return rec
     except (OSError, ValueError):
         pass
@@ -141,13 +157,62 @@ def max_over_ranks(x: float, device="cpu") -> float:
     return float(t.item())
 
 
-def cpu_oracle_step(X, w, delta, bcw=None):
-    """The oracle as it stands, on this host's cores: kNN + traversal + solves + CSR."""
+def host_cpu():
+    """(threads available to this process, CPU model) of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    return cores, model or platform.processor() or platform.machine()
+
+
+def _oracle_sample(seed):
+    return __import__("paper_1606_03135_gb300.nodesets", fromlist=["ball3d"]).ball3d(
+        ORACLE_SAMPLE_N, seed=seed)
+
+
+def oracle_sweep(seed):
+    """The oracle as it stands on one host core: the headline's delta sweep (kNN + traversal
+    + solves + CSR per delta) on a bounded sample of its recipe.  Returns (rows, seconds)."""
     from oracle import oracle as O
+    from paper_1606_03135_gb300 import nodesets as NS
+    w = NS.WORKLOADS[WORKLOAD]
+    X = _oracle_sample(seed)
     t = time.perf_counter()
-    bc, nrm = bcw if bcw is not None else (None, None)
-    O.assemble(X, w["n"], w["ell"], w["m"], delta, O.STAB_SEQ, bc=bc, normals=nrm)
-    return time.perf_counter() - t
+    for delta in w["deltas"]:
+        O.assemble(X, w["n"], w["ell"], w["m"], delta, O.STAB_SEQ)
+    return X.shape[0] * len(w["deltas"]), time.perf_counter() - t
+
+
+def cpu_baseline_entry():
+    """The oracle timed on this host: one core, then every core of the process at once (one
+    independent sample per core, a spawn pool, so no state of the GPU process is inherited)."""
+    from oracle import oracle as O
+    O.build()
+    cores, model = host_cpu()
+    rows1, t1 = oracle_sweep(3)
+    import multiprocessing
+    with multiprocessing.get_context("spawn").Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(oracle_sweep, [3 + k for k in range(cores)])
+        wall = time.perf_counter() - t0
+    rows_all = sum(r for r, _ in res)
+    sample = (f"the headline's delta sweep (1.0, 0.4, 0.2; n=45, ell=3, r^7) on the unit-ball "
+              f"recipe at N={ORACLE_SAMPLE_N} instead of 100,000 (brute-force kNN is quadratic "
+              f"in N): one sweep on 1 core in {t1:.1f} s; {cores} sweeps with their own seeds "
+              f"on {cores} cores at once in {wall:.1f} s")
+    return {"value": rows_all / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample, "single_core_value": rows1 / t1, "cpu_model": model,
+            "nproc": os.cpu_count()}
 
 
 def run_reference(args):
@@ -155,44 +220,70 @@ def run_reference(args):
     if rank != 0:
         return 0
     from oracle import oracle as O
+    from paper_1606_03135_gb300 import nodesets as NS
     O.build()
-    X, w, _ = _workload()
+    w = NS.WORKLOADS[WORKLOAD]
+    X = _oracle_sample(3)
     deltas = w["deltas"]
-    for s in range(args.warmup):
-        cpu_oracle_step(X, w, deltas[s % len(deltas)])
-    times = []
-    for s in range(args.steps):
-        times.append(cpu_oracle_step(X, w, deltas[s % len(deltas)]))
+
+    def step(k):
+        t = time.perf_counter()
+        O.assemble(X, w["n"], w["ell"], w["m"], deltas[k % len(deltas)], O.STAB_SEQ)
+        return time.perf_counter() - t
+
+    for k in range(args.warmup):
+        step(k)
+    times = [step(k) for k in range(args.steps)]
     total = sum(times)
-    rows = X.shape[0] * args.steps
-    value = rows / total
+    value = X.shape[0] * args.steps / total
+    cores, model = host_cpu()
+    sample = (f"one delta of the sweep per step (1.0, 0.4, 0.2 in turn), the unit-ball recipe at "
+              f"N={ORACLE_SAMPLE_N} (n=45, ell=3, r^7; the workload has N=100,000), "
+              f"single-threaded plain C oracle (brute-force kNN)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": X.shape[0], "d": 2, "n": w["n"], "ell": w["ell"],
-                   "m": w["m"], "deltas": list(deltas), "stab": "seq"},
+        "config": {"workload": WORKLOAD, "N": ORACLE_SAMPLE_N, "d": 3, "n": w["n"],
+                   "ell": w["ell"], "m": w["m"], "deltas": list(deltas), "stab": "seq"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "one delta of the sweep per step, full N=40000 node set, "
-                                   "single-threaded plain C oracle (brute-force kNN)"},
+                         "sample": sample, "cpu_model": model, "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_gpu(args):
+def roofline_entry(stats, kernel_ms, kernel, share=None, traffic=None, factor_lu=False):
+    """FP64 roofline of the local-solve kernels over the launches in `stats` (rbffd_stats
+    dicts) taking `kernel_ms` of device time (CUDA events on the launching stream).
+    flops_executed: (1/3) K^3 per LDL^T factorization ((2/3) K^3 for LU) + 2 K^2 per solved
+    column (every retained node, kept or rejected); flops_survey: the cost model's
+    (2/3) K^3 + 2 K^2 p.  The refinement step's work is reported beside, not counted."""
+    k3 = sum(s["sum_k3"] for s in stats)
+    k2c = sum(s["sum_k2_cols"] for s in stats)
+    executed = (2.0 / 3.0 if factor_lu else 1.0 / 3.0) * k3 + 2.0 * k2c
+    survey = 2.0 / 3.0 * k3 + 2.0 * k2c
+    sec = kernel_ms / 1e3
+    achieved = executed / sec / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "flops_executed": executed, "flops_survey": survey,
+            "frac_survey": survey / sec / 1e12 / FP64_PEAK_TFLOPS,
+            "flops_refine": sum(s["flops_refine"] for s in stats),
+            "peak_source": PEAK_DERIVATION, "traffic": traffic, "share_of_step": share,
+            "kernel_ms": kernel_ms}
+
+
+def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
+    """One delta sweep workload: autotuned schedules, `steps` timed steps (L2 flushed
+    between them), the end-to-end form with host buffers.  Returns the JSON fields."""
     import torch
-    rank, world, local = _env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     from paper_1606_03135_gb300 import rbffd as R
-    R.load()
-    X, w, bcw = _workload(args.workload)
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    X, w, bcw = _workload(name)
     N, n, ell, m, deltas = X.shape[0], w["n"], w["ell"], w["m"], w["deltas"]
     d = X.shape[1]
     Xd = torch.from_numpy(X).to(dev)
@@ -218,9 +309,8 @@ def run_gpu(args):
         # for its sizing covers only its own stencils; the assemblies run in order on the
         # compute stream.
         launches = 0
-        alg = trav_ms = 0.0
         d2h = 0
-        plans = []
+        plans, sts = [], []
         plan_stream.wait_stream(stream)  # (after the step's start event)
         for delta in deltas:
             p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta, sync=False,
@@ -240,14 +330,13 @@ def run_gpu(args):
             if st["status"] != 0:
                 raise RuntimeError(f"delta {delta}: {R.rbffd_strerror(st['status'])}")
             launches += st["n_launches"]
-            alg += st["alg_flops"]
-            trav_ms += st["ms_traversal"]
+            sts.append(st)
             if detail is not None:
                 detail.setdefault(delta, []).append(st)
             p.close()
-        return launches, alg, trav_ms, d2h
+        return launches, sts, d2h
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
 
@@ -258,62 +347,63 @@ def run_gpu(args):
         torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     detail = {}
     launches = 0
-    alg = trav_ms = 0.0
+    all_st = []
     barrier()
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for s in range(args.steps):
-            flush.fill_(float(s))  # evict L2 between timed steps (not inside a step's events)
-            ev[s][0].record(stream)
-            l, a, t, _ = one_step(detail)
-            ev[s][1].record(stream)
+        for k in range(steps):
+            flush.fill_(float(k))  # evict L2 between timed steps (not inside a step's events)
+            ev[k][0].record(stream)
+            l, sts, _ = one_step(detail)
+            ev[k][1].record(stream)
             launches += l
-            alg += a
-            trav_ms += t
+            all_st += sts
         barrier()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_ms = max_over_ranks(sum(step_ms), dev)
-    rows = N * len(deltas) * args.steps * world
+    rows = N * len(deltas) * steps * world
     value = rows / (total_ms / 1e3)
 
-    # end to end through the public API with host buffers: host nodes in, host CSR out, both
-    # in pinned memory allocated once (as a caller that streams many node sets would)
-    e2e_steps = max(1, min(args.steps, 5))
-    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
-    X_pinned = pin(X.shape, torch.float64)
-    X_pinned[...] = X
-    bufs = {delta: (pin(N + 1, torch.int64), pin(N * n, torch.int32), pin(N * n, torch.float64),
-                    pin(N, torch.int32)) for delta in deltas}
-    one_step(nodes=X_pinned, host_out=bufs)  # warm-up of the host path
-    barrier()
-    t0 = time.perf_counter()
-    d2h = 0
-    for _ in range(e2e_steps):
-        _, _, _, d2h = one_step(nodes=X_pinned, host_out=bufs)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
-    e2e_value = N * len(deltas) * e2e_steps * world / e2e_s
+    out = {"value": value, "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
+           "config": {"workload": name, "N": N, "d": d, "n": n, "ell": ell, "m": m,
+                      "deltas": list(deltas), "stab": "seq",
+                      **({"boundary": f"{int((bcw[0] > 0).sum())} boundary rows (kind "
+                                      f"{int(bcw[0].max())}) + time-stepping matrix c="
+                                      f"{w['timestep_c']:.3g}"} if bcw is not None else {}),
+                      "l2": "flushed between timed steps (256 MB write)",
+                      "plans": "built on a side stream beside the previous delta's assembly "
+                               "(per_delta ms_stencils of later deltas include that overlap)",
+                      "schedule": ({str(k): v for k, v in sched.items()}
+                                   if not args.no_autotune else "library default")},
+           "gpu_launches": launches, "clocks": clk.summary()}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import oracle as O
-        O.build()
-        t_cpu = cpu_oracle_step(X, w, deltas[1], bcw)
-        cpu = {"value": N / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one full assembly at delta={deltas[1]} (N={N}, kNN + traversal + "
-                         f"solves + CSR), single-threaded plain C oracle, {t_cpu:.1f} s"}
+    if e2e:  # end to end through the public API with host buffers: host nodes in, host CSR
+        # out, both in pinned memory allocated once (as a caller that streams node sets would)
+        e2e_steps = max(1, min(steps, 5))
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+        X_pinned = pin(X.shape, torch.float64)
+        X_pinned[...] = X
+        bufs = {delta: (pin(N + 1, torch.int64), pin(N * n, torch.int32),
+                        pin(N * n, torch.float64), pin(N, torch.int32)) for delta in deltas}
+        one_step(nodes=X_pinned, host_out=bufs)  # warm-up of the host path
+        barrier()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(e2e_steps):
+            _, _, d2h = one_step(nodes=X_pinned, host_out=bufs)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+        out["e2e"] = {"value": N * len(deltas) * e2e_steps * world / e2e_s, "unit": UNIT,
+                      "h2d_bytes_per_step": int(X.nbytes * len(deltas)),
+                      "d2h_bytes_per_step": int(d2h)}
 
-    achieved = alg / (trav_ms / 1e3) / 1e12  # TFLOP/s of the traversal kernel
-    tr = _traffic_entry()
-    roofline = {"bound": "alu", "kernel": "k_traversal (FP64 LDL^T + solves)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (profiling recipe); "
-                               "MEASURED_PEAKS.json has no FP64 entry",
-                "traffic": (tr["bytes_per_launch"] if tr else None),
-                "share_of_step": trav_ms / total_ms}
+    trav_ms = sum(s["ms_traversal"] for s in all_st)
+    tr = _traffic_entry(name)
+    out["roofline"] = roofline_entry(
+        all_st, trav_ms, "k_traversal (FP64 LDL^T factorization + solves, persistent)",
+        share=trav_ms / total_ms * world, traffic=(tr["bytes_per_launch"] if tr else None))
     per_delta = {}
     for delta, sts in detail.items():
         per_delta[str(delta)] = {
@@ -321,58 +411,33 @@ def run_gpu(args):
             "ms_stencils": statistics.median(s["ms_stencils"] for s in sts),
             "ms_traversal": statistics.median(s["ms_traversal"] for s in sts),
             "ms_finalize": statistics.median(s["ms_finalize"] for s in sts),
-            "traversal_tflops": statistics.median(s["alg_flops"] / s["ms_traversal"] / 1e9
-                                                  for s in sts)}
+            "traversal_tflops_executed": statistics.median(
+                (s["sum_k3"] / 3.0 + 2.0 * s["sum_k2_cols"]) / s["ms_traversal"] / 1e9
+                for s in sts)}
+    out["per_delta"] = per_delta
     from paper_1606_03135_gb300 import model as CM
     M_terms = math.comb(ell + d, d)
-    speedup = CM.sweep_report({float(k): {"n_centers": v["n_centers"], "sum_cols": v["sum_cols"],
-                                          "ms_traversal": v["ms_traversal"]}
-                               for k, v in per_delta.items()}, N, n, M_terms, d)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload or WORKLOAD, "N": N, "d": d, "n": n, "ell": ell, "m": m,
-                   "deltas": list(deltas), "stab": "seq",
-                   **({"boundary": f"{int((bcw[0] > 0).sum())} boundary rows (kind "
-                                   f"{int(bcw[0].max())}) + time-stepping matrix c="
-                                   f"{w['timestep_c']:.3g}"} if bcw is not None else {}),
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "plans": "built on a side stream beside the previous delta's assembly "
-                            "(per_delta ms_stencils of later deltas include that overlap)",
-                   "schedule": ({str(k): v for k, v in sched.items()} if not args.no_autotune
-                                else "library default"),
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roofline, "cpu_baseline": cpu, "speedup_model": speedup,
-        "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(X.nbytes * len(deltas)),
-                "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": launches, "clocks": clk.summary(), "per_delta": per_delta,
-    }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
+    out["speedup_model"] = CM.sweep_report(
+        {float(k): {"n_centers": v["n_centers"], "sum_cols": v["sum_cols"],
+                    "ms_traversal": v["ms_traversal"]} for k, v in per_delta.items()},
+        N, n, M_terms, d)
+    return out
 
 
-def run_mixed(args):
+def run_mixed_config(args, steps=3, warmup=1):
     """The mixed-degree workload: one plan + assemble per step on the clustered cube with
-    per-node degree 2..5 (n = 2M + 1), delta = 0.3, FALLBACK stabilization."""
+    per-node degree 2..5 (n = 2M + 1), delta = 0.3, FALLBACK stabilization; then the same
+    assembly replayed from one captured CUDA graph."""
     import torch
     from paper_1606_03135_gb300 import nodesets as NS
     from paper_1606_03135_gb300 import rbffd as R
-    R.load()
-    torch.cuda.set_device(0)
-    name = args.workload
+    name = MIXED
     w = NS.MIXED_WORKLOADS[name]
     X = w["gen"](**w["kw"])
     n_node, ell_node, m_node = NS.mixed_degree_params(X, w["ells"])
     Xd = torch.from_numpy(X).cuda()
     delta = w["deltas"][0]
     stream = torch.cuda.current_stream()
-
     # schedule picked by the autotuner on this node set (untimed, like a library's heuristics)
     sched, sched_ms = R.autotune(Xd, n_node, ell_node, m_node, delta, mode=R.STAB_FALLBACK,
                                  repeats=1)
@@ -384,34 +449,35 @@ def run_mixed(args):
         p.close()
         return st
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     sts = []
-    for s_ in range(args.steps):
-        ev[s_][0].record(stream)
-        sts.append(step())
-        ev[s_][1].record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(steps):
+            ev[k][0].record(stream)
+            sts.append(step())
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     N = X.shape[0]
     st = sts[-1]
-    trav = sum(x["ms_traversal"] + x["ms_fallback"] for x in sts)
-    alg = sum(x["alg_flops"] for x in sts)
-    line = {"metric": METRIC, "value": N * args.steps / (total_ms / 1e3), "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": name, "N": N, "d": 3, "ells": list(w["ells"]),
-                       "n_max": int(n_node.max()), "delta": delta, "stab": "fallback"},
-            "roofline": {"bound": "alu", "achieved": alg / (trav / 1e3) / 1e12,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": alg / (trav / 1e3) / 1e12 / FP64_PEAK_TFLOPS},
-            "stats": {k: st[k] for k in ("n_centers", "n_fallback", "n_rejected", "sum_cols",
-                                         "max_ball", "nnz", "ms_stencils", "ms_traversal",
-                                         "ms_fallback", "ms_finalize")}}
+    solve_ms = sum(x["ms_traversal"] + x["ms_fallback"] for x in sts)
+    out = {"value": N * steps / (total_ms / 1e3), "unit": UNIT, "steps": steps,
+           "warmup": warmup, "ms_per_step": total_ms / steps,
+           "config": {"workload": name, "N": N, "d": 3, "ells": list(w["ells"]),
+                      "n_max": int(n_node.max()), "delta": delta, "stab": "fallback",
+                      "refine": "auto (pivot ratio >= 2^16)"},
+           "roofline": roofline_entry(sts, solve_ms, "k_traversal + k_fallback_solve (FP64 "
+                                      "LDL^T local solves, refined where ill-conditioned)",
+                                      share=solve_ms / total_ms),
+           "split_ms": {k: statistics.median(x[k] for x in sts)
+                        for k in ("ms_stencils", "ms_traversal", "ms_fallback", "ms_finalize")},
+           "stats": {k: st[k] for k in ("n_centers", "n_fallback", "n_rejected", "sum_cols",
+                                        "max_ball", "nnz")},
+           "clocks": clk.summary()}
     # the assembly as one captured CUDA graph (plan outside the graph), replayed
     with R.Plan(Xd, n_node, ell_node, m_node, delta, mode=R.STAB_FALLBACK, sync=False,
                 **sched) as p:
@@ -424,54 +490,106 @@ def run_mixed(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(gs):
             e0.record(gs)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 g.replay()
             e1.record(gs)
         torch.cuda.synchronize()
-        rep_ms = e0.elapsed_time(e1) / args.steps
+        rep_ms = e0.elapsed_time(e1) / steps
         gst = p.stats()
         if gst["status"] != 0:
             raise RuntimeError(f"graph replay: {R.rbffd_strerror(gst['status'])}")
-    line["schedule"] = {"autotuned": {k: int(v) for k, v in sched.items()},
-                        "candidates_ms": {str(dict(k)): round(v, 3) for k, v in sched_ms.items()}}
-    line["graph_replay"] = {"ms_per_assembly": rep_ms, "assemble_rows_per_s": N / (rep_ms / 1e3),
-                            "eager_assemble_ms": st["ms_traversal"] + st["ms_fallback"]
-                            + st["ms_finalize"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    out["schedule"] = {"autotuned": {k: int(v) for k, v in sched.items()},
+                       "candidates_ms": {str(dict(k)): round(v, 3) for k, v in sched_ms.items()}}
+    out["graph_replay"] = {"ms_per_assembly": rep_ms, "assemble_rows_per_s": N / (rep_ms / 1e3),
+                           "eager_assemble_ms": st["ms_traversal"] + st["ms_fallback"]
+                           + st["ms_finalize"]}
+    return out
 
 
-def run_serve(args):
-    """The serving workload: a seeded mix of jobs (2D/3D, N log-uniform, ell 2..5, random
-    delta) replayed with Poisson arrivals at two offered loads of the measured single-stream
-    throughput; prints one JSON line with p50/p99 latency and rows/s per load."""
-    import torch
+def run_serve_config(args):
+    """The serving workload: a seeded mix of jobs (2D/3D, N log-uniform in [1k, 200k], ell
+    2..5, random delta), replayed on equal terms with 1 slot (one job at a time: the plain
+    per-config path) and with `slots` slots (continuous batching): saturated (every job
+    available at t = 0) and with the same Poisson arrival trace at 0.5 and 0.9 of the
+    1-slot saturated rate.  p50/p99 latency, rows/s and the GPU-wide FP64 rate of each."""
     from paper_1606_03135_gb300 import serve as S
-    from paper_1606_03135_gb300 import rbffd as R
-    R.load()
-    torch.cuda.set_device(0)
     count = args.jobs
     jobs = S.serving_jobs(count=count)
     warm = S.serving_jobs(count=4, seed=77, n_min=1000, n_max=5000)
     S.Server(slots=1, keep_results=False).run(warm)
+    S.Server(slots=args.slots, keep_results=False).run(warm)
+
+    def summarise(results, summ):
+        sts = [r.stats for r in results if r.error is None and r.stats]
+        solve_ms = sum(s["ms_traversal"] + s["ms_fallback"] for s in sts)
+        rf = roofline_entry(sts, summ["makespan_s"] * 1e3, "local-solve kernels of every job, "
+                            "over the makespan (GPU-wide FP64 rate)")
+        keep = ("jobs", "failed", "rows", "makespan_s", "rows_per_s", "p50_latency_s",
+                "p99_latency_s", "peak_reserved_bytes", "slots")
+        return {**{k: summ[k] for k in keep}, "fp64_tflops": rf["achieved"],
+                "fp64_frac": rf["frac"], "solve_kernel_ms": solve_ms}
+
+    out = {"config": {"workload": f"serve{count}: d in {{2,3}}, N log-uniform [1k,200k], "
+                                  "ell 2..5, n=2M+1, delta U[0.2,1]", "hbm_budget_gb": 40,
+                      "slots": args.slots}, "saturated": {}, "poisson": {}}
     for j in jobs:
         j.arrival = 0.0
-    _, single = S.Server(slots=1, keep_results=False).run(jobs)
-    rate1 = count / single["makespan_s"]
-    out = {"metric": "serving rows/s and p50/p99 latency (FP64)", "unit": "rows/s",
-           "value": None, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"serve{count}: d in {{2,3}}, N log-uniform [1k,200k], "
-                                  "ell 2..5, n=2M+1, delta U[0.2,1], Poisson arrivals",
-                      "slots": args.slots, "hbm_budget_gb": 40},
-           "single_stream": {"rows_per_s": single["rows_per_s"],
-                             "makespan_s": single["makespan_s"]},
-           "loads": {}}
+    for slots in (1, args.slots):
+        res, summ = S.Server(slots=slots, keep_results=False).run(jobs)
+        out["saturated"][f"{slots}_slot"] = summarise(res, summ)
+    rate1 = count / out["saturated"]["1_slot"]["makespan_s"]
     for load in (0.5, 0.9):
         S.poisson_arrivals(jobs, rate=load * rate1)
-        _, summ = S.Server(slots=args.slots, keep_results=False).run(jobs)
-        out["loads"][str(load)] = summ
-    out["value"] = out["loads"]["0.9"]["rows_per_s"]
-    print(json.dumps(out), flush=True)
+        out["poisson"][str(load)] = {}
+        for slots in (1, args.slots):
+            res, summ = S.Server(slots=slots, keep_results=False).run(jobs)
+            out["poisson"][str(load)][f"{slots}_slot"] = summarise(res, summ)
+    sat = out["saturated"]
+    out["value"] = sat[f"{args.slots}_slot"]["rows_per_s"]
+    out["unit"] = UNIT
+    out["speedup_saturated"] = sat[f"{args.slots}_slot"]["rows_per_s"] / sat["1_slot"]["rows_per_s"]
+    return out
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = _env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1606_03135_gb300 import rbffd as R
+    R.load()
+    name = args.workload or WORKLOAD
+    t_start = time.perf_counter()
+    h = run_sweep(args, name, dev, world=world)
+    line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world,
+            "steps": h["steps"], "warmup": h["warmup"], "ms_per_step": h["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {**h["config"],
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": h["roofline"], "cpu_baseline": None, "e2e": h["e2e"],
+            "gpu_launches": h["gpu_launches"], "clocks": h["clocks"],
+            "per_delta": h["per_delta"], "speedup_model": h["speedup_model"]}
+    if rank == 0 and world == 1 and args.workload is None and not args.headline_only:
+        cfg = {}
+        s2 = run_sweep(args, SWEEP_2D, dev, e2e=True)
+        cfg[SWEEP_2D] = {k: s2[k] for k in ("value", "ms_per_step", "steps", "roofline", "e2e",
+                                            "per_delta", "gpu_launches", "clocks")}
+        cfg[SWEEP_2D]["schedule"] = s2["config"]["schedule"]
+        cfg[MIXED] = run_mixed_config(args)
+        cfg["serve"] = run_serve_config(args)
+        line["configs"] = cfg
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_entry()
+    line["bench_wall_s"] = time.perf_counter() - t_start
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     return 0
 
 
@@ -485,18 +603,26 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true",
                     help="the library's default schedule instead of one tuned per delta "
                          "(rbffd.autotune, before the timed region)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the headline sweep (no 2D, mixed or serving configs)")
     ap.add_argument("--workload", default=None,
-                    help="another named node-set workload (default: the 2D delta sweep), "
-                         "or 'serve' for the serving trace")
+                    help="one named delta-sweep workload instead of the default set, "
+                         f"'{MIXED}' or 'serve'")
     ap.add_argument("--jobs", type=int, default=256, help="serving trace length")
     ap.add_argument("--slots", type=int, default=4, help="serving slots (streams)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "serve":
-        return run_serve(args)
-    if args.workload and args.workload.startswith("cube3d_") and "mixed" in args.workload:
-        return run_mixed(args)
+    if args.workload in ("serve", MIXED):
+        import torch
+        from paper_1606_03135_gb300 import rbffd as R
+        R.load()
+        torch.cuda.set_device(0)
+        out = run_serve_config(args) if args.workload == "serve" else run_mixed_config(
+            args, steps=args.steps, warmup=args.warmup)
+        print(json.dumps({"metric": METRIC if args.workload == MIXED else
+                          "serving rows/s and p50/p99 latency (FP64)", **out}), flush=True)
+        return 0
     return run_gpu(args)
 
 

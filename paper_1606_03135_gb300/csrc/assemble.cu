@@ -367,6 +367,47 @@ __device__ bool factor_solve_lu(int K, int q, const StencilSmem& sm) {
     return true;
 }
 
+// Forward substitution with the unit lower factor of one column Xc (row stride xs) by one
+// warp, 32 rows at a time (2x2 pivots update a row with both columns in one expression, as in
+// the factorization; a block never splits a 2x2 pivot): inside a block the lanes keep x in
+// registers and take each pivot's value by a shuffle; below the block every lane applies the
+// block's updates to its rows in pivot order.  Each entry receives the same FMAs in the same
+// order as in forward_subst, with one warp synchronisation per block instead of per pivot.
+__device__ __forceinline__ void forward_subst_warp(int K, const StencilSmem& sm, double* Xc, int xs) {
+    const int lane = threadIdx.x & 31;
+    for (int b0 = 0; b0 < K;) {
+        int b1 = min(b0 + 32, K);
+        if (b1 < K && sm.pk[b1 - 1] == 2) --b1;
+        const int i = b0 + lane;
+        double x = i < b1 ? Xc[i * xs] : 0.0;
+        for (int p = b0; p < b1;) {
+            const int k = sm.pk[p];
+            const double xp = __shfl_sync(0xffffffffu, x, p - b0);
+            const double xq = __shfl_sync(0xffffffffu, x, min(p + 1 - b0, 31));
+            if (i > p + k - 1 && i < b1) {
+                const double* Ti = sm.T + tri(i);
+                x = k == 1 ? fma(-Ti[p], xp, x) : fma(-Ti[p + 1], xq, fma(-Ti[p], xp, x));
+            }
+            p += k;
+        }
+        if (i < b1) Xc[i * xs] = x;
+        __syncwarp();
+        for (int r = b1 + lane; r < K; r += 32) {
+            const double* Tr = sm.T + tri(r);
+            double xr = Xc[r * xs];
+            for (int p = b0; p < b1;) {
+                const int k = sm.pk[p];
+                xr = k == 1 ? fma(-Tr[p], Xc[p * xs], xr)
+                            : fma(-Tr[p + 1], Xc[(p + 1) * xs], fma(-Tr[p], Xc[p * xs], xr));
+                p += k;
+            }
+            Xc[r * xs] = xr;
+        }
+        __syncwarp();
+        b0 = b1;
+    }
+}
+
 // D solve and back substitution of the right-hand-side columns 0 .. q-1 held in sm.X, after
 // the forward substitution (carried through the factorization, or forward_subst).
 template <int NT>
@@ -813,7 +854,7 @@ __device__ void refine_columns(const SolveArgs& a, const Shape& sh, int c0, int 
                                const StencilSmem& sm, const double* __restrict__ gA,
                                double* __restrict__ gX0, int kind, int i) {
     constexpr int NW = NT / 32;
-    const int K = sh.K, xs = sm.xs, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int K = sh.K, xs = sm.xs, tid = threadIdx.x, wid = tid >> 5;
     double* gP = gX0 + (size_t)K * qk;  // kRefineSegs partial sums per entry
     __syncthreads();  // (the last solve steps may have been warp-synchronous)
     // adaptive: only systems whose pivots span at least 2^16 (unless every system is refined)
@@ -843,22 +884,7 @@ __device__ void refine_columns(const SolveArgs& a, const Shape& sh, int c0, int 
     }
     __syncthreads();
     if (qk <= NW) {  // forward substitution, a warp per column with warp synchronisation only
-        if (wid < qk) {
-            double* Xc = sm.X + wid;
-            for (int p = 0; p < K;) {
-                const int k = sm.pk[p];
-                const int p0 = p + k - 1;
-                const double xp = Xc[p * xs], xq = k == 2 ? Xc[(p + 1) * xs] : 0.0;
-                for (int r = p0 + 1 + lane; r < K; r += 32) {
-                    const double* Tr = sm.T + tri(r);
-                    double* dst = Xc + r * xs;
-                    if (k == 1) *dst = fma(-Tr[p], xp, *dst);
-                    else *dst = fma(-Tr[p + 1], xq, fma(-Tr[p], xp, *dst));
-                }
-                __syncwarp();
-                p += k;
-            }
-        }
+        if (wid < qk) forward_subst_warp(K, sm, sm.X + wid, xs);
     } else {
         forward_subst<NT>(K, qk, sm);
     }
@@ -1608,7 +1634,9 @@ static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool 
     if (nt == 0) {
         int per_sm = 0;
         if ((rc = occ(kNT, &per_sm))) return rc;
-        nt = (per_sm <= 4 || refined) ? kMaxNT : kNT;
+        // The fallback's one-column systems hide each other's serial pivot steps when two or
+        // more share an SM (512-thread teams run one per SM: their registers fill it).
+        nt = TRAVERSAL ? ((per_sm <= 4 || refined) ? kMaxNT : kNT) : (per_sm <= 1 ? kMaxNT : kNT);
         if (TRAVERSAL && PACKED && nt == kNT) {
             int p96 = 0;
             if ((rc = occ(96, &p96))) return rc;

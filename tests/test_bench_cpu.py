@@ -75,3 +75,22 @@ def test_kernel_source_hash_ignores_comments_only(tmp_path):
     assert bench.kernel_source_hash(str(a)) == bench.kernel_source_hash(str(b))
     assert bench.kernel_source_hash(str(a)) != bench.kernel_source_hash(str(c))
 
+
+
+def test_roofline_counts_follow_the_cost_model():
+    """flops_executed = (1/3) K^3 per LDL^T factorization + 2 K^2 per solved column; the
+    survey count uses (2/3) K^3 (§4.3 cost model); frac = achieved / peak."""
+    K, q = 65, 7
+    st = {"sum_k3": 10 * K ** 3, "sum_k2_cols": 10 * K * K * q, "flops_refine": 0.0}
+    r = bench.roofline_entry([st, st], 2.0, "k")
+    ex = 2 * (10 * K ** 3 / 3.0 + 2.0 * 10 * K * K * q)
+    sv = 2 * (10 * 2.0 * K ** 3 / 3.0 + 2.0 * 10 * K * K * q)
+    assert abs(r["flops_executed"] - ex) <= 1e-9 * ex and abs(r["flops_survey"] - sv) <= 1e-9 * sv
+    assert abs(r["achieved"] - ex / 2e-3 / 1e12) <= 1e-12
+    assert abs(r["frac"] - r["achieved"] / bench.FP64_PEAK_TFLOPS) <= 1e-12
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+
+
+def test_host_cpu_reports_cores_and_a_model():
+    cores, model = bench.host_cpu()
+    assert cores >= 1 and isinstance(model, str) and model
