@@ -255,6 +255,9 @@ def run_reference(args):
     return 0
 
 
+PROBE = None  # FP64 pipe rates measured on this GPU before anything is timed (probe.measure)
+
+
 def roofline_entry(stats, kernel_ms, kernel, share=None, traffic=None, factor_lu=False):
     """FP64 roofline of the local-solve kernels over the launches in `stats` (rbffd_stats
     dicts) taking `kernel_ms` of device time (CUDA events on the launching stream).
@@ -273,7 +276,13 @@ def roofline_entry(stats, kernel_ms, kernel, share=None, traffic=None, factor_lu
             "frac_survey": survey / sec / 1e12 / FP64_PEAK_TFLOPS,
             "flops_refine": sum(s["flops_refine"] for s in stats),
             "peak_source": PEAK_DERIVATION, "traffic": traffic, "share_of_step": share,
-            "kernel_ms": kernel_ms}
+            "kernel_ms": kernel_ms,
+            **({"peak_measured_dfma": PROBE["dfma"]["tflops"],
+                "frac_of_measured_dfma": achieved / PROBE["dfma"]["tflops"],
+                "dmma_tflops_measured": PROBE["dmma"]["tflops"],
+                "peak_probe": "include/fp64_probe.h: independent DFMA chains and FP64 "
+                              "mma.sync m8n8k4 tiles on every SM, CUDA events, best of 3"}
+               if PROBE else {})}
 
 
 def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
@@ -560,7 +569,10 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     from paper_1606_03135_gb300 import rbffd as R
+    from paper_1606_03135_gb300 import probe as P
     R.load()
+    global PROBE
+    PROBE = P.measure(iters=5000, repeats=3)
     name = args.workload or WORKLOAD
     t_start = time.perf_counter()
     h = run_sweep(args, name, dev, world=world)
@@ -572,7 +584,8 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": h["roofline"], "cpu_baseline": None, "e2e": h["e2e"],
             "gpu_launches": h["gpu_launches"], "clocks": h["clocks"],
-            "per_delta": h["per_delta"], "speedup_model": h["speedup_model"]}
+            "per_delta": h["per_delta"], "speedup_model": h["speedup_model"],
+            "fp64_probe": PROBE}
     if rank == 0 and world == 1 and args.workload is None and not args.headline_only:
         cfg = {}
         s2 = run_sweep(args, SWEEP_2D, dev, e2e=True)

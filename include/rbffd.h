@@ -247,10 +247,14 @@ int rbffd_export_lambda(rbffd_plan_t plan, double* lam_row, uint8_t* is_center);
  *            writes nothing.  d, n, delta as for rbffd_plan.
  * It allocates nothing: its working memory is one fixed array in the library's device
  * memory (about 2 MB, held on every GPU that loads the library until the process exits).
- * The first call on a device looks that array up for the current device; make that first
- * call before any stream capture.  All calls share the array, so calls that overlap on the
- * GPU (other streams, other host threads) race and must be serialised by the caller.  The
- * call waits for `stream` to read the device status (RBFFD_EDUPLICATE for coincident nodes). */
+ * The first call on a device looks that array's device address up for the current device
+ * and keeps it for the process; after cudaDeviceReset of that device the kept address is no
+ * longer valid, so the call must not be used on that device again in the process.  All calls
+ * share the array, so calls that overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller; each call clears the status it reads.  Every call
+ * ends by copying the device status to the host and waiting for `stream`
+ * (RBFFD_EDUPLICATE for coincident nodes), so no call can be made while `stream` is being
+ * captured into a CUDA graph. */
 #define RBFFD_NOALLOC_MAX_NODES 32768
 int rbffd_stencils_noalloc(const double* nodes, int64_t N, int d, int n, double delta,
                            int32_t* nbr, double* rho2, int32_t* ball_len, void* stream);

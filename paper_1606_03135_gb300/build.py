@@ -16,6 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librbffd.so")
+PROBE_LIB = os.path.join(OUT_DIR, "libfp64probe.so")  # FP64 pipe probe (include/fp64_probe.h)
 SOURCES = ["knn.cu", "assemble.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -31,13 +32,14 @@ def nvcc() -> str:
 
 def _deps():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + \
-        [os.path.join(ROOT, "include", "rbffd.h")]
+        [os.path.join(ROOT, "include", f) for f in ("rbffd.h", "fp64_probe.h")]
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and \
-            os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in _deps()):
+    if not force and os.path.exists(LIB) and os.path.exists(PROBE_LIB) and \
+            min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB)) >= \
+            max(os.path.getmtime(f) for f in _deps()):
         return LIB
     cc = nvcc()
     objs = [os.path.join(OUT_DIR, s.replace(".cu", ".o")) for s in SOURCES]
@@ -49,8 +51,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
         return r.stderr
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        logs = list(ex.map(one, SOURCES, objs))
+    probe_obj = os.path.join(OUT_DIR, "fp64_probe.o")
+    with cf.ThreadPoolExecutor(len(SOURCES) + 1) as ex:
+        logs = list(ex.map(one, SOURCES + ["fp64_probe.cu"], objs + [probe_obj]))
     if verbose:
         for l in logs:
             print(l)
@@ -59,6 +62,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, probe_obj], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed (probe):\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
     return LIB
 
 

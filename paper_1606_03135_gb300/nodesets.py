@@ -245,6 +245,11 @@ WORKLOADS = {
                                       m=7, deltas=(1.0, 0.5, 0.3)),
     "ball3d_N100000_l3_n45_r7": dict(gen=ball3d, kw=dict(N=100000, seed=3), d=3, n=45, ell=3,
                                      m=7, deltas=(1.0, 0.4, 0.2)),
+    # reduced sizes of the same recipes (small cases for full profiler captures)
+    "ball3d_N20000_l3_n45_r7": dict(gen=ball3d, kw=dict(N=20000, seed=3), d=3, n=45, ell=3,
+                                    m=7, deltas=(1.0, 0.4, 0.2)),
+    "square2d_N10000_l4_n31_r7": dict(gen=square2d, kw=dict(N=10000, seed=2), d=2, n=31, ell=4,
+                                      m=7, deltas=(1.0, 0.5, 0.3)),
     # the 2D square in row-major order: the traversal order is part of the input (§4.1), and
     # this one makes long dependency chains
     "square2d_raster_N40000_l4_n31_r7": dict(gen=square2d, kw=dict(N=40000, seed=2,

@@ -80,3 +80,14 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == C.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+
+
+def test_fp64_probe_library_loads_exports_and_checks_arguments_without_a_gpu():
+    from paper_1606_03135_gb300 import probe as P
+    L = P.load()
+    src = open(os.path.join(os.path.dirname(HEADER), "fp64_probe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    for name in set(re.findall(r"\b(fp64_probe_[a-z_]+)\s*\(", src)):
+        assert hasattr(L, name), name
+    assert P.fp64_probe_run(7, 10)[0] == -1   # unknown kind: refused before any CUDA call
+    assert P.fp64_probe_run(0, 0)[0] == -1    # no iterations

@@ -57,3 +57,18 @@ def test_noalloc_rejects_sizes_beyond_its_capacity():
     rc, nbr, _, _ = _noalloc(X, 12, 0.5)
     assert rc == R.EINVAL
     assert np.all(nbr == -7)  # nothing written
+
+
+def test_a_failing_call_leaves_no_error_for_the_next_one():
+    """A call on a node set with two coincident nodes returns RBFFD_EDUPLICATE (as rbffd_plan
+    does); the next call on a clean node set returns OK and matches rbffd_plan bit for bit, so
+    the error status kept in the shared array does not leak into it."""
+    X = NS.disk2d(3000, seed=4)
+    bad = X.copy()
+    bad[100] = bad[17]
+    rc, _, _, _ = _noalloc(bad, 12, 0.5)
+    assert rc == R.EDUPLICATE
+    rc, nbr, rho2, bl = _noalloc(X, 12, 0.5)
+    assert rc == R.OK, R.rbffd_strerror(rc)
+    nbr_p, rho2_p, bl_p = _with_plan(X, 12, 2, 3, 0.5)
+    assert np.array_equal(nbr, nbr_p) and np.array_equal(rho2, rho2_p) and np.array_equal(bl, bl_p)
