@@ -6,11 +6,12 @@ Lebesgue stabilization, one factorization per center, multi-RHS solves, CSR) for
 quasi-uniform nodes in the unit ball, PHS r^7, degree-3 polynomials (M = 20), n = 45.
 Metric: matrix rows per second.  The same JSON line carries, under "configs", the 2D square
 sweep (N = 40,000), the clustered mixed-degree cube (N = 500,000, eager and replayed from a
-captured CUDA graph) and the serving trace (256 jobs: 1 slot against 4 slots on the same
-arrival traces), each with its own roofline.
+captured CUDA graph), a batch of four node sets of different dimension and degree (one graph
+against one graph per plan) and the serving trace (256 jobs: 1 slot against 4 slots on the
+same arrival traces), each with its own roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--headline-only] [--workload NAME | serve]
+                    [--headline-only] [--workload NAME | batch | serve]
 
 Under torchrun (N > 1) every rank forms its own copy of the headline workload (independent
 replicas: the method has no exchange step on this path) and rank 0 prints one JSON line with
@@ -302,6 +303,12 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
     stream = torch.cuda.current_stream(dev)
     copy_stream = torch.cuda.Stream(dev)
     plan_stream = torch.cuda.Stream(dev)
+    # with --concurrent-deltas each delta's assembly runs on its own stream, and CTAs of a
+    # traversal's dependency tail leave (rbffd_opts.elastic) so the next delta's kernel fills
+    # their SMs
+    conc = getattr(args, "concurrent_deltas", False)
+    asm_streams = [torch.cuda.Stream(dev) for _ in deltas] if conc else [stream] * len(deltas)
+    elastic = args.elastic if conc else 0
     # Schedule per delta (team size, grid cap, right-hand sides per factorization), chosen by
     # timing the candidates on this node set before anything is timed; the matrix does not
     # depend on it.
@@ -310,7 +317,7 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
         for delta in deltas:
             sched[delta], _ = R.autotune(Xd, n, ell, m, delta, repeats=3)
 
-    def one_step(detail=None, nodes=None, host_out=False):
+    def one_step(detail=None, nodes=None, host_out=False, spans=None):
         # The sweep keeps its plans (and their CSR) on the device until every delta is
         # assembled, so the host plans the next delta while the GPU assembles the current one.
         # Each delta's plan (kNN, retention balls: independent of the other deltas) is built
@@ -321,15 +328,28 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
         d2h = 0
         plans, sts = [], []
         plan_stream.wait_stream(stream)  # (after the step's start event)
-        for delta in deltas:
+        for k, delta in enumerate(deltas):
             p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta, sync=False,
-                       stream=plan_stream, **sched[delta])
+                       stream=plan_stream, elastic=elastic, **sched[delta])
             if bcw is not None:  # boundary rows and the time-stepping matrix of §5
                 p.set_boundary(*bcw)
-            p.assemble(stream=stream)
+            s_k = asm_streams[k]
+            if s_k is not stream:
+                s_k.wait_stream(stream)
+            if spans is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(s_k)
+            p.assemble(stream=s_k)
             if bcw is not None:
                 p.timestep_matrix(w["timestep_c"], out=ts_buf[delta])
+            if spans is not None:
+                f = torch.cuda.Event(enable_timing=True)
+                f.record(s_k)
+                spans.append((e, f))
             plans.append((delta, p))
+        for s_k in asm_streams:
+            if s_k is not stream:
+                stream.wait_stream(s_k)
         if host_out:  # into pinned host buffers allocated once, on a copy stream: one delta's
             for delta, p in plans:  # copies overlap the next deltas' assembly
                 row_ptr, col, val, owner = p.export_async(host_out[delta], copy_stream)
@@ -360,17 +380,31 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
     detail = {}
     launches = 0
     all_st = []
+    spans = [[] for _ in range(steps)]
     barrier()
     with ClockSampler(torch.cuda.current_device()) as clk:
         for k in range(steps):
             flush.fill_(float(k))  # evict L2 between timed steps (not inside a step's events)
             ev[k][0].record(stream)
-            l, sts, _ = one_step(detail)
+            l, sts, _ = one_step(detail, spans=spans[k])
             ev[k][1].record(stream)
             launches += l
             all_st += sts
         barrier()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    # device time of the assemblies (traversal + its small init and CSR launches): the union
+    # of their intervals, so that assemblies running side by side count once
+    asm_union_ms = 0.0
+    for k in range(steps):
+        iv = sorted((ev[k][0].elapsed_time(a), ev[k][0].elapsed_time(b)) for a, b in spans[k])
+        lo, hi = iv[0]
+        for a, b in iv[1:]:
+            if a > hi:
+                asm_union_ms += hi - lo
+                lo, hi = a, b
+            else:
+                hi = max(hi, b)
+        asm_union_ms += hi - lo
     total_ms = max_over_ranks(sum(step_ms), dev)
     rows = N * len(deltas) * steps * world
     value = rows / (total_ms / 1e3)
@@ -385,7 +419,8 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
                       "plans": "built on a side stream beside the previous delta's assembly "
                                "(per_delta ms_stencils of later deltas include that overlap)",
                       "schedule": ({str(k): v for k, v in sched.items()}
-                                   if not args.no_autotune else "library default")},
+                                   if not args.no_autotune else "library default"),
+                      "deltas_concurrent": bool(conc), "elastic": elastic},
            "gpu_launches": launches, "clocks": clk.summary()}
 
     if e2e:  # end to end through the public API with host buffers: host nodes in, host CSR
@@ -408,10 +443,13 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
                       "h2d_bytes_per_step": int(X.nbytes * len(deltas)),
                       "d2h_bytes_per_step": int(d2h)}
 
-    trav_ms = sum(s["ms_traversal"] for s in all_st)
+    # the traversal kernels' device time: their own events when they run one after another,
+    # else the union of the assemblies' intervals (which adds the tiny init and CSR launches)
+    trav_ms = asm_union_ms if conc else sum(s["ms_traversal"] for s in all_st)
     tr = _traffic_entry(name)
     out["roofline"] = roofline_entry(
-        all_st, trav_ms, "k_traversal (FP64 LDL^T factorization + solves, persistent)",
+        all_st, trav_ms, "k_traversal (FP64 LDL^T factorization + solves, persistent)"
+        + ("; time = union of the concurrent assemblies' intervals" if conc else ""),
         share=trav_ms / total_ms * world, traffic=(tr["bytes_per_launch"] if tr else None))
     per_delta = {}
     for delta, sts in detail.items():
@@ -515,6 +553,80 @@ def run_mixed_config(args, steps=3, warmup=1):
     return out
 
 
+def run_batch_config(args, steps=5, warmup=2):
+    """Batching across dimensions and degrees: four node sets (2D square, degree 4; 3D ball,
+    degree 3; 2D disk, degree 5; 3D ball, degree 2), each planned once, their assemblies
+    replayed (a) one after another, each from its own captured graph, on one stream (the
+    plain per-config path) and (b) from one graph holding all four on concurrent streams: as
+    they are, with the elastic traversal grid (tail CTAs leave for the other plans' kernels),
+    and with each grid capped to a share of the GPU.
+    Rows/s of each and the GPU-wide FP64 rate of the solve kernels."""
+    import torch
+    from paper_1606_03135_gb300 import nodesets as NS
+    from paper_1606_03135_gb300 import rbffd as R
+    setups = [("square2d N=40000, ell=4, n=31, r^7, delta=0.5", NS.square2d(40000, seed=2),
+               (31, 4, 7), 0.5),
+              ("ball3d N=100000, ell=3, n=45, r^7, delta=0.4", NS.ball3d(100000, seed=3),
+               (45, 3, 7), 0.4),
+              ("disk2d N=20000, ell=5, n=43, r^7, delta=0.3", NS.disk2d(20000, seed=11),
+               (43, 5, 7), 0.3),
+              ("ball3d N=20000, ell=2, n=21, r^5, delta=0.5", NS.ball3d(20000, seed=12),
+               (21, 2, 5), 0.5)]
+    rows = sum(X.shape[0] for _, X, _, _ in setups)
+
+    def make(cap, elastic=0):
+        ps = []
+        for _, X, params, delta in setups:
+            p = R.Plan(torch.from_numpy(X).cuda(), *params, delta, sync=False, max_ctas=cap,
+                       elastic=elastic)
+            p.assemble()
+            ps.append(p)
+        torch.cuda.synchronize()
+        return ps
+
+    def timed(replay, plans):
+        for _ in range(warmup):
+            replay()
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            replay()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        sts = [p.stats() for p in plans]
+        for st in sts:
+            if st["status"] != 0:
+                raise RuntimeError(f"batch replay: {R.rbffd_strerror(st['status'])}")
+        rf = roofline_entry(sts, ms, "local-solve kernels of the four plans, over the replay")
+        return {"ms_per_batch": ms, "rows_per_s": rows / (ms / 1e3), "fp64_tflops": rf["achieved"],
+                "fp64_frac": rf["frac"]}
+
+    out = {"config": {"workload": "batch of 4: " + "; ".join(n for n, _, _, _ in setups),
+                      "rows_per_batch": rows}}
+    plans = make(0)
+    graphs = [p.capture_assemble() for p in plans]
+    out["plain"] = timed(lambda: [g.replay() for g in graphs], plans)
+    for p in plans:
+        p.close()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    variants = (("batched", 0, 0), ("batched_elastic", 0, sms), ("batched_shared", 4 * sms, 0))
+    for name, cap, elastic in variants:
+        plans = make(cap, elastic)
+        g = R.capture_assemble_batch(plans)
+        out[name] = timed(g.replay, plans)
+        out[name]["max_ctas"] = cap
+        out[name]["elastic"] = elastic
+        for p in plans:
+            p.close()
+    out["value"] = max(out[v[0]]["rows_per_s"] for v in variants)
+    out["unit"] = UNIT
+    out["speedup"] = out["value"] / out["plain"]["rows_per_s"]
+    return out
+
+
 def run_serve_config(args):
     """The serving workload: a seeded mix of jobs (2D/3D, N log-uniform in [1k, 200k], ell
     2..5, random delta), replayed on equal terms with 1 slot (one job at a time: the plain
@@ -593,6 +705,7 @@ def run_gpu(args):
                                             "per_delta", "gpu_launches", "clocks")}
         cfg[SWEEP_2D]["schedule"] = s2["config"]["schedule"]
         cfg[MIXED] = run_mixed_config(args)
+        cfg["batch"] = run_batch_config(args)
         cfg["serve"] = run_serve_config(args)
         line["configs"] = cfg
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -620,21 +733,28 @@ def main(argv=None):
                     help="only the headline sweep (no 2D, mixed or serving configs)")
     ap.add_argument("--workload", default=None,
                     help="one named delta-sweep workload instead of the default set, "
-                         f"'{MIXED}' or 'serve'")
+                         f"'{MIXED}', 'batch' or 'serve'")
+    ap.add_argument("--concurrent-deltas", action="store_true",
+                    help="assemble the deltas of a sweep on concurrent streams with an "
+                         "elastic traversal grid (rbffd_opts.elastic)")
+    ap.add_argument("--elastic", type=int, default=152,
+                    help="waiting CTAs beyond which a traversal CTA leaves (with "
+                         "--concurrent-deltas)")
     ap.add_argument("--jobs", type=int, default=256, help="serving trace length")
     ap.add_argument("--slots", type=int, default=4, help="serving slots (streams)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("serve", MIXED):
+    if args.workload in ("serve", "batch", MIXED):
         import torch
         from paper_1606_03135_gb300 import rbffd as R
         R.load()
         torch.cuda.set_device(0)
-        out = run_serve_config(args) if args.workload == "serve" else run_mixed_config(
-            args, steps=args.steps, warmup=args.warmup)
-        print(json.dumps({"metric": METRIC if args.workload == MIXED else
-                          "serving rows/s and p50/p99 latency (FP64)", **out}), flush=True)
+        out = run_serve_config(args) if args.workload == "serve" else \
+            run_batch_config(args) if args.workload == "batch" else \
+            run_mixed_config(args, steps=args.steps, warmup=args.warmup)
+        print(json.dumps({"metric": "serving rows/s and p50/p99 latency (FP64)"
+                          if args.workload == "serve" else METRIC, **out}), flush=True)
         return 0
     return run_gpu(args)
 

@@ -102,6 +102,14 @@ typedef struct {
                            traversal's 96- and 128-thread teams have no refinement step, so
                            forcing them (opts.team) on a plan that refines is RBFFD_EINVAL.
                            RBFFD_FACTOR_LU is never refined.  Other values: RBFFD_EINVAL */
+    int elastic;        /* 0 (default): the persistent traversal grid keeps every CTA until the
+                           traversal is done; T > 0: a CTA that has finished a center leaves
+                           instead of claiming the next queue entry when at least T others are
+                           already waiting for entries (the dependency tail of delta < 1), so a
+                           kernel launched beside it (another plan's assembly on another stream)
+                           takes over its SM.  The matrix does not change.  Fewer waiting CTAs
+                           also means fewer solves made ahead, so a plan assembled alone is not
+                           faster with it.  < 0: RBFFD_EINVAL */
 } rbffd_opts;
 
 #define RBFFD_REFINE_AUTO 0

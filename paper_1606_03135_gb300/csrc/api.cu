@@ -358,7 +358,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         }
     }
     rbffd_opts o{RBFFD_STAB_SEQ, 0, 5000, 1, 0, RBFFD_FACTOR_LDLT, 0, 0, 0, RBFFD_LREF_CENTER,
-                 RBFFD_REFINE_AUTO};
+                 RBFFD_REFINE_AUTO, 0};
     if (opts) o = *opts;
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
         (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0 ||
@@ -367,7 +367,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         (o.factor == RBFFD_FACTOR_LU && o.team != 0 && o.team != 128 && o.team != 512) ||
         o.rhs_chunk < 0 || (o.factor == RBFFD_FACTOR_LU && o.rhs_chunk > 0) ||
         (o.lebesgue_ref != RBFFD_LREF_CENTER && o.lebesgue_ref != RBFFD_LREF_CENTROID) ||
-        o.refine < RBFFD_REFINE_AUTO || o.refine > RBFFD_REFINE_NONE)
+        o.refine < RBFFD_REFINE_AUTO || o.refine > RBFFD_REFINE_NONE || o.elastic < 0)
         return RBFFD_EINVAL;
     if (o.timeout_ms <= 0) o.timeout_ms = 5000;
 
@@ -631,6 +631,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.no_seed = p->opts.fault_inject == 1;
     a.factor = p->opts.factor;
     a.max_ctas = p->opts.max_ctas;
+    a.elastic = p->opts.elastic;
     a.rs = p->rs;
     a.rs_stride = p->rs_stride;
     a.rs_x0 = p->rs_x0;

@@ -1112,8 +1112,16 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
     for (;;) {
         if (tid == 0) {
             int j = -1, k = -1, sp = 0;
-            if (slot < 0) slot = atomicAdd(&a.ctr->q_head, 1);
-            if (slot < N) {
+            bool leave = false;
+            if (slot < 0 && a.elastic > 0) {
+                // Elastic grid: holding no slot, this CTA may leave; the CTAs that hold the
+                // unfilled slots (at least a.elastic of them) process every entry still to
+                // come, and none of them leaves while it holds one.
+                const int waiting = *((volatile int*)&a.ctr->q_head) - *((volatile int*)&a.ctr->q_tail);
+                leave = waiting >= a.elastic;
+            }
+            if (slot < 0 && !leave) slot = atomicAdd(&a.ctr->q_head, 1);
+            if (!leave && slot < N) {
                 const unsigned long long t0 = globaltimer_ns();
                 unsigned nsl = 32;
                 for (;;) {

@@ -151,6 +151,7 @@ struct SolveArgs {
     int no_seed;               // fault injection: push no initial center (waits run out)
     int factor;                // RBFFD_FACTOR_LDLT (packed layout) or RBFFD_FACTOR_LU (full)
     int max_ctas;              // cap on the persistent grid (0 = fill the GPU)
+    int elastic;               // > 0: a CTA holding no queue slot leaves when this many wait
     // One step of iterative refinement of ill-conditioned LDL^T local solves, in plans whose
     // largest system has K >= refine_min_K: per-CTA scratch of rs_stride doubles at
     // rs + blockIdx.x rs_stride holding the assembled matrix in full (K x K) and, from offset

@@ -27,7 +27,7 @@ class rbffd_opts(C.Structure):
     _fields_ = [("stab_mode", C.c_int), ("nodes_on_host", C.c_int), ("timeout_ms", C.c_int),
                 ("sync", C.c_int), ("fault_inject", C.c_int), ("factor", C.c_int),
                 ("max_ctas", C.c_int), ("team", C.c_int), ("rhs_chunk", C.c_int),
-                ("lebesgue_ref", C.c_int), ("refine", C.c_int)]
+                ("lebesgue_ref", C.c_int), ("refine", C.c_int), ("elastic", C.c_int)]
 
 
 class rbffd_csr(C.Structure):
@@ -193,7 +193,7 @@ class Plan:
 
     def __init__(self, nodes, n, ell, m, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True,
                  stream=None, fault_inject=0, factor=FACTOR_LDLT, max_ctas=0, team=0,
-                 rhs_chunk=0, lebesgue_ref=0, refine=REFINE_AUTO):
+                 rhs_chunk=0, lebesgue_ref=0, refine=REFINE_AUTO, elastic=0):
         self._plan = None
         self._stream = stream
         if isinstance(nodes, np.ndarray):
@@ -209,7 +209,7 @@ class Plan:
         self.ell, self.m, self.delta, self.mode = ell, m, delta, mode
         self.sync = bool(sync)
         opts = rbffd_opts(mode, on_host, timeout_ms, 1 if sync else 0, fault_inject, factor,
-                          max_ctas, team, rhs_chunk, lebesgue_ref, refine)
+                          max_ctas, team, rhs_chunk, lebesgue_ref, refine, elastic)
         if np.ndim(n) == 0:  # one stencil size, degree and exponent for every node
             self.n = int(n)
             rc, plan = rbffd_plan(_p(self._nodes), self.N, self.d, n, ell, m, delta, opts,
@@ -344,6 +344,35 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def capture_assemble_batch(plans, streams=None):
+    """Record one rbffd_assemble of every plan in `plans` into a single CUDA graph
+    (torch.cuda.CUDAGraph): each plan on its own stream, forked from the capture stream and
+    joined back, so a replay runs the plans' kernels concurrently, whatever their dimension,
+    degree or stencil sizes.  Every plan must be asynchronous (sync=False) and assembled once
+    before capture (so the graph allocates nothing).  Each plan's later calls (stats, export)
+    use its stream from the capture."""
+    import torch
+    for p in plans:
+        if p.sync:
+            raise ValueError("capture needs plans created with sync=False")
+    g = torch.cuda.CUDAGraph()
+    s0 = torch.cuda.Stream()
+    ss = list(streams) if streams is not None else [torch.cuda.Stream() for _ in plans]
+    s0.wait_stream(torch.cuda.current_stream())
+    rcs = []
+    with torch.cuda.graph(g, stream=s0):
+        for p, s in zip(plans, ss):
+            s.wait_stream(s0)
+            rcs.append(rbffd_assemble(p._plan, C.c_void_p(s.cuda_stream))[0])
+        for s in ss:
+            s0.wait_stream(s)
+    for rc in rcs:
+        _check(rc, "rbffd_assemble (batch capture)")
+    for p, s in zip(plans, ss):
+        p._stream = s
+    return g
 
 
 # ------------------------------------------------------------------ schedule autotuner

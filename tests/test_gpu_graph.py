@@ -58,3 +58,40 @@ def test_graph_replay_of_a_mixed_degree_plan_with_fallback():
         for a, b in zip(ref, got):
             assert np.array_equal(a, b)
         assert p.stats()["status"] == 0
+
+
+def test_one_graph_assembles_plans_of_different_dimension_and_degree():
+    """A 2D plan, a 3D plan, a per-node mixed-degree plan with fallback and a degree-5 2D plan
+    captured together into one CUDA graph (each on its own stream: their kernels run side by
+    side); every replay rebuilds each plan's matrix bit for bit as assembled alone."""
+    setups = [
+        (NS.square2d(10000, seed=5), (31, 4, 7), 0.3, R.STAB_SEQ),
+        (NS.ball3d(10000, seed=3), (45, 3, 7), 0.4, R.STAB_SEQ),
+        (NS.cube3d_clustered(3000, seed=4), None, 0.3, R.STAB_FALLBACK),
+        (NS.disk2d(4000, seed=9), (43, 5, 7), 0.5, R.STAB_SEQ),
+    ]
+    solo, plans, csrs = [], [], []
+    for X, params, delta, mode in setups:
+        params = params if params is not None else NS.mixed_degree_params(X)
+        Xd = torch.from_numpy(X).cuda()
+        with R.Plan(Xd, *params, delta, mode=mode) as p:
+            p.assemble()
+            solo.append(p.export())
+        p = R.Plan(Xd, *params, delta, mode=mode, sync=False, max_ctas=300)
+        csrs.append(p.assemble())
+        plans.append(p)
+    torch.cuda.synchronize()
+    g = R.capture_assemble_batch(plans)
+    for _ in range(2):
+        torch.cuda.synchronize()
+        for p, csr, ref in zip(plans, csrs, solo):
+            _memset_device(csr.val, int(ref[0][-1]) * 8)
+        g.replay()
+        torch.cuda.synchronize()
+        for p, ref in zip(plans, solo):
+            got = p.export()
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b)
+            assert p.stats()["status"] == 0
+    for p in plans:
+        p.close()

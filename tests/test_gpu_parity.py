@@ -617,3 +617,29 @@ def test_teams_without_the_refinement_step_are_refused_for_refined_systems():
         assert e.value.code == R.EINVAL
         with R.Plan(X, *params, 0.3, team=team, refine=R.REFINE_NONE) as p:
             p.assemble()
+
+
+@pytest.mark.parametrize("elastic", [1, 8, 152])
+def test_elastic_grid_forms_the_same_matrix_alone_and_beside_other_plans(elastic):
+    """CTAs that leave the traversal's dependency tail (rbffd_opts.elastic) change who solves a
+    center, never its arithmetic: the matrix is bit-identical, for one plan and for three
+    deltas assembled at once on their own streams."""
+    X = NS.square2d(10000, seed=5)
+    Xd = torch.from_numpy(X).cuda()
+    ref = {d: gpu_run(X, 31, 4, 7, d) for d in (1.0, 0.5, 0.3)}
+    g = gpu_run(X, 31, 4, 7, 0.3, elastic=elastic)
+    for key in ("row_ptr", "col", "val", "owner", "is_center", "lam_row"):
+        assert np.array_equal(g[key], ref[0.3][key]), key
+    streams = [torch.cuda.Stream() for _ in ref]
+    plans = []
+    for s, d in zip(streams, ref):
+        p = R.Plan(Xd, 31, 4, 7, d, sync=False, elastic=elastic)
+        p.assemble(stream=s)
+        plans.append((d, p))
+    torch.cuda.synchronize()
+    for d, p in plans:
+        assert p.stats()["status"] == 0
+        got = p.export()
+        for a, b in zip(got, (ref[d][k] for k in ("row_ptr", "col", "val", "owner"))):
+            assert np.array_equal(a, b), d
+        p.close()
