@@ -317,7 +317,7 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
         for delta in deltas:
             sched[delta], _ = R.autotune(Xd, n, ell, m, delta, repeats=3)
 
-    def one_step(detail=None, nodes=None, host_out=False, spans=None):
+    def one_step(detail=None, nodes=None, host_out=False, spans=None, end_event=None):
         # The sweep keeps its plans (and their CSR) on the device until every delta is
         # assembled, so the host plans the next delta while the GPU assembles the current one.
         # Each delta's plan (kNN, retention balls: independent of the other deltas) is built
@@ -350,6 +350,8 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
         for s_k in asm_streams:
             if s_k is not stream:
                 stream.wait_stream(s_k)
+        if end_event is not None:  # the step's device work ends with the last assembly
+            end_event.record(stream)
         if host_out:  # into pinned host buffers allocated once, on a copy stream: one delta's
             for delta, p in plans:  # copies overlap the next deltas' assembly
                 row_ptr, col, val, owner = p.export_async(host_out[delta], copy_stream)
@@ -381,17 +383,20 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
     launches = 0
     all_st = []
     spans = [[] for _ in range(steps)]
+    ev_host = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     barrier()
     with ClockSampler(torch.cuda.current_device()) as clk:
         for k in range(steps):
             flush.fill_(float(k))  # evict L2 between timed steps (not inside a step's events)
             ev[k][0].record(stream)
-            l, sts, _ = one_step(detail, spans=spans[k])
-            ev[k][1].record(stream)
+            l, sts, _ = one_step(detail, spans=spans[k], end_event=ev[k][1])
+            ev_host[k].record(stream)
             launches += l
             all_st += sts
         barrier()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    # (the host then reads each plan's counters and frees it: up to the event after that)
+    host_ms = [e0.elapsed_time(h) for (e0, _), h in zip(ev, ev_host)]
     # device time of the assemblies (traversal + its small init and CSR launches): the union
     # of their intervals, so that assemblies running side by side count once
     asm_union_ms = 0.0
@@ -410,6 +415,7 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
     value = rows / (total_ms / 1e3)
 
     out = {"value": value, "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
+           "ms_per_step_with_host_readout": sum(host_ms) / steps,
            "config": {"workload": name, "N": N, "d": d, "n": n, "ell": ell, "m": m,
                       "deltas": list(deltas), "stab": "seq",
                       **({"boundary": f"{int((bcw[0] > 0).sum())} boundary rows (kind "

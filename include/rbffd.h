@@ -180,8 +180,8 @@ typedef struct {
  *   out     receives the plan.
  * Runs the exact kNN search and the retention balls on the device and waits for the
  * stream once (to size the local systems).  Each local system lives in one SM's shared
- * memory with q of its right-hand sides: with K = n + M, about 8 (K (K + 1) / 2 + K q + 7 K)
- * bytes (LU option: 8 K (K + q + 5)) must fit the device's per-block limit (227 KB on GB300).
+ * memory with q of its right-hand sides: with K = n + M, about 8 (K (K + 1) / 2 + K q + 6 K)
+ * bytes (LU option: 8 K (K + q + 4)) must fit the device's per-block limit (227 KB on GB300).
  * LU carries every column (q = the largest retention ball); LDL^T carries opts->rhs_chunk
  * columns and solves the rest in chunks of that many, so its limit is q = 1: in 3D,
  * n = 128 with degree 7 (K = 248) is too large.  Else RBFFD_EINVAL.  Errors: RBFFD_EINVAL,

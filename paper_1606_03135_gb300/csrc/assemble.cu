@@ -57,9 +57,9 @@ struct StencilSmem {
     double* X;
     int xs;
     double* xi;     // n x D scaled stencil coordinates
-    double* rdiag;  // K reciprocal pivots (LDL^T: 1x1 reciprocal or 2x2 inverse entry 00)
-    double* dinv1;  // K  LDL^T 2x2 inverse entry 01
-    double* dinv2;  // K  LDL^T 2x2 inverse entry 11
+    double* rdiag;  // K reciprocal pivots (LDL^T: 1x1 reciprocal; for a 2x2 block at rows p,
+                    //   p+1 the inverse's entry 00 at p and entry 11 at p+1)
+    double* dinv1;  // K  LDL^T 2x2 inverse entry 01 (at the block's first row)
     double* wv;     // K  unscaled pivot column(s) of the current LDL^T step
     double* wv2;    // K
     int* perm;      // K  original unknown held by each row (symmetric pivoting)
@@ -116,7 +116,7 @@ size_t solve_smem_per_cta(int n, int K, int qcap, int qmax, int D, int packed,
     if (stride_out) *stride_out = stride;
     const size_t mat = packed ? ((size_t)tri(K) + 1) / 2 * 2 + (size_t)K * stride
                               : (size_t)K * stride;
-    size_t b = mat * 8 + (size_t)n * D * 8 + (size_t)K * 5 * 8 + (size_t)qmax * 8 +
+    size_t b = mat * 8 + (size_t)n * D * 8 + (size_t)K * 4 * 8 + (size_t)qmax * 8 +
                (size_t)(qmax + n) * 4 + (size_t)K * 2 * 4 + (size_t)K + (size_t)qmax;
     return (b + 15) & ~size_t(15);
 }
@@ -144,8 +144,6 @@ __device__ __forceinline__ void carve(char* p, int n, int K, int qmax, int S, St
     sm.rdiag = reinterpret_cast<double*>(p);
     p += (size_t)K * 8;
     sm.dinv1 = reinterpret_cast<double*>(p);
-    p += (size_t)K * 8;
-    sm.dinv2 = reinterpret_cast<double*>(p);
     p += (size_t)K * 8;
     sm.wv = reinterpret_cast<double*>(p);
     p += (size_t)K * 8;
@@ -435,7 +433,7 @@ __device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem&
                     double* Bn = Bi + xs;
                     const double y0 = *Bi, y1 = *Bn;
                     *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
-                    *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
+                    *Bn = fma(sm.dinv1[i], y0, sm.rdiag[i + 1] * y1);
                 }
             }
             __syncwarp();
@@ -458,7 +456,7 @@ __device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem&
             double* Bn = Bi + xs;
             const double y0 = *Bi, y1 = *Bn;
             *Bi = fma(sm.rdiag[i], y0, sm.dinv1[i] * y1);
-            *Bn = fma(sm.dinv1[i], y0, sm.dinv2[i] * y1);
+            *Bn = fma(sm.dinv1[i], y0, sm.rdiag[i + 1] * y1);
         }
     }
     __syncthreads();
@@ -617,7 +615,7 @@ __device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
                     const double rdet = rcp_fixed(fma(d0, d2, -d1 * d1));
                     const double i00 = d2 * rdet, i01 = -d1 * rdet, i11 = d0 * rdet;
                     if (lane == 0) {
-                        sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.dinv2[p] = i11;
+                        sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.rdiag[p + 1] = i11;
                         sm.pk[p] = 2; sm.pk[p + 1] = 0;
                         T[tri(p + 1) + p] = 0.0;  // L has no entry inside a 2x2 pivot block
                         if (TRACK) {
