@@ -633,6 +633,7 @@ int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {
     a.max_ctas = p->opts.max_ctas;
     a.elastic = p->opts.elastic;
     a.rs = p->rs;
+    a.fma_r2 = p->rs == nullptr ? 1 : 0;
     a.rs_stride = p->rs_stride;
     a.rs_x0 = p->rs_x0;
     a.refine_min_K = p->refine_min_K;

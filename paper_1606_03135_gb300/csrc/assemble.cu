@@ -73,6 +73,24 @@ struct StencilSmem {
 
 __host__ __device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
 
+// Squared distance of two scaled stencil nodes inside a local system, with FMA:
+// fma(t_D, t_D, ... fma(t_1, t_1, t_0 t_0)), t_c = a_c - b_c (6 FP64 operations in 3D instead
+// of 8).  Symmetric in a and b (b - a = -(a - b) exactly).  Only the local systems of plans
+// that refine nothing use it (a.fma_r2): ill-conditioned systems amplify its different
+// rounding, so plans that refine keep sqdist_rn (no FMA, as the oracle forms it), and so do
+// the stencils, balls and every structural comparison.
+template <int D>
+__device__ __forceinline__ double sqdist_local(const double* a, const double* b) {
+    double t = __dsub_rn(a[0], b[0]);
+    double s = __dmul_rn(t, t);
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+        t = __dsub_rn(a[c], b[c]);
+        s = __fma_rn(t, t, s);
+    }
+    return s;
+}
+
 // Monomial basis tables in shared memory (built on the host in graded order):
 //   psi_l = psi_parent[l] * xi_var[l]            (l >= 1; psi_0 = 1)
 //   Laplacian psi_l = sum_a lap_coef[l][a] * psi_lap_child[l][a]
@@ -225,7 +243,8 @@ __device__ void assemble_local(const SolveArgs& a, const Shape& sh, int j, int q
             const int t = first ? off : off - len0;
             if (first || ra != pr) {
                 const int rb = ra + 1 + t;
-                const double r2 = sqdist_rn<D>(sm.xi + ra * D, sm.xi + rb * D);
+                const double r2 = a.fma_r2 ? sqdist_local<D>(sm.xi + ra * D, sm.xi + rb * D)
+                                           : sqdist_rn<D>(sm.xi + ra * D, sm.xi + rb * D);
                 const double r = sqrt_fast(r2);
                 double pm2 = r;
                 for (int s = 0; s < (m - 3) / 2; ++s) pm2 = __dmul_rn(pm2, r2);
@@ -715,12 +734,14 @@ __device__ __forceinline__ double mono_value(const Basis& bs, int l, const doubl
 // r^(m-2) (as in the pair loop) for a stencil node, the Laplacian of psi_(u-n) at node t for a
 // monomial.
 template <int D>
-__device__ __forceinline__ double rhs_entry(const Shape& sh, int u, int t, const StencilSmem& sm) {
+__device__ __forceinline__ double rhs_entry(const Shape& sh, int u, int t, const StencilSmem& sm,
+                                            bool fma_r2) {
     const int n = sh.n;
     double v = 0.0;
     if (u < n) {
         if (u != t) {
-            const double r2 = sqdist_rn<D>(sm.xi + u * D, sm.xi + t * D);
+            const double r2 = fma_r2 ? sqdist_local<D>(sm.xi + u * D, sm.xi + t * D)
+                                     : sqdist_rn<D>(sm.xi + u * D, sm.xi + t * D);
             double pm2 = sqrt_fast(r2);
             for (int k = 0; k < (sh.m - 3) / 2; ++k) pm2 = __dmul_rn(pm2, r2);
             v = __dmul_rn(sh.coef, pm2);
@@ -739,11 +760,11 @@ __device__ __forceinline__ double rhs_entry(const Shape& sh, int u, int t, const
 // Right-hand sides of columns c0 .. c0+qk-1 into sm.X, rows in the factorization's permuted
 // order (row r holds unknown perm[r]).
 template <int D, int NT>
-__device__ void chunk_rhs(const Shape& sh, int c0, int qk, const StencilSmem& sm) {
+__device__ void chunk_rhs(const Shape& sh, int c0, int qk, const StencilSmem& sm, bool fma_r2) {
     const int K = sh.K;
     for (int e = threadIdx.x; e < K * qk; e += NT) {
         const int r = e / qk, c = e - (e / qk) * qk;
-        sm.X[r * sm.xs + c] = rhs_entry<D>(sh, sm.perm[r], sm.cols[c0 + c], sm);
+        sm.X[r * sm.xs + c] = rhs_entry<D>(sh, sm.perm[r], sm.cols[c0 + c], sm, fma_r2);
     }
 }
 
@@ -864,7 +885,7 @@ __device__ void refine_columns(const SolveArgs& a, const Shape& sh, int c0, int 
     if (kind == 2) {
         for (int r = tid; r < K; r += NT) sm.X[r * xs] = neumann_value<D>(a, sh, i, sm.perm[r], sm);
     } else {
-        chunk_rhs<D, NT>(sh, c0, qk, sm);
+        chunk_rhs<D, NT>(sh, c0, qk, sm, a.fma_r2 != 0);
     }
     __syncthreads();
     for (int e = tid; e < K * qk * kRefineSegs; e += NT) {  // (unknown, column, segment) items
@@ -912,7 +933,7 @@ __device__ __forceinline__ void copy_full_matrix(int K, const StencilSmem& sm, d
 template <int D, int NT>
 __device__ __forceinline__ void solve_chunk(const SolveArgs& a, const Shape& sh, int c0, int qk,
                                             const StencilSmem& sm, int j) {
-    chunk_rhs<D, NT>(sh, c0, qk, sm);
+    chunk_rhs<D, NT>(sh, c0, qk, sm, a.fma_r2 != 0);
     __syncthreads();
     forward_subst<NT>(sh.K, qk, sm);
     ldlt_solve_tail<NT>(sh.K, qk, sm);

@@ -152,6 +152,8 @@ struct SolveArgs {
     int factor;                // RBFFD_FACTOR_LDLT (packed layout) or RBFFD_FACTOR_LU (full)
     int max_ctas;              // cap on the persistent grid (0 = fill the GPU)
     int elastic;               // > 0: a CTA holding no queue slot leaves when this many wait
+    int fma_r2;                // 1: squared distances of the local systems with FMA (plans
+                               // that refine nothing), 0: rounded like the oracle's
     // One step of iterative refinement of ill-conditioned LDL^T local solves, in plans whose
     // largest system has K >= refine_min_K: per-CTA scratch of rs_stride doubles at
     // rs + blockIdx.x rs_stride holding the assembled matrix in full (K x K) and, from offset
