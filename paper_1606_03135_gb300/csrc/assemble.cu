@@ -425,6 +425,90 @@ __device__ __forceinline__ void forward_subst_warp(int K, const StencilSmem& sm,
     }
 }
 
+// Blocked triangular solves of the columns 0 .. q-1 of sm.X with the whole team, 32 unknowns
+// at a time, for teams that hold one system per SM (512 threads): a warp solves a column's
+// diagonal block (lanes keep x in registers, each pivot's value by a shuffle), then every
+// thread updates the column's remaining rows with that block in pivot order.  On GB300 a warp
+// issues FP64 instructions to one quarter of the SM's FP64 units only, so a triangular solve
+// by a single warp runs at a quarter of the SM's rate; here the rows' updates spread over all
+// four.  Each entry receives the same FMAs in the same order as in the step-by-step forms
+// (forward_subst; the back substitution of ldlt_solve_tail), so results are bit-identical.
+
+// Forward substitution with the unit lower factor (a block never splits a 2x2 pivot).
+template <int NT>
+__device__ void forward_subst_blocked(int K, int q, const StencilSmem& sm) {
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int xs = sm.xs;
+    for (int b0 = 0; b0 < K;) {
+        int b1 = min(b0 + 32, K);
+        if (b1 < K && sm.pk[b1 - 1] == 2) --b1;
+        for (int c = wid; c < q; c += NW) {
+            double* Xc = sm.X + c;
+            const int i = b0 + lane;
+            double x = i < b1 ? Xc[i * xs] : 0.0;
+            for (int p = b0; p < b1;) {
+                const int k = sm.pk[p];
+                const double xp = __shfl_sync(0xffffffffu, x, p - b0);
+                const double xq = __shfl_sync(0xffffffffu, x, min(p + 1 - b0, 31));
+                if (i > p + k - 1 && i < b1) {
+                    const double* Ti = sm.T + tri(i);
+                    x = k == 1 ? fma(-Ti[p], xp, x) : fma(-Ti[p + 1], xq, fma(-Ti[p], xp, x));
+                }
+                p += k;
+            }
+            if (i < b1) Xc[i * xs] = x;
+        }
+        __syncthreads();
+        for (int e = tid; e < (K - b1) * q; e += NT) {
+            const int r = b1 + e / q, c = e - (e / q) * q;
+            const double* Tr = sm.T + tri(r);
+            const double* Xc = sm.X + c;
+            double xr = Xc[r * xs];
+            for (int p = b0; p < b1;) {
+                const int k = sm.pk[p];
+                xr = k == 1 ? fma(-Tr[p], Xc[p * xs], xr)
+                            : fma(-Tr[p + 1], Xc[(p + 1) * xs], fma(-Tr[p], Xc[p * xs], xr));
+                p += k;
+            }
+            sm.X[r * xs + c] = xr;
+        }
+        __syncthreads();
+        b0 = b1;
+    }
+}
+
+// Back substitution with L^T (after the D solve): x_j -= L[i][j] x_i for j < i, i descending.
+template <int NT>
+__device__ void back_subst_blocked(int K, int q, const StencilSmem& sm) {
+    constexpr int NW = NT / 32;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int xs = sm.xs;
+    for (int b1 = K; b1 > 0;) {
+        const int b0 = max(b1 - 32, 0);
+        for (int c = wid; c < q; c += NW) {
+            double* Xc = sm.X + c;
+            const int j = b0 + lane;
+            double x = j < b1 ? Xc[j * xs] : 0.0;
+            for (int i = b1 - 1; i > b0; --i) {
+                const double xi = __shfl_sync(0xffffffffu, x, i - b0);
+                if (j < i) x = fma(-sm.T[tri(i) + j], xi, x);
+            }
+            if (j < b1) Xc[j * xs] = x;
+        }
+        __syncthreads();
+        for (int e = tid; e < b0 * q; e += NT) {
+            const int r = e / q, c = e - (e / q) * q;
+            const double* Xc = sm.X + c;
+            double xr = Xc[r * xs];
+            for (int i = b1 - 1; i >= b0; --i) xr = fma(-sm.T[tri(i) + r], Xc[i * xs], xr);
+            sm.X[r * xs + c] = xr;
+        }
+        __syncthreads();
+        b1 = b0;
+    }
+}
+
 // D solve and back substitution of the right-hand-side columns 0 .. q-1 held in sm.X, after
 // the forward substitution (carried through the factorization, or forward_subst).
 template <int NT>
@@ -440,7 +524,7 @@ __device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem&
     // flattened (row, column) pairs keep the lanes busy) with a barrier per step.  Both do
     // the same operations on every element.
     constexpr int NW = NT / 32;
-    if (q <= NW) {
+    if (q <= NW && NT != 512) {
         if (wid < q) {
             double* Xc = X + wid;
             for (int i = lane; i < K; i += 32) {
@@ -479,6 +563,10 @@ __device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem&
         }
     }
     __syncthreads();
+    if constexpr (NT == 512) {
+        back_subst_blocked<NT>(K, q, sm);
+        return;
+    }
     for (int i = K - 1; i > 0; --i) {
         const int total = i * q;
         if (tid < total) {
@@ -516,188 +604,304 @@ constexpr int kRefinePivotLog2 = 16;  // refine systems whose pivots span at lea
 // Biased IEEE exponent of |v| (an integer-pipe floor(log2 |v|) + 1023).
 __device__ __forceinline__ int exp_bits(double v) { return (int)((abs_bits(v) >> 52) & 0x7ff); }
 
-template <int NT, bool TRACK = false>
-__device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
-    __shared__ int s_ok, s_kind;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+// One pivot step at p of the factorization below, by warp 0: the Bunch-Kaufman choice (1x1,
+// possibly after a symmetric swap, or 2x2), the reciprocal pivot or the 2x2 inverse, and the
+// scaled column(s) of L in place; the unscaled pivot column is kept in wb (a 1x1 step) or in
+// sm.wv and sm.wv2 (a 2x2 step) for the trailing update.  Lane 0 publishes s_ok and s_kind.
+__shared__ int s_ok, s_kind;
+
+template <bool TRACK>
+__device__ __forceinline__ void pivot_step(int K, int q, int p, const StencilSmem& sm, double* wb,
+                                           int& e_d, int& e_r) {
+    const int lane = threadIdx.x & 31;
     const int xs = sm.xs;
     double* T = sm.T;
     double* X = sm.X;
+    // The lane's first two entries of the pivot column and the reciprocal of the
+    // diagonal, in one straight-line block so the reciprocal's integer chain overlaps
+    // the loads and the search; the usual 1x1 step without a swap then scales these
+    // registers directly.
+    const double dpp = T[tri(p) + p];
+    const int i0 = p + 1 + lane, i1 = i0 + 32;
+    const double w0 = i0 < K ? T[tri(i0) + p] : 0.0;
+    const double w1 = i1 < K ? T[tri(i1) + p] : 0.0;
+    bool slow;
+    const double rcp_p = rcp_core(dpp, &slow);
+    // lambda = max |A[i][p]|, i > p, on magnitude keys (the top 32 bits of |A[i][p]|,
+    // an order-preserving truncation), lowest index among equal keys; two warp
+    // reductions instead of a shuffle tree
+    unsigned lk = 0u;
+    int r = 0x7fffffff;
+    {
+        const unsigned k0 = i0 < K ? mag_key(w0) : 0u;
+        const unsigned k1 = i1 < K ? mag_key(w1) : 0u;
+        if (k0 > lk) { lk = k0; r = i0; }
+        if (k1 > lk) { lk = k1; r = i1; }
+    }
+    for (int i = i1 + 32; i < K; i += 32) {  // columns longer than 64
+        const unsigned v = mag_key(T[tri(i) + p]);
+        if (v > lk) { lk = v; r = i; }
+    }
+    const unsigned lmax = __reduce_max_sync(0xffffffffu, lk);
+    r = (int)__reduce_min_sync(0xffffffffu,
+                               (lk == lmax && lmax != 0u) ? (unsigned)r : 0x7fffffffu);
+    const unsigned long long lv = (unsigned long long)lmax << 32;
+    // the pivot choice only has to be a valid Bunch-Kaufman choice, so the tests run in
+    // FP32 on values rebuilt from the FP64 bit patterns (no FP64 instructions)
+    const unsigned long long pv = abs_bits(dpp);
+    const float lam = approx_f32(lv), app = approx_f32(pv);
+    const float af = 0.6403882f;
+    int kind = 1, swap_a = p, swap_b = p;
+    bool ok = true;
+    if (lv == 0ull) {
+        ok = pv != 0ull;  // column already eliminated: 1x1 pivot if nonzero
+    } else if (!(app >= af * lam)) {
+        // sigma = max |A_rj| over the active part of row/column r, j != r
+        unsigned sk = 0u;
+        for (int jj = p + lane; jj < K; jj += 32) {
+            if (jj == r) continue;
+            const unsigned b = mag_key(jj < r ? T[tri(r) + jj] : T[tri(jj) + r]);
+            sk = b > sk ? b : sk;
+        }
+        sk = __reduce_max_sync(0xffffffffu, sk);
+        const float sig = approx_f32((unsigned long long)sk << 32),
+                    arr = approx_f32(abs_bits(T[tri(r) + r]));
+        if (app * sig >= af * lam * lam) {
+            kind = 1;
+        } else if (arr >= af * sig) {
+            kind = 1; swap_a = p; swap_b = r;
+        } else {
+            kind = 2; swap_a = p + 1; swap_b = r;
+        }
+    }
+    if (ok && swap_a != swap_b) {
+        // symmetric swap of unknowns ua < ub in the packed lower triangle, one uniform
+        // loop per segment (row parts left of ua, the part between, the columns below
+        // ub, the right-hand-side rows, the diagonal pair)
+        const int ua = swap_a, ub = swap_b;
+        auto exch = [](double* x, double* y) { const double t = *x; *x = *y; *y = t; };
+        for (int e = lane; e < ua; e += 32) exch(T + tri(ua) + e, T + tri(ub) + e);
+        for (int i = ua + 1 + lane; i < ub; i += 32) exch(T + tri(i) + ua, T + tri(ub) + i);
+        for (int i = ub + 1 + lane; i < K; i += 32) exch(T + tri(i) + ua, T + tri(i) + ub);
+        for (int c = lane; c < q; c += 32) exch(X + ua * xs + c, X + ub * xs + c);
+        if (lane == 0) {
+            exch(T + tri(ua) + ua, T + tri(ub) + ub);
+            const int t = sm.perm[ua]; sm.perm[ua] = sm.perm[ub]; sm.perm[ub] = t;
+        }
+        __syncwarp();
+    }
+    if (ok) {
+        if (kind == 1 && swap_a == swap_b && !slow) {  // the usual step: all in registers
+            if (lane == 0) { sm.rdiag[p] = rcp_p; sm.pk[p] = 1; }
+            if (TRACK && lane == 0) {
+                e_d = max(e_d, exp_bits(dpp));
+                e_r = max(e_r, exp_bits(rcp_p));
+            }
+            const double s0 = w0 * rcp_p, s1 = w1 * rcp_p;
+            if (i0 < K) { wb[i0] = w0; T[tri(i0) + p] = s0; }
+            if (i1 < K) { wb[i1] = w1; T[tri(i1) + p] = s1; }
+            for (int i = i1 + 32; i < K; i += 32) {
+                const double w = T[tri(i) + p];
+                wb[i] = w;
+                T[tri(i) + p] = w * rcp_p;
+            }
+        } else if (kind == 1) {  // after a swap (or an extreme pivot): reload
+            const double rcp = rcp_fixed(T[tri(p) + p]);
+            if (lane == 0) { sm.rdiag[p] = rcp; sm.pk[p] = 1; }
+            if (TRACK && lane == 0) {
+                e_d = max(e_d, exp_bits(T[tri(p) + p]));
+                e_r = max(e_r, exp_bits(rcp));
+            }
+            for (int i = p + 1 + lane; i < K; i += 32) {
+                const double w = T[tri(i) + p];
+                wb[i] = w;
+                T[tri(i) + p] = w * rcp;
+            }
+        } else {
+            const double d0 = T[tri(p) + p], d1 = T[tri(p + 1) + p], d2 = T[tri(p + 1) + p + 1];
+            const double rdet = rcp_fixed(fma(d0, d2, -d1 * d1));
+            const double i00 = d2 * rdet, i01 = -d1 * rdet, i11 = d0 * rdet;
+            if (lane == 0) {
+                sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.rdiag[p + 1] = i11;
+                sm.pk[p] = 2; sm.pk[p + 1] = 0;
+                T[tri(p + 1) + p] = 0.0;  // L has no entry inside a 2x2 pivot block
+                if (TRACK) {
+                    e_d = max(e_d, max(exp_bits(d0), max(exp_bits(d1), exp_bits(d2))));
+                    e_r = max(e_r, max(exp_bits(i00), max(exp_bits(i01), exp_bits(i11))));
+                }
+            }
+            for (int i = p + 2 + lane; i < K; i += 32) {
+                const double w1 = T[tri(i) + p], w2 = T[tri(i) + p + 1];
+                sm.wv[i] = w1;
+                sm.wv2[i] = w2;
+                T[tri(i) + p] = fma(w1, i00, w2 * i01);
+                T[tri(i) + p + 1] = fma(w1, i01, w2 * i11);
+            }
+        }
+    }
+    if (lane == 0) { s_ok = ok ? 1 : 0; s_kind = kind; }
+}
+
+// Trailing update after the pivot step at p (kind 1 or 2) by the threads U0 .. NT-1; wb holds a
+// 1x1 step's unscaled pivot column (sm.wv for a 2x2 step, with sm.wv2).
+template <int NT, int U0>
+__device__ __forceinline__ void trailing_update(int K, int q, int p, int kind, const StencilSmem& sm,
+                                                const double* wb, bool skip_next) {
+    constexpr int UT = NT - U0;
+    const int ut = (int)threadIdx.x - U0;
+    const int xs = sm.xs;
+    double* T = sm.T;
+    double* X = sm.X;
+    // Trailing update of the lower triangle and of the right-hand sides: row i (> p0)
+    // has (i - p0) triangle entries followed by q right-hand-side entries.  Rows r and
+    // rows-1-r are paired into one virtual row of constant length rows + 1 + 2q, so the
+    // flattened index steps in O(1).  The FP64 work is branch-free: source operands are
+    // selected with integer arithmetic so every lane issues the same FMA (a divergent
+    // FP64 instruction costs the whole warp on the FP64 pipe).
+    const int p0 = p + kind - 1;
+    const int rows = K - p0 - 1;
+    if (rows > 0) {
+        const int L2 = rows + 1 + 2 * q;
+        const int total = ((rows + 1) >> 1) * L2;
+        if (ut < total) {
+            int pr = ut / L2, off = ut - (ut / L2) * L2;
+            const int di = UT / L2, dj = UT - di * L2;
+            for (int e = ut; e < total; e += UT) {
+                const int len0 = pr + 1 + q;
+                const bool first = off < len0;
+                const int r = first ? pr : rows - 1 - pr;
+                const int t = first ? off : off - len0;
+                // an odd middle row pairs with itself: once only; with skip_next column p0 + 1 is
+                // left to warp 0
+                if ((first || r != pr) && (t != 0 || !skip_next)) {
+                    const int i = p0 + 1 + r;
+                    double* Ti = T + tri(i);
+                    const bool trin = t <= r;
+                    const int jj = p0 + 1 + t;      // triangle column
+                    const int c = t - (r + 1);      // right-hand-side column
+                    double* dst = trin ? Ti + jj : X + i * xs + c;
+                    const double* s1 = trin ? wb + jj : X + p * xs + c;
+                    if (kind == 1) {
+                        *dst = fma(-Ti[p], *s1, *dst);
+                    } else {
+                        const double* s2 = trin ? sm.wv2 + jj : X + (p + 1) * xs + c;
+                        *dst = fma(-Ti[p + 1], *s2, fma(-Ti[p], *s1, *dst));
+                    }
+                }
+                pr += di;
+                off += dj;
+                if (off >= L2) { off -= L2; ++pr; }
+            }
+        }
+    }
+}
+
+// Look-ahead of the next pivot for 512-thread teams (one system per SM, where nothing hides
+// the serial pivot step): while the other warps apply the 1x1 step at p, warp 0 applies it
+// to column pn = p + 1 (the FMA every entry of the trailing update gets) and tries the usual
+// next step there, a 1x1 pivot without a swap, which the column alone decides.  If it holds
+// (and the pivot is not extreme), the step is stored exactly as pivot_step would store it,
+// its unscaled column in wn (the other buffer: the update running now reads wc); otherwise
+// the updated column stays unscaled for pivot_step.  Results are bit-identical either way.
+template <bool TRACK>
+__device__ __forceinline__ bool lookahead_pivot(int K, int p, const StencilSmem& sm, const double* wc,
+                                                double* wn, int& e_d, int& e_r) {
+    const int lane = threadIdx.x & 31;
+    double* T = sm.T;
+    const int pn = p + 1;
+    const double f = wc[pn];
+    const double dpp = fma(-T[tri(pn) + p], f, T[tri(pn) + pn]);
+    const int i0 = pn + 1 + lane, i1 = i0 + 32;
+    const double w0 = i0 < K ? fma(-T[tri(i0) + p], f, T[tri(i0) + pn]) : 0.0;
+    const double w1 = i1 < K ? fma(-T[tri(i1) + p], f, T[tri(i1) + pn]) : 0.0;
+    bool slow;
+    const double rcp_p = rcp_core(dpp, &slow);
+    unsigned lk = 0u;
+    {
+        const unsigned k0 = i0 < K ? mag_key(w0) : 0u;
+        const unsigned k1 = i1 < K ? mag_key(w1) : 0u;
+        lk = k0 > k1 ? k0 : k1;
+    }
+    for (int i = i1 + 32; i < K; i += 32) {
+        const double w = fma(-T[tri(i) + p], f, T[tri(i) + pn]);
+        T[tri(i) + pn] = w;
+        const unsigned v = mag_key(w);
+        lk = v > lk ? v : lk;
+    }
+    const unsigned long long lv = (unsigned long long)__reduce_max_sync(0xffffffffu, lk) << 32;
+    const unsigned long long pv = abs_bits(dpp);
+    const float lam = approx_f32(lv), app = approx_f32(pv);
+    const float af = 0.6403882f;
+    const bool take = lv != 0ull && app >= af * lam && !slow;
+    if (lane == 0) T[tri(pn) + pn] = dpp;
+    if (take) {
+        if (lane == 0) { sm.rdiag[pn] = rcp_p; sm.pk[pn] = 1; }
+        if (TRACK && lane == 0) {
+            e_d = max(e_d, exp_bits(dpp));
+            e_r = max(e_r, exp_bits(rcp_p));
+        }
+        if (i0 < K) { wn[i0] = w0; T[tri(i0) + pn] = w0 * rcp_p; }
+        if (i1 < K) { wn[i1] = w1; T[tri(i1) + pn] = w1 * rcp_p; }
+        for (int i = i1 + 32; i < K; i += 32) {
+            const double w = T[tri(i) + pn];
+            wn[i] = w;
+            T[tri(i) + pn] = w * rcp_p;
+        }
+    } else {
+        if (i0 < K) T[tri(i0) + pn] = w0;
+        if (i1 < K) T[tri(i1) + pn] = w1;
+    }
+    return take;
+}
+
+template <int NT, bool TRACK = false>
+__device__ bool factor_solve_ldlt(int K, int q, const StencilSmem& sm) {
+    const int tid = threadIdx.x, wid = tid >> 5;
     int e_d = 0, e_r = 0;  // (thread 0, TRACK) largest exponents of |D| and |D^-1| entries
     for (int r = tid; r < K; r += NT) sm.perm[r] = r;
     __syncthreads();
     int p = 0;
-    while (p < K) {
-        if (wid == 0) {
-            // The lane's first two entries of the pivot column and the reciprocal of the
-            // diagonal, in one straight-line block so the reciprocal's integer chain overlaps
-            // the loads and the search; the usual 1x1 step without a swap then scales these
-            // registers directly.
-            const double dpp = T[tri(p) + p];
-            const int i0 = p + 1 + lane, i1 = i0 + 32;
-            const double w0 = i0 < K ? T[tri(i0) + p] : 0.0;
-            const double w1 = i1 < K ? T[tri(i1) + p] : 0.0;
-            bool slow;
-            const double rcp_p = rcp_core(dpp, &slow);
-            // lambda = max |A[i][p]|, i > p, on magnitude keys (the top 32 bits of |A[i][p]|,
-            // an order-preserving truncation), lowest index among equal keys; two warp
-            // reductions instead of a shuffle tree
-            unsigned lk = 0u;
-            int r = 0x7fffffff;
-            {
-                const unsigned k0 = i0 < K ? mag_key(w0) : 0u;
-                const unsigned k1 = i1 < K ? mag_key(w1) : 0u;
-                if (k0 > lk) { lk = k0; r = i0; }
-                if (k1 > lk) { lk = k1; r = i1; }
+    if constexpr (NT == 512) {
+        // Warp 0 looks one pivot ahead (lookahead_pivot) while warps 1-15 update; the 1x1
+        // steps alternate their unscaled column between sm.wv and sm.wv + K (= sm.wv2, which
+        // only 2x2 steps use otherwise), and the look-ahead's outcome alternates between two
+        // flags, so no flag or column is rewritten while another warp may still read it.
+        __shared__ int s_took[2];
+        int cur = 0, it = 0;
+        bool have_pivot = false;
+        while (p < K) {
+            if (!have_pivot) {
+                if (wid == 0) pivot_step<TRACK>(K, q, p, sm, sm.wv + cur * K, e_d, e_r);
+                __syncthreads();
+                if (!s_ok) return false;
             }
-            for (int i = i1 + 32; i < K; i += 32) {  // columns longer than 64
-                const unsigned v = mag_key(T[tri(i) + p]);
-                if (v > lk) { lk = v; r = i; }
-            }
-            const unsigned lmax = __reduce_max_sync(0xffffffffu, lk);
-            r = (int)__reduce_min_sync(0xffffffffu,
-                                       (lk == lmax && lmax != 0u) ? (unsigned)r : 0x7fffffffu);
-            const unsigned long long lv = (unsigned long long)lmax << 32;
-            // the pivot choice only has to be a valid Bunch-Kaufman choice, so the tests run in
-            // FP32 on values rebuilt from the FP64 bit patterns (no FP64 instructions)
-            const unsigned long long pv = abs_bits(dpp);
-            const float lam = approx_f32(lv), app = approx_f32(pv);
-            const float af = 0.6403882f;
-            int kind = 1, swap_a = p, swap_b = p;
-            bool ok = true;
-            if (lv == 0ull) {
-                ok = pv != 0ull;  // column already eliminated: 1x1 pivot if nonzero
-            } else if (!(app >= af * lam)) {
-                // sigma = max |A_rj| over the active part of row/column r, j != r
-                unsigned sk = 0u;
-                for (int jj = p + lane; jj < K; jj += 32) {
-                    if (jj == r) continue;
-                    const unsigned b = mag_key(jj < r ? T[tri(r) + jj] : T[tri(jj) + r]);
-                    sk = b > sk ? b : sk;
+            const int kind = have_pivot ? 1 : s_kind;
+            const double* wb = kind == 2 ? sm.wv : sm.wv + cur * K;
+            const bool look = kind == 1 && p + 1 < K;
+            if (wid == 0) {
+                if (look) {
+                    const bool took = lookahead_pivot<TRACK>(K, p, sm, wb, sm.wv + (cur ^ 1) * K, e_d, e_r);
+                    if ((tid & 31) == 0) s_took[it & 1] = took ? 1 : 0;
                 }
-                sk = __reduce_max_sync(0xffffffffu, sk);
-                const float sig = approx_f32((unsigned long long)sk << 32),
-                            arr = approx_f32(abs_bits(T[tri(r) + r]));
-                if (app * sig >= af * lam * lam) {
-                    kind = 1;
-                } else if (arr >= af * sig) {
-                    kind = 1; swap_a = p; swap_b = r;
-                } else {
-                    kind = 2; swap_a = p + 1; swap_b = r;
-                }
+            } else {
+                trailing_update<NT, 32>(K, q, p, kind, sm, wb, look);
             }
-            if (ok && swap_a != swap_b) {
-                // symmetric swap of unknowns ua < ub in the packed lower triangle, one uniform
-                // loop per segment (row parts left of ua, the part between, the columns below
-                // ub, the right-hand-side rows, the diagonal pair)
-                const int ua = swap_a, ub = swap_b;
-                auto exch = [](double* x, double* y) { const double t = *x; *x = *y; *y = t; };
-                for (int e = lane; e < ua; e += 32) exch(T + tri(ua) + e, T + tri(ub) + e);
-                for (int i = ua + 1 + lane; i < ub; i += 32) exch(T + tri(i) + ua, T + tri(ub) + i);
-                for (int i = ub + 1 + lane; i < K; i += 32) exch(T + tri(i) + ua, T + tri(i) + ub);
-                for (int c = lane; c < q; c += 32) exch(X + ua * xs + c, X + ub * xs + c);
-                if (lane == 0) {
-                    exch(T + tri(ua) + ua, T + tri(ub) + ub);
-                    const int t = sm.perm[ua]; sm.perm[ua] = sm.perm[ub]; sm.perm[ub] = t;
-                }
-                __syncwarp();
-            }
-            if (ok) {
-                if (kind == 1 && swap_a == swap_b && !slow) {  // the usual step: all in registers
-                    if (lane == 0) { sm.rdiag[p] = rcp_p; sm.pk[p] = 1; }
-                    if (TRACK && lane == 0) {
-                        e_d = max(e_d, exp_bits(dpp));
-                        e_r = max(e_r, exp_bits(rcp_p));
-                    }
-                    const double s0 = w0 * rcp_p, s1 = w1 * rcp_p;
-                    if (i0 < K) { sm.wv[i0] = w0; T[tri(i0) + p] = s0; }
-                    if (i1 < K) { sm.wv[i1] = w1; T[tri(i1) + p] = s1; }
-                    for (int i = i1 + 32; i < K; i += 32) {
-                        const double w = T[tri(i) + p];
-                        sm.wv[i] = w;
-                        T[tri(i) + p] = w * rcp_p;
-                    }
-                } else if (kind == 1) {  // after a swap (or an extreme pivot): reload
-                    const double rcp = rcp_fixed(T[tri(p) + p]);
-                    if (lane == 0) { sm.rdiag[p] = rcp; sm.pk[p] = 1; }
-                    if (TRACK && lane == 0) {
-                        e_d = max(e_d, exp_bits(T[tri(p) + p]));
-                        e_r = max(e_r, exp_bits(rcp));
-                    }
-                    for (int i = p + 1 + lane; i < K; i += 32) {
-                        const double w = T[tri(i) + p];
-                        sm.wv[i] = w;
-                        T[tri(i) + p] = w * rcp;
-                    }
-                } else {
-                    const double d0 = T[tri(p) + p], d1 = T[tri(p + 1) + p], d2 = T[tri(p + 1) + p + 1];
-                    const double rdet = rcp_fixed(fma(d0, d2, -d1 * d1));
-                    const double i00 = d2 * rdet, i01 = -d1 * rdet, i11 = d0 * rdet;
-                    if (lane == 0) {
-                        sm.rdiag[p] = i00; sm.dinv1[p] = i01; sm.rdiag[p + 1] = i11;
-                        sm.pk[p] = 2; sm.pk[p + 1] = 0;
-                        T[tri(p + 1) + p] = 0.0;  // L has no entry inside a 2x2 pivot block
-                        if (TRACK) {
-                            e_d = max(e_d, max(exp_bits(d0), max(exp_bits(d1), exp_bits(d2))));
-                            e_r = max(e_r, max(exp_bits(i00), max(exp_bits(i01), exp_bits(i11))));
-                        }
-                    }
-                    for (int i = p + 2 + lane; i < K; i += 32) {
-                        const double w1 = T[tri(i) + p], w2 = T[tri(i) + p + 1];
-                        sm.wv[i] = w1;
-                        sm.wv2[i] = w2;
-                        T[tri(i) + p] = fma(w1, i00, w2 * i01);
-                        T[tri(i) + p + 1] = fma(w1, i01, w2 * i11);
-                    }
-                }
-            }
-            if (lane == 0) { s_ok = ok ? 1 : 0; s_kind = kind; }
+            __syncthreads();
+            have_pivot = look && s_took[it & 1] != 0;
+            if (have_pivot) cur ^= 1;
+            ++it;
+            p += kind;
         }
-        __syncthreads();
-        if (!s_ok) return false;
-        const int kind = s_kind;
-        // Trailing update of the lower triangle and of the right-hand sides: row i (> p0)
-        // has (i - p0) triangle entries followed by q right-hand-side entries.  Rows r and
-        // rows-1-r are paired into one virtual row of constant length rows + 1 + 2q, so the
-        // flattened index steps in O(1).  The FP64 work is branch-free: source operands are
-        // selected with integer arithmetic so every lane issues the same FMA (a divergent
-        // FP64 instruction costs the whole warp on the FP64 pipe).
-        const int p0 = p + kind - 1;
-        const int rows = K - p0 - 1;
-        if (rows > 0) {
-            const int L2 = rows + 1 + 2 * q;
-            const int total = ((rows + 1) >> 1) * L2;
-            if (tid < total) {
-                int pr = tid / L2, off = tid - (tid / L2) * L2;
-                const int di = NT / L2, dj = NT - di * L2;
-                for (int e = tid; e < total; e += NT) {
-                    const int len0 = pr + 1 + q;
-                    const bool first = off < len0;
-                    const int r = first ? pr : rows - 1 - pr;
-                    const int t = first ? off : off - len0;
-                    if (first || r != pr) {  // an odd middle row pairs with itself: once only
-                        const int i = p0 + 1 + r;
-                        double* Ti = T + tri(i);
-                        const bool trin = t <= r;
-                        const int jj = p0 + 1 + t;      // triangle column
-                        const int c = t - (r + 1);      // right-hand-side column
-                        double* dst = trin ? Ti + jj : X + i * xs + c;
-                        const double* s1 = trin ? sm.wv + jj : X + p * xs + c;
-                        if (kind == 1) {
-                            *dst = fma(-Ti[p], *s1, *dst);
-                        } else {
-                            const double* s2 = trin ? sm.wv2 + jj : X + (p + 1) * xs + c;
-                            *dst = fma(-Ti[p + 1], *s2, fma(-Ti[p], *s1, *dst));
-                        }
-                    }
-                    pr += di;
-                    off += dj;
-                    if (off >= L2) { off -= L2; ++pr; }
-                }
-            }
+    } else {
+        while (p < K) {
+            if (wid == 0) pivot_step<TRACK>(K, q, p, sm, sm.wv, e_d, e_r);
+            __syncthreads();
+            if (!s_ok) return false;
+            const int kind = s_kind;
+            trailing_update<NT, 0>(K, q, p, kind, sm, sm.wv, false);
+            __syncthreads();
+            p += kind;
         }
-        __syncthreads();
-        p += kind;
     }
     // The inverse permutation (read after the caller's next barrier).
     for (int r = tid; r < K; r += NT) sm.rowof[sm.perm[r]] = r;
@@ -902,7 +1106,9 @@ __device__ void refine_columns(const SolveArgs& a, const Shape& sh, int c0, int 
         sm.X[r * xs + c] = sm.X[r * xs + c] - ((__ldcg(P) + __ldcg(P + st)) + (__ldcg(P + 2 * st) + __ldcg(P + 3 * st)));
     }
     __syncthreads();
-    if (qk <= NW) {  // forward substitution, a warp per column with warp synchronisation only
+    if (NT == 512) {  // forward substitution
+        forward_subst_blocked<NT>(K, qk, sm);
+    } else if (qk <= NW) {  // a warp per column with warp synchronisation only
         if (wid < qk) forward_subst_warp(K, sm, sm.X + wid, xs);
     } else {
         forward_subst<NT>(K, qk, sm);
@@ -935,7 +1141,8 @@ __device__ __forceinline__ void solve_chunk(const SolveArgs& a, const Shape& sh,
                                             const StencilSmem& sm, int j) {
     chunk_rhs<D, NT>(sh, c0, qk, sm, a.fma_r2 != 0);
     __syncthreads();
-    forward_subst<NT>(sh.K, qk, sm);
+    if constexpr (NT == 512) forward_subst_blocked<NT>(sh.K, qk, sm);
+    else forward_subst<NT>(sh.K, qk, sm);
     ldlt_solve_tail<NT>(sh.K, qk, sm);
     if constexpr (team_refines(NT)) {
         if (double* gA = refine_scratch<NT>(a))
