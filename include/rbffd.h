@@ -72,11 +72,12 @@ typedef struct {
                            concurrently on several streams share the GPU; 0 = fill the GPU */
     int team;           /* threads per stencil team: 0 = chosen from the shared-memory
                            footprint (96 for LDL^T, or 128 if that keeps more stencils
-                           resident, when more than 4 fit an SM; else 512), or
-                           32 (one warp per stencil), 64, 96, 128 or 512 to force one (used
-                           by the schedule autotuner); 32, 64 and 96 need RBFFD_FACTOR_LDLT,
-                           else RBFFD_EINVAL; 96 and 128 are refused for plans that refine
-                           (see refine) */
+                           resident, when more than 4 fit an SM and the plan does not
+                           refine; 256 when 2 to 4 fit, or more for a plan that refines;
+                           512 when one fits), or 32 (one warp per stencil), 64, 96, 128,
+                           256 or 512 to force one (used by the schedule autotuner); 32, 64,
+                           96 and 256 need RBFFD_FACTOR_LDLT, else RBFFD_EINVAL; 96 and 128
+                           are refused for plans that refine (see refine) */
     int rhs_chunk;      /* right-hand sides carried through one factorization (RBFFD_FACTOR_LDLT):
                            a center with more columns solves the rest afterwards, this many at
                            a time, with the stored factors (same results, bit for bit).  0 = all

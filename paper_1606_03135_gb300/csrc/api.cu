@@ -363,7 +363,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
     if (o.stab_mode < 0 || o.stab_mode > 2 || o.fault_inject < 0 || o.fault_inject > 1 ||
         (o.factor != RBFFD_FACTOR_LDLT && o.factor != RBFFD_FACTOR_LU) || o.max_ctas < 0 ||
         (o.team != 0 && o.team != 32 && o.team != 64 && o.team != 96 && o.team != 128 &&
-         o.team != 512) ||
+         o.team != 256 && o.team != 512) ||
         (o.factor == RBFFD_FACTOR_LU && o.team != 0 && o.team != 128 && o.team != 512) ||
         o.rhs_chunk < 0 || (o.factor == RBFFD_FACTOR_LU && o.rhs_chunk > 0) ||
         (o.lebesgue_ref != RBFFD_LREF_CENTER && o.lebesgue_ref != RBFFD_LREF_CENTROID) ||

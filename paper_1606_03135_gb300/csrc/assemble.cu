@@ -37,14 +37,17 @@ namespace rbffd {
 
 constexpr int kNT = 128;     // default stencil team: one warp per SM sub-partition
 constexpr int kMaxNT = 512;  // largest team (big systems, when few fit in shared memory)
+constexpr int kMidNT = 256;  // fallback solves with two to four systems per SM
 // Device code is compiled for a team size NT of 128 (small systems, many per SM) or 512
 // (large systems, one or a few per SM); the LDL^T traversal also for 96, 64 and 32 (one warp
-// per stencil).  The host picks the instantiation per launch.
+// per stencil), the fallback solves also for 256 (two to four systems per SM).  The host
+// picks the instantiation per launch.
 
 // CTAs per SM the register allocation must allow for a team size (the shared-memory limit of
-// small systems): 40 registers for 96- and 128-thread teams, 64 for 32- and 64-thread teams.
+// small systems): 40 registers for 96- and 128-thread teams, 64 for 32-, 64- and 256-thread
+// teams.
 __host__ __device__ constexpr int team_min_blocks(int nt) {
-    return nt == 32 ? 32 : (nt == 64 ? 16 : (nt == 96 ? 16 : (nt == 128 ? 12 : 1)));
+    return nt == 32 ? 32 : (nt == 64 ? 16 : (nt == 96 ? 16 : (nt == 128 ? 12 : (nt == 256 ? 4 : 1))));
 }
 
 // Per-CTA shared-memory views of one local system.  Two layouts:
@@ -1818,6 +1821,7 @@ static const void* traversal_kernel(int nt) {
             case 64: if constexpr (PACKED) return (const void*)k_traversal<D, PACKED, 64, CH>; break;
             case 96: if constexpr (PACKED) return (const void*)k_traversal<D, PACKED, 96, CH>; break;
             case kNT: return (const void*)k_traversal<D, PACKED, kNT, CH>;
+            case kMidNT: if constexpr (PACKED) return (const void*)k_traversal<D, PACKED, kMidNT, CH>; break;
             case kMaxNT: return (const void*)k_traversal<D, PACKED, kMaxNT, CH>;
             default: break;
         }
@@ -1842,6 +1846,9 @@ static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
     *per_sm = 0;
     const void* k = nt == kMaxNT ? (const void*)k_fallback_solve<D, PACKED, kMaxNT>
                                  : (const void*)k_fallback_solve<D, PACKED, kNT>;
+    if constexpr (PACKED) {
+        if (nt == kMidNT) k = (const void*)k_fallback_solve<D, PACKED, kMidNT>;
+    }
     if (RB_CUDA(allow_max_smem(k)) ||
         RB_CUDA(occupancy(per_sm, k, nt, smem)) || *per_sm < 1)
         return RBFFD_EINVAL;
@@ -1855,7 +1862,7 @@ static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
 // 13 columns: 13 stencils of 96 threads beat 12 of 128 by 7%), and at equal residency the
 // smaller team wastes fewer lanes in its short steps (2D, 21 columns: 1.11 against 1.17 ms;
 // 3D, K = 65, one column: 15.5 against 15.7 ms).  A
-// forced size (32, 64 and 96 exist for the LDL^T traversal only) is taken as given.
+// forced size (32, 64, 96 and 256 exist for LDL^T only) is taken as given.
 template <int D, bool PACKED, bool TRAVERSAL>
 static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool chunked = false,
                      bool refined = false) {
@@ -1869,8 +1876,14 @@ static int pick_team(size_t smem, int force, int* nt_out, int* per_sm_out, bool 
         int per_sm = 0;
         if ((rc = occ(kNT, &per_sm))) return rc;
         // The fallback's one-column systems hide each other's serial pivot steps when two or
-        // more share an SM (512-thread teams run one per SM: their registers fill it).
-        nt = TRAVERSAL ? ((per_sm <= 4 || refined) ? kMaxNT : kNT) : (per_sm <= 1 ? kMaxNT : kNT);
+        // more share an SM (512-thread teams run one per SM: their registers fill it); two to
+        // four per SM take 256-thread teams (mixed cube, K = 106, four per SM: 315 -> 302 ms
+        // of fallback solves against 128-thread teams).
+        // 256-thread teams exist for LDL^T only; their 64 registers let four share an SM,
+        // where the 512-thread teams' registers allow one.
+        const int mid = PACKED ? kMidNT : kMaxNT;
+        nt = TRAVERSAL ? (per_sm <= 1 ? kMaxNT : ((per_sm <= 4 || refined) ? mid : kNT))
+                       : (per_sm <= 1 ? kMaxNT : (per_sm <= 4 ? mid : kNT));
         if (TRAVERSAL && PACKED && nt == kNT) {
             int p96 = 0;
             if ((rc = occ(96, &p96))) return rc;
@@ -1971,6 +1984,13 @@ int launch_traversal(int D, const SolveArgs& a, const LaunchPlan& lp, const int*
 }
 
 template <int D, bool PACKED>
+static void launch_fallback_mid(const SolveArgs& af, const FallbackClass& f, int basis_bytes,
+                                cudaStream_t s) {
+    if constexpr (PACKED)
+        k_fallback_solve<D, PACKED, kMidNT><<<f.grid, kMidNT, f.smem, s>>>(af, f.cls, f.n, f.K, f.xs, basis_bytes);
+}
+
+template <int D, bool PACKED>
 static int fallback(const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s, int* launches) {
     const int tb = 256, nb = (a.N + tb - 1) / tb;
     if (a.mode == RBFFD_STAB_FALLBACK) {  // rows that failed the test (boundary rows are queued)
@@ -1985,6 +2005,8 @@ static int fallback(const SolveArgs& a, const LaunchPlan& lp, cudaStream_t s, in
         af.rs_x0 = f.rs_x0;
         if (f.nt == kMaxNT)
             k_fallback_solve<D, PACKED, kMaxNT><<<f.grid, kMaxNT, f.smem, s>>>(af, f.cls, f.n, f.K, f.xs, basis_bytes);
+        else if (PACKED && f.nt == kMidNT)
+            launch_fallback_mid<D, PACKED>(af, f, basis_bytes, s);
         else
             k_fallback_solve<D, PACKED, kNT><<<f.grid, kNT, f.smem, s>>>(af, f.cls, f.n, f.K, f.xs, basis_bytes);
         ++*launches;

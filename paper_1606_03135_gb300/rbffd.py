@@ -387,7 +387,7 @@ def autotune(nodes, n, ell, m, delta, mode=STAB_SEQ, candidates=None, repeats=2)
     import torch
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     if candidates is None:
-        candidates = [dict(team=t) for t in (32, 64, 96, 128, 512)]
+        candidates = [dict(team=t) for t in (32, 64, 96, 128, 256, 512)]
         candidates += [dict(team=0, max_ctas=c) for c in (0, 4 * sms)]
         if np.ndim(n) == 0:
             with Plan(nodes, n, ell, m, delta, mode=mode) as p:
