@@ -307,6 +307,7 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
     # traversal's dependency tail leave (rbffd_opts.elastic) so the next delta's kernel fills
     # their SMs
     conc = getattr(args, "concurrent_deltas", False)
+    fresh = getattr(args, "fresh_plans", False)  # every delta runs its own kNN
     asm_streams = [torch.cuda.Stream(dev) for _ in deltas] if conc else [stream] * len(deltas)
     elastic = args.elastic if conc else 0
     # Schedule per delta (team size, grid cap, right-hand sides per factorization), chosen by
@@ -324,13 +325,18 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
         # on a side stream, so it runs while the previous delta assembles and the host's wait
         # for its sizing covers only its own stencils; the assemblies run in order on the
         # compute stream.
+        # The kNN stencils do not depend on delta (§4.1): the first delta's plan searches them
+        # and the others copy them from it (rbffd_plan_delta), recomputing only their balls.
         launches = 0
         d2h = 0
         plans, sts = [], []
         plan_stream.wait_stream(stream)  # (after the step's start event)
         for k, delta in enumerate(deltas):
-            p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta, sync=False,
-                       stream=plan_stream, elastic=elastic, **sched[delta])
+            kw = dict(sync=False, stream=plan_stream, elastic=elastic, **sched[delta])
+            if k == 0 or fresh:
+                p = R.Plan(Xd if nodes is None else nodes, n, ell, m, delta, **kw)
+            else:
+                p = plans[0][1].with_delta(delta, **kw)
             if bcw is not None:  # boundary rows and the time-stepping matrix of §5
                 p.set_boundary(*bcw)
             s_k = asm_streams[k]
@@ -422,7 +428,11 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
                                       f"{int(bcw[0].max())}) + time-stepping matrix c="
                                       f"{w['timestep_c']:.3g}"} if bcw is not None else {}),
                       "l2": "flushed between timed steps (256 MB write)",
-                      "plans": "built on a side stream beside the previous delta's assembly "
+                      "plans": ("each delta's own kNN" if fresh else
+                                "one kNN per step: the first delta's plan searches the stencils, "
+                                "the others copy them and recompute their balls "
+                                "(rbffd_plan_delta)") +
+                               "; built on a side stream beside the previous delta's assembly "
                                "(per_delta ms_stencils of later deltas include that overlap)",
                       "schedule": ({str(k): v for k, v in sched.items()}
                                    if not args.no_autotune else "library default"),
@@ -446,7 +456,7 @@ def run_sweep(args, name, dev, world=1, e2e=True, steps=None, warmup=None):
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         out["e2e"] = {"value": N * len(deltas) * e2e_steps * world / e2e_s, "unit": UNIT,
-                      "h2d_bytes_per_step": int(X.nbytes * len(deltas)),
+                      "h2d_bytes_per_step": int(X.nbytes * (len(deltas) if fresh else 1)),
                       "d2h_bytes_per_step": int(d2h)}
 
     # the traversal kernels' device time: their own events when they run one after another,
@@ -749,6 +759,9 @@ def main(argv=None):
     ap.add_argument("--elastic", type=int, default=152,
                     help="waiting CTAs beyond which a traversal CTA leaves (with "
                          "--concurrent-deltas)")
+    ap.add_argument("--fresh-plans", action="store_true",
+                    help="every delta of a sweep runs its own kNN instead of copying the first "
+                         "delta's stencils")
     ap.add_argument("--jobs", type=int, default=256, help="serving trace length")
     ap.add_argument("--slots", type=int, default=4, help="serving slots (streams)")
     args = ap.parse_args(argv)

@@ -201,6 +201,22 @@ int rbffd_plan_mixed(const double* nodes, int64_t N, int d, const int32_t* n_nod
                      const int32_t* ell_node, const int32_t* m_node, double delta,
                      const rbffd_opts* opts, void* stream, rbffd_plan_t* out);
 
+/* rbffd_plan_delta -- a plan for the node set, stencil sizes, degrees and PHS exponents of
+ * base (built by rbffd_plan or rbffd_plan_mixed) with another overlap parameter delta (§4.1)
+ * and options opts (NULL for defaults).  The kNN stencils and widths do not depend on delta,
+ * so they are copied from base on the device instead of searched again; the retention balls
+ * (closed, radius (1 - delta) rho_k, squared distances formed as rbffd_plan forms them) and the
+ * traversal's in-degrees are recomputed.  The result is the plan rbffd_plan would build for
+ * these arguments: the same stencils, balls and, after rbffd_assemble, the same matrix bit for
+ * bit.  base's stencils are complete when rbffd_plan returns, so base may be assembling on
+ * another stream meanwhile; it must stay alive until this call returns and may be destroyed
+ * after it (the copies are done by then).  Boundary nodes (rbffd_set_boundary) are not
+ * carried over.  Like rbffd_plan, waits for the stream once; for a per-node plan it also
+ * copies the per-node parameters back to the host first.  Errors: RBFFD_EINVAL (base or out
+ * NULL, delta outside (0, 1], bad opts), RBFFD_ENOMEM, RBFFD_ECUDA.  On error *out is NULL. */
+int rbffd_plan_delta(rbffd_plan_t base, double delta, const rbffd_opts* opts, void* stream,
+                     rbffd_plan_t* out);
+
 /* rbffd_assemble -- the traversal of §4.1 with the stabilization of §4.2.1: greedy center
  * selection, one factorization per center, multi-right-hand-side solves, Lebesgue test
  * and scatter into CSR (owned by the plan, described through *out, which may be NULL).

@@ -328,11 +328,13 @@ const char* rbffd_strerror(int code) {
 
 namespace {
 
-// Shared by rbffd_plan (uniform n, ell, m: n_node == NULL) and rbffd_plan_mixed (per-node
-// host arrays; n is then the largest stencil size).
+// Shared by rbffd_plan (uniform n, ell, m: n_node == NULL), rbffd_plan_mixed (per-node
+// host arrays; n is then the largest stencil size) and rbffd_plan_delta (like: the plan whose
+// nodes and stencils the new one copies instead of running the kNN; nodes is then like->X).
 int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
               const int32_t* n_node, const int32_t* ell_node, const int32_t* m_node,
-              double delta, const rbffd_opts* opts, void* stream, rbffd_plan_t* out) {
+              double delta, const rbffd_opts* opts, void* stream, rbffd_plan_t* out,
+              const rbffd_plan_s* like = nullptr) {
     if (!out) return RBFFD_EINVAL;
     *out = nullptr;
     if (!nodes || (d != 2 && d != 3) || n < 1 || n > kMaxStencil || N < n || N > 0x7ffffffeLL ||
@@ -436,10 +438,10 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         delete[] tmp;
         if (rc) goto fail;
     }
-    if ((rc = pool_alloc(&scratch, sbytes, p->device, s))) goto fail;
+    if (!like && (rc = pool_alloc(&scratch, sbytes, p->device, s))) goto fail;
     if ((rc = bad(cudaMemcpyAsync(p->X, nodes, (size_t)N * d * sizeof(double),
-                                  o.nodes_on_host ? cudaMemcpyHostToDevice
-                                                  : cudaMemcpyDeviceToDevice,
+                                  (o.nodes_on_host && !like) ? cudaMemcpyHostToDevice
+                                                             : cudaMemcpyDeviceToDevice,
                                   s))))
         goto fail;
     if ((rc = bad(cudaMemcpyAsync(p->basis, h_basis, basis_count * sizeof(short),
@@ -447,9 +449,19 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         (rc = bad(cudaMemsetAsync(p->ctr, 0, sizeof(DevCounters), s))))
         goto fail;
     cudaEventRecord(p->ev[0], s);
-    rc = launch_grid_and_knn(d, p->X, Ni, n, (1.0 - delta) * (1.0 - delta), scratch, sbytes,
-                             ncell_max, p->nbr, p->rho2, p->ball_len, p->indeg, p->node_n,
-                             p->ctr, s, &p->launches);
+    if (like) {  // the same nodes and stencil sizes: the same kNN; only the balls change
+        if ((rc = bad(cudaMemcpyAsync(p->nbr, like->nbr, (size_t)N * n * sizeof(int),
+                                      cudaMemcpyDeviceToDevice, s))) ||
+            (rc = bad(cudaMemcpyAsync(p->rho2, like->rho2, (size_t)N * sizeof(double),
+                                      cudaMemcpyDeviceToDevice, s))))
+            goto fail;
+        rc = launch_balls(d, p->X, Ni, n, (1.0 - delta) * (1.0 - delta), p->nbr, p->rho2,
+                          p->node_n, p->ball_len, p->indeg, p->ctr, s, &p->launches);
+    } else {
+        rc = launch_grid_and_knn(d, p->X, Ni, n, (1.0 - delta) * (1.0 - delta), scratch, sbytes,
+                                 ncell_max, p->nbr, p->rho2, p->ball_len, p->indeg, p->node_n,
+                                 p->ctr, s, &p->launches);
+    }
     if (rc) goto fail;
     rc = launch_scan_i32_to_i64(p->ball_len, p->slot_off, Ni, s, &p->launches);
     if (rc) goto fail;
@@ -458,7 +470,7 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
         if (rc) goto fail;
     }
     cudaEventRecord(p->ev[1], s);
-    cudaFreeAsync(scratch, s);
+    if (scratch) cudaFreeAsync(scratch, s);
     scratch = nullptr;
     {
         long long slots = 0;  // pageable copies: each returns once the stream has reached it
@@ -577,6 +589,32 @@ int rbffd_plan_mixed(const double* nodes, int64_t N, int d, const int32_t* n_nod
     for (int64_t k = 0; k < N; ++k) n_max = n_node[k] > n_max ? n_node[k] : n_max;
     return plan_impl(nodes, N, d, n_max, 0, 3, n_node, ell_node, m_node, delta, opts, stream,
                      out);
+}
+
+int rbffd_plan_delta(rbffd_plan_t base, double delta, const rbffd_opts* opts, void* stream,
+                     rbffd_plan_t* out) {
+    NvtxRange r("rbffd_plan_delta");
+    if (!out) return RBFFD_EINVAL;
+    *out = nullptr;
+    if (!base) return RBFFD_EINVAL;
+    if (!base->mixed)
+        return plan_impl(base->X, base->N, base->d, base->n, base->ell, base->m, nullptr,
+                         nullptr, nullptr, delta, opts, stream, out, base);
+    // per-node parameters back from the base plan's device copies (host arrays for the checks
+    // and the fallback classes, as rbffd_plan_mixed takes them)
+    const size_t N = (size_t)base->N;
+    std::vector<int32_t> nn(N), ll(N), mm(N);
+    std::vector<signed char> t8(2 * N);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc;
+    if ((rc = bad(cudaMemcpyAsync(nn.data(), base->node_n, N * sizeof(int), cudaMemcpyDeviceToHost, s))) ||
+        (rc = bad(cudaMemcpyAsync(t8.data(), base->node_ell, N, cudaMemcpyDeviceToHost, s))) ||
+        (rc = bad(cudaMemcpyAsync(t8.data() + N, base->node_m, N, cudaMemcpyDeviceToHost, s))) ||
+        (rc = bad(cudaStreamSynchronize(s))))
+        return rc;
+    for (size_t k = 0; k < N; ++k) { ll[k] = t8[k]; mm[k] = t8[N + k]; }
+    return plan_impl(base->X, base->N, base->d, base->n, 0, 3, nn.data(), ll.data(), mm.data(),
+                     delta, opts, stream, out, base);
 }
 
 int rbffd_assemble(rbffd_plan_t p, void* stream, rbffd_csr* out) {

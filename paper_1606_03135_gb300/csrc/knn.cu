@@ -522,6 +522,48 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
     }
 }
 
+// Retention balls and traversal in-degrees of another delta from a plan's stencils (§4.1):
+// node q's closed ball of radius (1 - delta) rho_q is the prefix of its neighbour list with
+// d^2 <= (1 - delta)^2 rho_q^2, d^2 formed exactly as k_knn forms it (sqdist_rn of the same
+// coordinates, query first), so the balls equal the ones a new kNN pass would give.  One
+// warp per node; indeg must be zero on entry.
+template <int D>
+__global__ void __launch_bounds__(256) k_balls(const double* __restrict__ X, int N, int n,
+                                               double omd2, const int* __restrict__ nbr,
+                                               const double* __restrict__ rho2,
+                                               const int* __restrict__ node_n,
+                                               int* __restrict__ ball_len, int* __restrict__ indeg,
+                                               DevCounters* ctr) {
+    const int lane = threadIdx.x & 31;
+    const long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= N) return;  // (whole warps)
+    double xq[3];
+    for (int a = 0; a < D; ++a) xq[a] = X[q * D + a];
+    const int nq = node_n ? node_n[q] : n;
+    const double rball = __dmul_rn(omd2, rho2[q]);
+    const int* nb = nbr + q * n;
+    int blen = 0;
+    for (int t0 = 0; t0 < nq; t0 += 32) {
+        const int t = t0 + lane;
+        bool inb = false;
+        if (t < nq) {
+            const int id = nb[t];
+            double xp[3];
+            for (int a = 0; a < D; ++a) xp[a] = X[(size_t)id * D + a];
+            inb = sqdist_rn<D>(xq, xp) <= rball;
+        }
+        blen += __popc(__ballot_sync(0xffffffffu, inb));
+    }
+    if (lane == 0) {
+        ball_len[q] = blen;
+        atomicMax(&ctr->max_ball, blen);
+    }
+    for (int t = 1 + lane; t < blen; t += 32) {
+        const int i = nb[t];
+        if (i > q) atomicAdd(&indeg[i], 1);
+    }
+}
+
 // ------------------------------------------------------------------ launcher
 // Every piece carved from the scratch buffer starts on a 256-byte boundary.
 static size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -592,6 +634,19 @@ int launch_grid_and_knn(int D, const double* X, int N, int n, double omd2, void*
                                node_n, ctr, s, launches);
     return grid_and_knn<3>(X, N, n, omd2, scratch, ncell_max, nbr, rho2, ball_len, indeg, node_n,
                            ctr, s, launches);
+}
+
+int launch_balls(int D, const double* X, int N, int n, double omd2, const int* nbr,
+                 const double* rho2, const int* node_n, int* ball_len, int* indeg,
+                 DevCounters* ctr, cudaStream_t s, int* launches) {
+    int rc = RB_CUDA(cudaMemsetAsync(indeg, 0, (size_t)N * sizeof(int), s));
+    if (rc) return rc;
+    const int tb = 256;
+    const unsigned nb = (unsigned)(((size_t)N * 32 + tb - 1) / tb);
+    if (D == 2) k_balls<2><<<nb, tb, 0, s>>>(X, N, n, omd2, nbr, rho2, node_n, ball_len, indeg, ctr);
+    else k_balls<3><<<nb, tb, 0, s>>>(X, N, n, omd2, nbr, rho2, node_n, ball_len, indeg, ctr);
+    ++*launches;
+    return RB_LAUNCHED(__func__);
 }
 
 }  // namespace rbffd

@@ -118,6 +118,11 @@ int launch_grid_and_knn(int D, const double* X, int N, int n, double omd2, void*
                         int* indeg, const int* node_n, DevCounters* ctr, cudaStream_t s,
                         int* launches);
 size_t grid_scratch_bytes(int N, int D, int ncell_max);
+// Retention balls, in-degrees and max_ball (ctr) of another delta from an existing plan's
+// stencils nbr / rho2 (k_balls).
+int launch_balls(int D, const double* X, int N, int n, double omd2, const int* nbr,
+                 const double* rho2, const int* node_n, int* ball_len, int* indeg,
+                 DevCounters* ctr, cudaStream_t s, int* launches);
 
 int launch_scan_i32_to_i64(const int* in, long long* out, int count, cudaStream_t s,
                            int* launches);

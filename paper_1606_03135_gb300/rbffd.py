@@ -62,6 +62,8 @@ _SIGS = {
     "rbffd_plan_mixed": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_double, C.POINTER(rbffd_opts), C.c_void_p,
                                    C.POINTER(C.c_void_p)]),
+    "rbffd_plan_delta": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(rbffd_opts), C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
     "rbffd_assemble": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(rbffd_csr)]),
     "rbffd_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbffd_set_boundary": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -126,6 +128,13 @@ def rbffd_plan_mixed(nodes_ptr, N, d, n_node, ell_node, m_node, delta, opts=None
     out = C.c_void_p()
     rc = load().rbffd_plan_mixed(nodes_ptr, N, d, _p(n_node), _p(ell_node), _p(m_node),
                                  float(delta), C.byref(opts) if opts is not None else None,
+                                 stream, C.byref(out))
+    return rc, out
+
+
+def rbffd_plan_delta(base, delta, opts=None, stream=None):
+    out = C.c_void_p()
+    rc = load().rbffd_plan_delta(base, float(delta), C.byref(opts) if opts is not None else None,
                                  stream, C.byref(out))
     return rc, out
 
@@ -222,6 +231,28 @@ class Plan:
                                         delta, opts, _stream_handle(stream))
             _check(rc, "rbffd_plan_mixed")
         self._plan = plan
+
+    def with_delta(self, delta, mode=STAB_SEQ, timeout_ms=5000, sync=True, stream=None,
+                   fault_inject=0, factor=FACTOR_LDLT, max_ctas=0, team=0, rhs_chunk=0,
+                   lebesgue_ref=0, refine=REFINE_AUTO, elastic=0):
+        """A plan for this plan's nodes and stencil parameters at another delta
+        (``rbffd_plan_delta``): the kNN stencils are copied from this plan on the device and
+        only the retention balls are recomputed; the result equals a new ``Plan`` with these
+        arguments.  This plan may be closed once the call returns."""
+        q = Plan.__new__(Plan)
+        q._plan = None
+        q._stream = stream
+        q._nodes = self._nodes
+        q.N, q.d, q.n, q.ell, q.m = self.N, self.d, self.n, self.ell, self.m
+        if hasattr(self, "_node_params"):
+            q._node_params = self._node_params
+        q.delta, q.mode, q.sync = delta, mode, bool(sync)
+        opts = rbffd_opts(mode, 0, timeout_ms, 1 if sync else 0, fault_inject, factor, max_ctas,
+                          team, rhs_chunk, lebesgue_ref, refine, elastic)
+        rc, plan = rbffd_plan_delta(self._plan, delta, opts, _stream_handle(stream))
+        _check(rc, "rbffd_plan_delta")
+        q._plan = plan
+        return q
 
     def assemble(self, stream=None):
         """Form L on the device (``rbffd_assemble``).  `stream` (a torch CUDA stream) moves the

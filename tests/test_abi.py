@@ -40,12 +40,15 @@ def test_strerror_and_argument_checks_need_no_gpu():
     assert R.rbffd_plan(dummy, 100, 2, 5, 2, 3, 0.5)[0] == R.EINVAL     # n < M
     assert R.rbffd_plan(dummy, 1000, 2, 129, 2, 3, 0.5)[0] == R.EINVAL  # n too large
     assert R.rbffd_assemble(None)[0] == R.EINVAL
+    assert R.rbffd_plan_delta(None, 0.5)[0] == R.EINVAL                 # no base plan
     assert R.rbffd_apply(None, None, None) == R.EINVAL
-    # team sizes: 32, 64, 96, 128, 512 or 0; teams below 128 only for LDL^T
+    # team sizes: 32, 64, 96, 128, 256, 512 or 0; 32, 64, 96 and 256 only for LDL^T
     bad_team = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LDLT, 0, 48)
     assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, bad_team)[0] == R.EINVAL
     lu_warp = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LU, 0, 32)
     assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, lu_warp)[0] == R.EINVAL
+    lu_256 = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LU, 0, 256)
+    assert R.rbffd_plan(dummy, 1000, 2, 12, 2, 3, 0.5, lu_256)[0] == R.EINVAL
     assert R.load().rbffd_set_boundary(None, None, None) == R.EINVAL
     assert R.load().rbffd_timestep_matrix(None, 0.5, None, None) == R.EINVAL
     assert R.rbffd_export_async(None, None, None, None, None, None) == R.EINVAL
