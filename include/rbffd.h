@@ -251,9 +251,10 @@ int rbffd_export_async(rbffd_plan_t plan, int64_t* row_ptr, int32_t* col, double
                        int32_t* owner, void* stream);
 
 /* rbffd_export_stencils -- copy the kNN stencils to host memory: nbr [N][n] (nbr[k][0] ==
- * k, ordered by (squared distance, index); n is the largest stencil size of the plan), rho2
- * [N] (squared stencil width), ball_len [N]
- * (retention-ball size; the ball is the prefix nbr[k][0..ball_len)).  NULL skips. */
+ * k, ordered by (squared distance, index); n is the largest stencil size of the plan; for
+ * rbffd_plan_mixed row k holds node k's n_k nearest and -1 after them), rho2 [N] (squared
+ * stencil width), ball_len [N] (retention-ball size; the ball is the prefix
+ * nbr[k][0..ball_len)).  NULL skips. */
 int rbffd_export_stencils(rbffd_plan_t plan, int32_t* nbr, double* rho2, int32_t* ball_len);
 
 /* rbffd_export_lambda -- scaled local Lebesgue value of every row under the stencil that

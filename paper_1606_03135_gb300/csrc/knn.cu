@@ -398,7 +398,10 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
             c0[a] = cell_coord<D>(g, xq[a], a);
         }
         const int kCollect = knn_collect_cap(n);
-        int r = first_ring<D>(g, c0, n, cell_start), cnt = 0;
+        // node q's own stencil size (per-node plans search only that many; row q of nbr is
+        // padded with -1 beyond it)
+        const int nq = node_n ? node_n[q] : n;
+        int r = first_ring<D>(g, c0, nq, cell_start), cnt = 0;
         bool all = false;
         for (;;) {  // collect the candidates inside the guaranteed radius of ring r
             int clo[3], chi[3];
@@ -456,17 +459,17 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
                 }
                 __syncwarp();  // soff/sbeg are rewritten by the next group
             }
-            if (cnt > kCollect || cnt >= n || all) break;
+            if (cnt > kCollect || cnt >= nq || all) break;
             ++r;
         }
         const unsigned long long* rk;
         const int* ri;
         if (cnt > kCollect) {  // too many candidates to sort: stream them
             __syncwarp();
-            const int cur = knn_stream<D>(g, xq, c0, r, n, cell_start, sorted_idx, sorted_X, wk,
+            const int cur = knn_stream<D>(g, xq, c0, r, nq, cell_start, sorted_idx, sorted_X, wk,
                                           wi, wk + 2 * n, wi + 2 * n);
-            rk = wk + cur * n;
-            ri = wi + cur * n;
+            rk = wk + cur * nq;
+            ri = wi + cur * nq;
         } else {
             int P = 32;
             while (P < cnt) P <<= 1;
@@ -491,20 +494,21 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
             rk = wk;
             ri = wi;
         }
-        // write the stencil (the first nq of the n nearest), its width and retention ball
-        const int nq = node_n ? node_n[q] : n;
+        // write the stencil (the nq nearest), its width and retention ball
         const double r2k = __longlong_as_double((long long)rk[nq - 1]);
         const double rball = __dmul_rn(omd2, r2k);
         int blen = 0;
         for (int t0 = 0; t0 < n; t0 += 32) {
             const int t = t0 + lane;
             bool inb = false;
-            if (t < n) {
+            if (t < nq) {
                 const int id = ri[t];
                 const double dd = __longlong_as_double((long long)rk[t]);
                 nbr[(size_t)q * n + t] = id;
-                inb = t < nq && dd <= rball;
+                inb = dd <= rball;
                 if (t >= 1 && dd == 0.0) set_error(ctr, RBFFD_EDUPLICATE);
+            } else if (t < n) {
+                nbr[(size_t)q * n + t] = -1;
             }
             blen += __popc(__ballot_sync(0xffffffffu, inb));
         }

@@ -425,6 +425,16 @@ def check_mixed_rows(X, g, ref, n_node, ell_node, m_node, per_class=25, seed=99,
     return summary
 
 
+def assert_stencils_equal(g_nbr, ref_nbr, n_node):
+    """Per-node stencils: row k's first n_k entries equal the oracle's kNN order (the GPU
+    searches only that many neighbours for node k) and the rest of the row is -1."""
+    ref_nbr = np.asarray(ref_nbr)
+    g = np.asarray(g_nbr).reshape(ref_nbr.shape)
+    inside = np.arange(ref_nbr.shape[1])[None, :] < np.asarray(n_node)[:, None]
+    assert np.array_equal(g[inside], ref_nbr[inside])
+    assert np.all(g[~inside] == -1)
+
+
 @pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
 def test_mixed_degrees_3d_match_the_mixed_oracle(mode):
     X = NS.cube3d_clustered(3000, seed=4)
@@ -432,7 +442,7 @@ def test_mixed_degrees_3d_match_the_mixed_oracle(mode):
     g = gpu_run_mixed(X, n_node, ell_node, m_node, 0.3, mode)
     ref = O.assemble_mixed(X, n_node, ell_node, m_node, 0.3, mode)
     assert ref["stats"]["n_near_tie"] == 0
-    assert np.array_equal(g["nbr"], ref["nbr"])
+    assert_stencils_equal(g["nbr"], ref["nbr"], n_node)
     assert np.array_equal(g["owner"], ref["owner"])
     assert np.array_equal(g["is_center"], ref["is_center"])
     assert np.array_equal(g["row_ptr"], ref["row_ptr"])
@@ -451,7 +461,8 @@ def test_mixed_degrees_3d_N20000_match_the_mixed_oracle(mode):
     g = gpu_run_mixed(X, n_node, ell_node, m_node, 0.3, mode)
     ref = O.assemble_mixed(X, n_node, ell_node, m_node, 0.3, mode)
     assert ref["stats"]["n_near_tie"] == 0
-    for key in ("nbr", "owner", "is_center", "row_ptr", "col"):
+    assert_stencils_equal(g["nbr"], ref["nbr"], n_node)
+    for key in ("owner", "is_center", "row_ptr", "col"):
         assert np.array_equal(g[key], ref[key]), key
     check_mixed_rows(X, g, ref, n_node, ell_node, m_node)
     assert g["stats"]["n_fallback"] == ref["stats"]["n_fallback"]
