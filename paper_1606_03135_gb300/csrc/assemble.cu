@@ -429,13 +429,15 @@ __device__ __forceinline__ void forward_subst_warp(int K, const StencilSmem& sm,
 }
 
 // Blocked triangular solves of the columns 0 .. q-1 of sm.X with the whole team, 32 unknowns
-// at a time, for teams that hold one system per SM (512 threads): a warp solves a column's
-// diagonal block (lanes keep x in registers, each pivot's value by a shuffle), then every
-// thread updates the column's remaining rows with that block in pivot order.  On GB300 a warp
-// issues FP64 instructions to one quarter of the SM's FP64 units only, so a triangular solve
-// by a single warp runs at a quarter of the SM's rate; here the rows' updates spread over all
-// four.  Each entry receives the same FMAs in the same order as in the step-by-step forms
-// (forward_subst; the back substitution of ldlt_solve_tail), so results are bit-identical.
+// at a time, for teams that hold one to four systems per SM (256 and 512 threads): a warp
+// solves a column's diagonal block (lanes keep x in registers, each pivot's value by a
+// shuffle), then every thread updates the column's remaining rows with that block in pivot
+// order.  On GB300 a warp issues FP64 instructions to one quarter of the SM's FP64 units
+// only, so a triangular solve by a single warp runs at a quarter of the SM's rate when few
+// systems share the SM; here the rows' updates spread over all four.  (With ten or more
+// systems per SM the step-by-step forms keep the pipe busier.)  Each entry receives the same
+// FMAs in the same order as in the step-by-step forms (forward_subst; the back substitution
+// of ldlt_solve_tail), so results are bit-identical.
 
 // Forward substitution with the unit lower factor (a block never splits a 2x2 pivot).
 template <int NT>
@@ -527,7 +529,7 @@ __device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem&
     // flattened (row, column) pairs keep the lanes busy) with a barrier per step.  Both do
     // the same operations on every element.
     constexpr int NW = NT / 32;
-    if (q <= NW && NT != 512) {
+    if (q <= NW && NT < 256) {
         if (wid < q) {
             double* Xc = X + wid;
             for (int i = lane; i < K; i += 32) {
@@ -566,7 +568,7 @@ __device__ __forceinline__ void ldlt_solve_tail(int K, int q, const StencilSmem&
         }
     }
     __syncthreads();
-    if constexpr (NT == 512) {
+    if constexpr (NT >= 256) {
         back_subst_blocked<NT>(K, q, sm);
         return;
     }
@@ -1109,7 +1111,7 @@ __device__ void refine_columns(const SolveArgs& a, const Shape& sh, int c0, int 
         sm.X[r * xs + c] = sm.X[r * xs + c] - ((__ldcg(P) + __ldcg(P + st)) + (__ldcg(P + 2 * st) + __ldcg(P + 3 * st)));
     }
     __syncthreads();
-    if (NT == 512) {  // forward substitution
+    if (NT >= 256) {  // forward substitution
         forward_subst_blocked<NT>(K, qk, sm);
     } else if (qk <= NW) {  // a warp per column with warp synchronisation only
         if (wid < qk) forward_subst_warp(K, sm, sm.X + wid, xs);
@@ -1144,7 +1146,7 @@ __device__ __forceinline__ void solve_chunk(const SolveArgs& a, const Shape& sh,
                                             const StencilSmem& sm, int j) {
     chunk_rhs<D, NT>(sh, c0, qk, sm, a.fma_r2 != 0);
     __syncthreads();
-    if constexpr (NT == 512) forward_subst_blocked<NT>(sh.K, qk, sm);
+    if constexpr (NT >= 256) forward_subst_blocked<NT>(sh.K, qk, sm);
     else forward_subst<NT>(sh.K, qk, sm);
     ldlt_solve_tail<NT>(sh.K, qk, sm);
     if constexpr (team_refines(NT)) {

@@ -608,21 +608,22 @@ def test_centroid_reference_at_the_largest_stencil_size():
 
 
 @pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
-def test_blocked_triangular_solves_of_512_thread_teams_are_bitwise_equal(mode):
-    """512-thread teams take the triangular solves 32 unknowns at a time with all warps (the
-    back substitution always, the forward substitution for chunks after the first); every
-    entry gets the same FMAs in the same order as the step-by-step solves of a warp team."""
+def test_blocked_triangular_solves_of_large_teams_are_bitwise_equal(mode):
+    """256- and 512-thread teams take the triangular solves 32 unknowns at a time with all
+    warps (the back substitution always, the forward substitution for chunks after the first);
+    every entry gets the same FMAs in the same order as the step-by-step solves of a warp
+    team.  (512-thread teams also look one pivot ahead in the factorization.)"""
     for X, n, ell, m in ((NS.disk2d(3000, seed=4), 31, 4, 7),
                          (NS.ball3d(3000, seed=5), 45, 3, 7),
                          (NS.jittered_grid(40, 2, seed=21), 128, 5, 5)):
         a = gpu_run(X, n, ell, m, 0.3, mode, team=32)
-        for chunk in (0, 2):
-            b = gpu_run(X, n, ell, m, 0.3, mode, team=512, rhs_chunk=chunk)
+        for team, chunk in ((512, 0), (512, 2), (256, 0), (256, 2)):
+            b = gpu_run(X, n, ell, m, 0.3, mode, team=team, rhs_chunk=chunk)
             for key in ("row_ptr", "col", "val", "owner", "is_center", "lam_row"):
-                assert np.array_equal(a[key], b[key]), (key, n, chunk)
+                assert np.array_equal(a[key], b[key]), (key, n, team, chunk)
 
 
-@pytest.mark.parametrize("team,chunk", [(32, 0), (64, 3), (512, 0), (512, 2)])
+@pytest.mark.parametrize("team,chunk", [(32, 0), (64, 3), (256, 0), (256, 3), (512, 0), (512, 2)])
 def test_refined_schedules_are_bitwise_equal(team, chunk):
     """The refinement step does the same arithmetic on every entry whatever the team size or
     chunk (a warp per column or per residual entry), so refined results agree bit for bit."""
