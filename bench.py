@@ -670,7 +670,10 @@ def run_serve_config(args):
 
     out = {"config": {"workload": f"serve{count}: d in {{2,3}}, N log-uniform [1k,200k], "
                                   "ell 2..5, n=2M+1, delta U[0.2,1]", "hbm_budget_gb": 40,
-                      "slots": args.slots}, "saturated": {}, "poisson": {}}
+                      "slots": args.slots,
+                      "overlap": "full traversal grids; with several slots a job's CTAs leave "
+                                 "its dependency tail (elastic = SM count) for the next job"},
+           "saturated": {}, "poisson": {}}
     for j in jobs:
         j.arrival = 0.0
     for slots in (1, args.slots):
