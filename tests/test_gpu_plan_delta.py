@@ -76,3 +76,19 @@ def test_per_node_plans_for_other_deltas_equal_fresh_plans():
     with R.Plan(Xd, *params, 0.3, mode=R.STAB_FALLBACK) as f:
         b = run(f)
     same(a, b)
+
+
+def test_invalid_arguments_leave_no_plan():
+    X = torch.from_numpy(NS.disk2d(2000, seed=6)).cuda()
+    with R.Plan(X, 21, 3, 5, 1.0) as base:
+        for delta in (0.0, -0.5, 1.5, float("nan")):
+            rc, out = R.rbffd_plan_delta(base._plan, delta)
+            assert rc == R.EINVAL and not out.value, delta
+        bad = R.rbffd_opts(R.STAB_SEQ, 0, 5000, 1, 0, R.FACTOR_LDLT, 0, 48)  # no such team
+        rc, out = R.rbffd_plan_delta(base._plan, 0.5, bad)
+        assert rc == R.EINVAL and not out.value
+        with pytest.raises(R.RbffdError):
+            base.with_delta(2.0)
+        # the base plan is untouched and still assembles
+        base.assemble()
+        assert base.stats()["status"] == 0
