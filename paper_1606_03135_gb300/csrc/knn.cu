@@ -135,6 +135,13 @@ __device__ void set_grid_params(const double* L, const double* H, int N, int n, 
     double w = (D == 2) ? 3.14159265358979 : 4.18879020478639;
     double r = (D == 2) ? sqrt(n / (per * w)) : cbrt(n / (per * w));
     gp->r0 = (int)fmax(1.0, ceil(r));
+    // Coordinates rounded to FP32 are within 2^-24 |x| <= 2^-24 X (X = the largest coordinate
+    // magnitude) of the node's, plus 2^-149 where they fall below the normal range; the FP32
+    // difference of two of them rounds once more, by at most 2^-24 of its size (<= 2^-23 X).
+    // So |fl32(fl32(a) - fl32(b))| <= |a - b| + 2^-22 X (1 + 2^-20) + 2^-148.
+    double X = 0.0;
+    for (int a = 0; a < D; ++a) X = fmax(X, fmax(fabs(L[a]), fabs(H[a])));
+    gp->xerr = __double2float_ru(0x1p-22 * X * (1.0 + 0x1p-20) + 0x1p-148);
 }
 
 // Bounding box over all CTAs (integer keys, one set of atomics per CTA); the last CTA to
@@ -218,12 +225,17 @@ __global__ void k_cell_count(const double* __restrict__ X, int N, const GridPara
 template <int D>
 __global__ void k_cell_fill(const double* __restrict__ X, int N, const int* __restrict__ cell_of,
                             const int* __restrict__ cell_start, int* __restrict__ cursor,
-                            int* __restrict__ sorted_idx, double* __restrict__ sorted_X) {
+                            int* __restrict__ sorted_idx, double* __restrict__ sorted_X,
+                            float* __restrict__ sorted_Xf) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         int c = cell_of[i];
         int pos = cell_start[c] + atomicAdd(&cursor[c], 1);
         sorted_idx[pos] = i;
-        for (int a = 0; a < D; ++a) sorted_X[(size_t)pos * D + a] = X[(size_t)i * D + a];
+        for (int a = 0; a < D; ++a) {
+            const double x = X[(size_t)i * D + a];
+            sorted_X[(size_t)pos * D + a] = x;
+            sorted_Xf[(size_t)pos * D + a] = __double2float_rn(x);
+        }
     }
 }
 
@@ -238,7 +250,8 @@ __device__ __forceinline__ bool key_less(unsigned long long ka, int ia, unsigned
 // the box faces is larger, but admitting more candidates only makes the sort dearer.)
 template <int D>
 __device__ __forceinline__ bool ring_box(const GridParams& g, const double* xq, const int* c0,
-                                         int r, int* clo, int* chi, unsigned long long* bkey) {
+                                         int r, int* clo, int* chi, unsigned long long* bkey,
+                                         float* thr) {
     (void)xq;
     bool all = true;
     for (int a = 0; a < D; ++a) {
@@ -247,9 +260,31 @@ __device__ __forceinline__ bool ring_box(const GridParams& g, const double* xq, 
         all = all && clo[a] == 0 && chi[a] == g.dims[a] - 1;
     }
     const double rb = (double)r * g.h;
+    const double R2 = rb * rb * (1.0 - 1e-8);
     *bkey = dkey(all ? __longlong_as_double(0x7ff0000000000000LL)  // +inf
-                     : rb * rb * (1.0 - 1e-8));
+                     : R2);
+    // FP32 screen threshold (screen_outside): above R2 by more than the screen's rounding
+    *thr = all ? __int_as_float(0x7f800000) : __double2float_ru(R2 * (1.0 + 0x1p-19));
     return all;
+}
+
+// FP32 screen of a kNN candidate: true only if its squared distance to the query certainly
+// exceeds the ring's guaranteed radius R2, so its exact FP64 distance is not needed (the
+// candidate could not be collected).  Per axis t = max(0, |fl32(qf - pf)| - xerr) <= |dx| (1 +
+// 2^-24) (see xerr), and the sum of the t^2 in FP32 (three roundings at most, FMA) is at most
+// d^2 (1 + 2^-21); thr is R2 (1 + 2^-19) rounded up, so a screened-out candidate has d^2 > R2
+// and its FP64 key is not below the ring's key either.  Coordinates outside the FP32 range
+// give inf or NaN, which never screens out.
+template <int D>
+__device__ __forceinline__ bool screen_outside(const float* qf, const float* __restrict__ pf,
+                                               float xerr, float thr) {
+    float lb = 0.0f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float t = fmaxf(fabsf(__fsub_rn(qf[a], pf[a])) - xerr, 0.0f);
+        lb = __fmaf_rn(t, t, lb);
+    }
+    return lb > thr;
 }
 
 // First ring to search for a query: the radius that holds n nodes at the density of the
@@ -283,16 +318,18 @@ __device__ __forceinline__ int first_ring(const GridParams& g, const int* c0, in
 // counting, so the order is exact), growing the ring from r until n candidates lie inside the
 // guaranteed radius.  Returns the buffer (0 or 1) that holds the list.
 template <int D>
-__device__ int knn_stream(const GridParams& g, const double* xq, const int* c0, int r, int n,
-                          const int* __restrict__ cell_start, const int* __restrict__ sorted_idx,
-                          const double* __restrict__ sorted_X, unsigned long long* lk, int* li,
+__device__ int knn_stream(const GridParams& g, const double* xq, const float* xqf, const int* c0,
+                          int r, int n, const int* __restrict__ cell_start,
+                          const int* __restrict__ sorted_idx, const double* __restrict__ sorted_X,
+                          const float* __restrict__ sorted_Xf, unsigned long long* lk, int* li,
                           unsigned long long* bk, int* bi) {
     const int lane = threadIdx.x & 31;
     int cnt = 0, cur = 0;
     for (;;) {
         int clo[3], chi[3];
         unsigned long long bkey;
-        const bool all = ring_box<D>(g, xq, c0, r, clo, chi, &bkey);
+        float thr;
+        const bool all = ring_box<D>(g, xq, c0, r, clo, chi, &bkey, &thr);
         cnt = 0;
         cur = 0;
         const int ny = chi[1] - clo[1] + 1;
@@ -308,6 +345,8 @@ __device__ int knn_stream(const GridParams& g, const double* xq, const int* c0, 
                     bool valid = p < end;
                     unsigned long long key = ~0ull;
                     int id = 0x7fffffff;
+                    if (valid && screen_outside<D>(xqf, sorted_Xf + (size_t)p * D, g.xerr, thr))
+                        valid = false;
                     if (valid) {
                         double xp[3];
                         for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)p * D + a];
@@ -376,6 +415,7 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
                                              const int* __restrict__ cell_start,
                                              const int* __restrict__ sorted_idx,
                                              const double* __restrict__ sorted_X,
+                                             const float* __restrict__ sorted_Xf,
                                              int* __restrict__ nbr, double* __restrict__ rho2,
                                              int* __restrict__ ball_len, int* __restrict__ indeg,
                                              const int* __restrict__ node_n, DevCounters* ctr) {
@@ -386,15 +426,18 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
     const int W = knn_words(n);
     unsigned long long* wk = knn_smem + (size_t)wib * W;
     int* wi = reinterpret_cast<int*>(knn_smem + (size_t)wpb * W) + (size_t)wib * W;
-    int* soff = reinterpret_cast<int*>(knn_smem + (size_t)wpb * W) + (size_t)wpb * W + wib * 64;
+    int* soff = reinterpret_cast<int*>(knn_smem + (size_t)wpb * W) + (size_t)wpb * W + wib * 128;
     int* sbeg = soff + 32;
+    int* squeue = soff + 64;  // candidates that passed the FP32 screen, awaiting FP64 (< 64)
     const GridParams g = *gp;
 
     for (int q = blockIdx.x * wpb + wib; q < N; q += gridDim.x * wpb) {
         double xq[3];
+        float xqf[3];
         int c0[3];
         for (int a = 0; a < D; ++a) {
             xq[a] = X[(size_t)q * D + a];
+            xqf[a] = __double2float_rn(xq[a]);
             c0[a] = cell_coord<D>(g, xq[a], a);
         }
         const int kCollect = knn_collect_cap(n);
@@ -406,7 +449,8 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
         for (;;) {  // collect the candidates inside the guaranteed radius of ring r
             int clo[3], chi[3];
             unsigned long long bkey;
-            all = ring_box<D>(g, xq, c0, r, clo, chi, &bkey);
+            float thr;
+            all = ring_box<D>(g, xq, c0, r, clo, chi, &bkey, &thr);
             cnt = 0;
             const int ny = chi[1] - clo[1] + 1;
             const int nz = (D == 3) ? chi[2] - clo[2] + 1 : 1;
@@ -434,10 +478,15 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
                 soff[lane] = incl - len;
                 sbeg[lane] = beg;
                 __syncwarp();
+                // Each batch's candidates pass an FP32 screen first (screen_outside); those that
+                // may lie inside the guaranteed radius queue up, and their exact FP64 distances
+                // are formed a full warp at a time, so an FP64 instruction is issued only for
+                // candidates that can be collected.
+                int qn = 0;
                 for (int b0 = 0; b0 < total && cnt <= kCollect; b0 += 32) {
                     const int e = b0 + lane;
-                    unsigned long long key = ~0ull;
-                    int id = 0;
+                    bool pass = false;
+                    int p = 0;
                     if (e < total) {
                         int lo = 0, hi = 31;  // the last row whose offset is <= e (non-empty)
                         while (lo < hi) {
@@ -445,17 +494,38 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
                             if (soff[mid] <= e) lo = mid;
                             else hi = mid - 1;
                         }
-                        const int p = sbeg[lo] + (e - soff[lo]);
-                        double xp[3];
-                        for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)p * D + a];
-                        key = dkey(sqdist_rn<D>(xq, xp));
-                        id = sorted_idx[p];
+                        p = sbeg[lo] + (e - soff[lo]);
+                        pass = !screen_outside<D>(xqf, sorted_Xf + (size_t)p * D, g.xerr, thr);
                     }
-                    const bool in = e < total && key < bkey;
-                    const unsigned bal = __ballot_sync(0xffffffffu, in);
-                    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-                    if (in && pos < kCollect) { wk[pos] = key; wi[pos] = id; }
-                    cnt += __popc(bal);
+                    const unsigned pb = __ballot_sync(0xffffffffu, pass);
+                    if (pass) squeue[qn + __popc(pb & ((1u << lane) - 1u))] = p;
+                    qn += __popc(pb);
+                    __syncwarp();
+                    const bool last = b0 + 32 >= total;
+                    while (qn >= 32 || (last && qn > 0)) {
+                        const int m = min(qn, 32);
+                        unsigned long long key = ~0ull;
+                        int id = 0;
+                        if (lane < m) {
+                            const int pp = squeue[lane];
+                            double xp[3];
+                            for (int a = 0; a < D; ++a) xp[a] = sorted_X[(size_t)pp * D + a];
+                            key = dkey(sqdist_rn<D>(xq, xp));
+                            id = sorted_idx[pp];
+                        }
+                        const bool in = lane < m && key < bkey;
+                        const unsigned bal = __ballot_sync(0xffffffffu, in);
+                        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                        if (in && pos < kCollect) { wk[pos] = key; wi[pos] = id; }
+                        cnt += __popc(bal);
+                        __syncwarp();
+                        const int rest = qn - m;  // (< 32)
+                        const int moved = lane < rest ? squeue[m + lane] : 0;
+                        __syncwarp();
+                        if (lane < rest) squeue[lane] = moved;
+                        __syncwarp();
+                        qn = rest;
+                    }
                 }
                 __syncwarp();  // soff/sbeg are rewritten by the next group
             }
@@ -466,8 +536,8 @@ __global__ void __launch_bounds__(256) k_knn(const double* __restrict__ X, int N
         const int* ri;
         if (cnt > kCollect) {  // too many candidates to sort: stream them
             __syncwarp();
-            const int cur = knn_stream<D>(g, xq, c0, r, nq, cell_start, sorted_idx, sorted_X, wk,
-                                          wi, wk + 2 * n, wi + 2 * n);
+            const int cur = knn_stream<D>(g, xq, xqf, c0, r, nq, cell_start, sorted_idx, sorted_X,
+                                          sorted_Xf, wk, wi, wk + 2 * n, wi + 2 * n);
             rk = wk + cur * nq;
             ri = wi + cur * nq;
         } else {
@@ -577,6 +647,7 @@ size_t grid_scratch_bytes(int N, int D, int ncell_max) {
     b += 3 * round256((size_t)(ncell_max + 1) * sizeof(int));  // count, start, cursor
     b += 2 * round256((size_t)N * sizeof(int));                // cell_of, sorted_idx
     b += round256((size_t)N * D * sizeof(double));             // sorted_X
+    b += round256((size_t)N * D * sizeof(float));              // sorted_Xf (FP32 screen)
     return b;
 }
 
@@ -598,6 +669,7 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     int* cell_of = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
     int* sorted_idx = reinterpret_cast<int*>(take((size_t)N * sizeof(int)));
     double* sorted_X = reinterpret_cast<double*>(take((size_t)N * D * sizeof(double)));
+    float* sorted_Xf = reinterpret_cast<float*>(take((size_t)N * D * sizeof(float)));
 
     int rc;
     if ((rc = RB_CUDA(cudaMemsetAsync(acc, 0, sizeof(BBoxAcc), s))) ||
@@ -613,17 +685,18 @@ static int grid_and_knn(const double* X, int N, int n, double omd2, void* scratc
     k_grid_params<D><<<nb < sms ? nb : sms, tb, 0, s>>>(X, N, n, ncell_max, acc, gp);
     k_cell_count<D><<<nb, tb, 0, s>>>(X, N, gp, cell_of, count);
     k_scan<int, int><<<1, 1024, 0, s>>>(count, start, ncell_max, &gp->ncell);
-    k_cell_fill<D><<<nb, tb, 0, s>>>(X, N, cell_of, start, cursor, sorted_idx, sorted_X);
+    k_cell_fill<D><<<nb, tb, 0, s>>>(X, N, cell_of, start, cursor, sorted_idx, sorted_X,
+                                     sorted_Xf);
     const int wpb = 8;
     const int words = knn_words(n);
-    size_t smem = (size_t)wpb * (words * (sizeof(unsigned long long) + sizeof(int)) + 64 * sizeof(int));
+    size_t smem = (size_t)wpb * (words * (sizeof(unsigned long long) + sizeof(int)) + 128 * sizeof(int));
     if (smem > 48 * 1024 &&
         (rc = RB_CUDA(cudaFuncSetAttribute(k_knn<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem))))
         return rc;
     int blocks = (N + wpb - 1) / wpb;
-    k_knn<D><<<blocks, wpb * 32, smem, s>>>(X, N, n, omd2, gp, start, sorted_idx, sorted_X, nbr,
-                                            rho2, ball_len, indeg, node_n, ctr);
+    k_knn<D><<<blocks, wpb * 32, smem, s>>>(X, N, n, omd2, gp, start, sorted_idx, sorted_X,
+                                            sorted_Xf, nbr, rho2, ball_len, indeg, node_n, ctr);
     *launches += 5;
     return RB_LAUNCHED(__func__);
 }

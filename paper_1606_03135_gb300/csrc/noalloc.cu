@@ -18,7 +18,8 @@ constexpr int kMaxCells = 2 * kMaxNodes + 64;  // the cell-grid bound rbffd_plan
 // grid scratch for the largest case (3D) + in-degree counts + device status block
 constexpr size_t kGridBytes = r256(sizeof(GridParams)) + r256(sizeof(BBoxAcc)) +
                               3 * r256((size_t)(kMaxCells + 1) * 4) +
-                              2 * r256((size_t)kMaxNodes * 4) + r256((size_t)kMaxNodes * 3 * 8);
+                              2 * r256((size_t)kMaxNodes * 4) + r256((size_t)kMaxNodes * 3 * 8) +
+                              r256((size_t)kMaxNodes * 3 * 4);
 constexpr size_t kIndegBytes = r256((size_t)kMaxNodes * 4);
 constexpr size_t kScratchBytes = kGridBytes + kIndegBytes + r256(sizeof(DevCounters));
 

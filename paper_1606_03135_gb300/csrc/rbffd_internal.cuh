@@ -38,6 +38,7 @@ struct GridParams {
     int dims[3];
     int ncell;
     int r0;        // first search ring (in cells)
+    float xerr;    // FP32 screen of the kNN: bound on |fl32(fl32(a) - fl32(b))| - |a - b|
 };
 
 // Bounding-box accumulators of the grid build (zeroed before the launch): nlo holds the

@@ -131,6 +131,21 @@ def test_raster_order_has_deep_dependency_chains():
     compare(X, 31, 4, 7, 0.5)
 
 
+@pytest.mark.parametrize("scale,offset", [(1.0, 0.0), (1e-40, 0.0), (1e-20, 5e-20), (1e20, 0.0),
+                                          (1e150, 0.0), (1.0, 1e6)])
+def test_knn_is_exact_at_any_scale_and_offset(scale, offset):
+    """The kNN screens candidates in FP32 before their exact FP64 distances: coordinates that
+    are FP32 subnormals (1e-40), beyond FP32's range (1e150) or far from the origin (1e6)
+    must still give the oracle's stencils and widths bit for bit."""
+    for X0, n in ((NS.disk2d(2000, seed=11), 21), (NS.ball3d(2000, seed=12), 30)):
+        X = X0 * scale + offset
+        nbr, d2 = O.knn(X, n)
+        with R.Plan(torch.from_numpy(X).cuda(), n, 2, 3, 0.5) as p:
+            g_nbr, rho2, _ = p.export_stencils()
+        assert np.array_equal(g_nbr, nbr), (scale, offset, X.shape[1])
+        assert np.array_equal(rho2, d2[:, -1]), (scale, offset, X.shape[1])
+
+
 def test_lattice_with_exact_distance_ties():
     # exact ties in distance are broken by index on both sides
     P = np.array([[i, j] for i in range(30) for j in range(30)], dtype=np.float64) * 0.125
