@@ -1029,8 +1029,8 @@ __device__ __forceinline__ double neumann_value(const SolveArgs& a, const Shape&
 
 // Team sizes whose traversal kernels carry the refinement step: the 96- and 128-thread teams
 // run with 40 registers for small systems (many per SM), and the planner gives plans that
-// refine (largest system K >= 100, at most a few per SM) 512-thread teams, or 32 or 64 when
-// forced.  The fallback kernel carries it at every team size (ALL_TEAMS).
+// refine (largest system K >= 100, at most a few per SM) 256- or 512-thread teams, or 32 or
+// 64 when forced.  The fallback kernel carries it at every team size (ALL_TEAMS).
 __host__ __device__ constexpr bool team_refines(int nt) { return nt != 96 && nt != 128; }
 
 // Per-CTA scratch of the refinement step of this launch, or nullptr when the plan refines
@@ -1857,10 +1857,11 @@ static int fallback_occupancy(int nt, size_t smem, int* per_sm) {
     return RBFFD_OK;
 }
 
-// Team size for a launch when none is forced: 128 threads when several stencils fit an SM's
-// shared memory, else 512 so that the one or few resident stencils still keep enough warps
-// busy.  The LDL^T traversal takes 96 threads instead of 128 unless that keeps fewer stencils
-// resident: more stencils in flight hide more of each one's serial pivot steps (2D, K = 46,
+// Team size for a launch when none is forced: 128 threads when more than four stencils fit an
+// SM's shared memory, 256 when two to four fit (LDL^T), else 512 so that the one resident
+// stencil still keeps enough warps busy.  The LDL^T traversal takes 96 threads instead of 128
+// unless that keeps fewer stencils resident: more stencils in flight hide more of each one's
+// serial pivot steps (2D, K = 46,
 // 13 columns: 13 stencils of 96 threads beat 12 of 128 by 7%), and at equal residency the
 // smaller team wastes fewer lanes in its short steps (2D, 21 columns: 1.11 against 1.17 ms;
 // 3D, K = 65, one column: 15.5 against 15.7 ms).  A
