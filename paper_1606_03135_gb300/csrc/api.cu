@@ -97,7 +97,7 @@ namespace {
 
 // One stream-ordered memory pool per device, owned by the library, that keeps freed blocks
 // cached (release threshold = unlimited): repeated plans on a device reuse memory without
-// returning to the driver.
+// handing it back to the CUDA runtime.
 constexpr int kMaxDevices = 64;
 std::mutex g_pool_mu;
 cudaMemPool_t g_pool[kMaxDevices] = {};
