@@ -548,7 +548,8 @@ int plan_impl(const double* nodes, int64_t N, int d, int n, int ell, int m,
             auto sq32 = [](long long K) { return (K * K + 31) / 32 * 32; };
             const long long K = p->K;
             p->rs_x0 = (int)sq32(K);
-            p->rs_stride = (p->rs_x0 + 5 * K * p->qcap + 31) / 32 * 32;
+            // (+ K qcap + qcap: the moved block of refine_kept_columns)
+            p->rs_stride = (p->rs_x0 + 6 * K * p->qcap + p->qcap + 31) / 32 * 32;
             long long doubles = (long long)p->lp.grid * p->rs_stride;
             for (int c = 0; c < p->lp.n_fb; ++c) {
                 FallbackClass& f = p->lp.fb[c];

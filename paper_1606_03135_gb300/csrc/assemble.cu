@@ -1128,6 +1128,91 @@ __device__ void refine_columns(const SolveArgs& a, const Shape& sh, int c0, int 
     __syncthreads();
 }
 
+// The refinement step for the columns that can be kept (refine_columns on a subset).  With a
+// Lebesgue test (SEQ, FALLBACK) a column whose first solution's Lebesgue value exceeds the
+// test's reference value by more than 2^-10 of it fails the test whatever the refinement does
+// (a step changes the values by far less on the systems it is for: about the condition number
+// times the rounding, below 1e-5), and its weights are discarded; only the center, the
+// reference column and the other columns are refined.  They are moved to the front of the
+// right-hand-side block (and sm.cols with them), refined there and moved back; each column's
+// arithmetic does not depend on the others, so a kept column gets the same bits as when every
+// column is refined.  cref is the reference column (0, or 1 with the centroid option); the
+// chunk's unrefined Lebesgue values are left in sm.lam for the caller to recompute.  The
+// scratch slot holds the moved block after the refinement's own arrays (6 K q_cap + q_cap).
+template <int D, int NT>
+__device__ void refine_kept_columns(const SolveArgs& a, const Shape& sh, int c0, int qk,
+                                    const StencilSmem& sm, double* __restrict__ gA, int cref,
+                                    int j) {
+    __syncthreads();
+    if (a.refine_all == 0 && s_pivot_log2_ratio < kRefinePivotLog2) return;
+    double* gX0 = gA + a.rs_x0;
+    if (a.mode == RBFFD_STAB_OFF || qk == 1) {
+        refine_columns<D, NT>(a, sh, c0, qk, sm, gA, gX0, 0, j);
+        return;
+    }
+    const int K = sh.K, xs = sm.xs, tid = threadIdx.x;
+    lebesgue_values<NT>(sh.n, K, qk, sm, c0);
+    __syncthreads();
+    // the selection, in column order, by warp 0: kept columns first (map[c'] = column of
+    // position c'); sm.keep[c0 ..] serves as the map (the test writes it afterwards)
+    __shared__ int s_qr;
+    unsigned char* map = sm.keep + c0;
+    if (tid < 32) {
+        const double lref = sm.lam[cref];
+        const double lim = lref * (1.0 + 0x1p-10);
+        int nsel = 0;
+        for (int b = 0; b < qk; b += 32) {  // selected columns, in order
+            const int c = b + tid;
+            const bool sel = c < qk && (c0 + c == 0 || c0 + c == cref || sm.lam[c0 + c] <= lim);
+            const unsigned bal = __ballot_sync(0xffffffffu, sel);
+            if (sel) map[nsel + __popc(bal & ((1u << tid) - 1u))] = (unsigned char)c;
+            nsel += __popc(bal);
+        }
+        int nrest = nsel;
+        for (int b = 0; b < qk; b += 32) {  // then the others, in order
+            const int c = b + tid;
+            const bool sel = c < qk && (c0 + c == 0 || c0 + c == cref || sm.lam[c0 + c] <= lim);
+            const bool other = c < qk && !sel;
+            const unsigned bal = __ballot_sync(0xffffffffu, other);
+            if (other) map[nrest + __popc(bal & ((1u << tid) - 1u))] = (unsigned char)c;
+            nrest += __popc(bal);
+        }
+        if (tid == 0) s_qr = nsel;
+    }
+    __syncthreads();
+    const int qr = s_qr;
+    if (qr == qk) {
+        refine_columns<D, NT>(a, sh, c0, qk, sm, gA, gX0, 0, j);
+        return;
+    }
+    double* gT = gX0 + (size_t)5 * K * qk;   // the block in the new column order
+    int* gC = reinterpret_cast<int*>(gT + (size_t)K * qk);  // sm.cols of the chunk, saved
+    for (int e = tid; e < K * qk; e += NT) {
+        const int c = e / K, r = e - c * K;
+        gT[e] = sm.X[r * xs + map[c]];
+    }
+    for (int c = tid; c < qk; c += NT) gC[c] = sm.cols[c0 + c];
+    __syncthreads();
+    for (int e = tid; e < K * qr; e += NT) {
+        const int c = e / K, r = e - c * K;
+        sm.X[r * xs + c] = __ldcg(gT + e);
+    }
+    for (int c = tid; c < qk; c += NT) sm.cols[c0 + c] = __ldcg(gC + map[c]);
+    __syncthreads();
+    refine_columns<D, NT>(a, sh, c0, qr, sm, gA, gX0, 0, j);  // (ends with a barrier)
+    for (int e = tid; e < K * qr; e += NT) {  // the refined columns over their first solutions
+        const int c = e / K, r = e - c * K;
+        gT[e] = sm.X[r * xs + c];
+    }
+    __syncthreads();
+    for (int e = tid; e < K * qk; e += NT) {  // back to the original order
+        const int c = e / K, r = e - c * K;
+        sm.X[r * xs + map[c]] = __ldcg(gT + e);
+    }
+    for (int c = tid; c < qk; c += NT) sm.cols[c0 + c] = __ldcg(gC + c);
+    __syncthreads();
+}
+
 // The assembled symmetric matrix (packed lower triangle in shared memory) to gA in full,
 // row-major K x K, before the factorization overwrites it.
 template <int NT>
@@ -1143,7 +1228,7 @@ __device__ __forceinline__ void copy_full_matrix(int K, const StencilSmem& sm, d
 // the first of a center).
 template <int D, int NT>
 __device__ __forceinline__ void solve_chunk(const SolveArgs& a, const Shape& sh, int c0, int qk,
-                                            const StencilSmem& sm, int j) {
+                                            const StencilSmem& sm, int j, int cref) {
     chunk_rhs<D, NT>(sh, c0, qk, sm, a.fma_r2 != 0);
     __syncthreads();
     if constexpr (NT >= 256) forward_subst_blocked<NT>(sh.K, qk, sm);
@@ -1151,15 +1236,16 @@ __device__ __forceinline__ void solve_chunk(const SolveArgs& a, const Shape& sh,
     ldlt_solve_tail<NT>(sh.K, qk, sm);
     if constexpr (team_refines(NT)) {
         if (double* gA = refine_scratch<NT>(a))
-            refine_columns<D, NT>(a, sh, c0, qk, sm, gA, gA + a.rs_x0, 0, j);
+            refine_kept_columns<D, NT>(a, sh, c0, qk, sm, gA, cref, j);
     }
+    __syncthreads();
     lebesgue_values<NT>(sh.n, sh.K, qk, sm, c0);
 }
 
 // Assemble, factor and solve the first q columns of stencil j (refined when its shape asks).
 template <int D, bool PACKED, int NT>
 __device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
-                            const StencilSmem& sm) {
+                            const StencilSmem& sm, int cref) {
     assemble_local<D, PACKED, NT>(a, sh, j, q, sm);
     if constexpr (!PACKED) {
         return factor_solve_lu<NT>(sh.K, q, sm);
@@ -1168,7 +1254,7 @@ __device__ bool solve_local(const SolveArgs& a, const Shape& sh, int j, int q,
         if (gA) copy_full_matrix<NT>(sh.K, sm, gA);
         if (!factor_solve_ldlt<NT, team_refines(NT)>(sh.K, q, sm)) return false;
         if constexpr (team_refines(NT)) {
-            if (gA) refine_columns<D, NT>(a, sh, 0, q, sm, gA, gA + a.rs_x0, 0, j);
+            if (gA) refine_kept_columns<D, NT>(a, sh, 0, q, sm, gA, cref, j);
         }
         return true;
     }
@@ -1450,7 +1536,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
             for (int c = tid; c < q; c += NT) sm.lam[c] = __ldcg(&a.slot_lam[base + sm.cols[c]]);
         } else {
             const int q1 = CHUNKED ? min(q, a.qcap) : q;
-            ok = solve_local<D, PACKED, NT>(a, sh, j, q1, sm);
+            ok = solve_local<D, PACKED, NT>(a, sh, j, q1, sm, s_ref);
             if (ok) lebesgue_values<NT>(n, sh.K, q1, sm);
         }
         __syncthreads();
@@ -1503,7 +1589,7 @@ __global__ void __launch_bounds__(NT, team_min_blocks(NT)) k_traversal(SolveArgs
                 const int qk = min(qc, q - c0);
                 __syncthreads();  // sm.X is read until here
                 // (the shape is read again rather than kept in registers)
-                if (ok) solve_chunk<D, NT>(a, shape_of<D>(a, sbasis, j), c0, qk, sm, j);
+                if (ok) solve_chunk<D, NT>(a, shape_of<D>(a, sbasis, j), c0, qk, sm, j, s_ref);
                 __syncthreads();
                 emit(c0, qk);
             }
