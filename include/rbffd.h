@@ -99,7 +99,11 @@ typedef struct {
                            in FP64 with the assembled system (copied to the plan's assembly
                            memory before the factorization: one full K x K copy per resident
                            CTA) and the correction is solved with
-                           the stored factors (about 4 K^2 flops per refined column).  The
+                           the stored factors (about 4 K^2 flops per refined column).  With a
+                           Lebesgue test (SEQ, FALLBACK) a column whose first Lebesgue value
+                           exceeds the test's reference by more than 2^-10 of it is not
+                           refined: it fails the test either way and its weights are
+                           discarded; the matrix is the same as with every column refined.  The
                            traversal's 96- and 128-thread teams have no refinement step, so
                            forcing them (opts.team) on a plan that refines is RBFFD_EINVAL.
                            RBFFD_FACTOR_LU is never refined.  Other values: RBFFD_EINVAL */
