@@ -484,6 +484,28 @@ def test_mixed_degrees_3d_N20000_match_the_mixed_oracle(mode):
     assert g["stats"]["refine_min_K"] == R.REFINE_MIN_K
 
 
+@pytest.mark.parametrize("mode", [R.STAB_SEQ, R.STAB_FALLBACK])
+def test_degree4_3d_plan_with_refinement_matches_the_oracle(mode):
+    """A uniform degree-4 3D plan (n = 71, K = 106, delta = 0.4): large-system teams, the
+    refinement step and, with a Lebesgue test in force, its selection of the columns that can
+    be kept, against the oracle (structure bit-exact, weights and Lebesgue values at the
+    double-double bar of check_mixed_rows)."""
+    X = NS.ball3d(3000, seed=7)
+    N, n, ell, m = X.shape[0], 71, 4, 7
+    g = gpu_run(X, n, ell, m, 0.4, mode)
+    ref = O.assemble(X, n, ell, m, 0.4, mode)
+    assert ref["stats"]["n_near_tie"] == 0
+    for key in ("nbr", "owner", "is_center", "row_ptr", "col"):
+        assert np.array_equal(g[key], ref[key]), key
+    check_rows(g, ref, n)  # (these stencils are well enough conditioned for 1e-9)
+    check_mixed_rows(X, g, ref, np.full(N, n), np.full(N, ell), np.full(N, m), per_class=100)
+    assert g["stats"]["refine_min_K"] == R.REFINE_MIN_K and g["stats"]["flops_refine"] > 0
+    assert g["stats"]["n_fallback"] == ref["stats"]["n_fallback"]
+    # the kept-column selection refines fewer columns than refining every solved one
+    a = gpu_run(X, n, ell, m, 0.4, mode, refine=R.REFINE_ALL)
+    assert g["stats"]["flops_refine"] < a["stats"]["flops_refine"]
+
+
 def test_refinement_options_on_per_node_stencils():
     """Refinement changes weights only (rounding), never the structure: with every system
     refined, only the ill-conditioned ones (the default) or none, the matrices share their
