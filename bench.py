@@ -494,7 +494,7 @@ def run_mixed_config(args, steps=3, warmup=1):
     import torch
     from paper_1606_03135_gb300 import nodesets as NS
     from paper_1606_03135_gb300 import rbffd as R
-    name = MIXED
+    name = args.workload if args.workload in NS.MIXED_WORKLOADS else MIXED
     w = NS.MIXED_WORKLOADS[name]
     X = w["gen"](**w["kw"])
     n_node, ell_node, m_node = NS.mixed_degree_params(X, w["ells"])
@@ -770,7 +770,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload in ("serve", "batch", MIXED):
+    from paper_1606_03135_gb300 import nodesets as NS
+    if args.workload in ("serve", "batch") or args.workload in NS.MIXED_WORKLOADS:
         import torch
         from paper_1606_03135_gb300 import rbffd as R
         R.load()

@@ -262,6 +262,9 @@ WORKLOADS = {
 MIXED_WORKLOADS = {
     "cube3d_N500000_mixed_l2to5": dict(gen=cube3d_clustered, kw=dict(N=500000, seed=4), d=3,
                                        ells=(2, 3, 4, 5), deltas=(0.3,), mode="fallback"),
+    # the same recipe at a size for full ncu captures of its kernels
+    "cube3d_N20000_mixed_l2to5": dict(gen=cube3d_clustered, kw=dict(N=20000, seed=4), d=3,
+                                      ells=(2, 3, 4, 5), deltas=(0.3,), mode="fallback"),
 }
 
 
