@@ -40,7 +40,8 @@ def test_plans_for_other_deltas_equal_fresh_plans(case):
     Xd = torch.from_numpy(X).cuda()
     with R.Plan(Xd, n, ell, m, 1.0) as base:
         for delta, kw in ((0.5, {}), (0.3, dict(mode=R.STAB_FALLBACK)), (0.2, dict(team=32)),
-                          (1.0, {})):
+                          (1.0, {}), (0.5, dict(factor=R.FACTOR_LU)),
+                          (0.3, dict(lebesgue_ref=R.LREF_CENTROID))):
             with base.with_delta(delta, **kw) as q:
                 a = run(q)
             with R.Plan(Xd, n, ell, m, delta, **kw) as f:
@@ -92,3 +93,13 @@ def test_invalid_arguments_leave_no_plan():
         # the base plan is untouched and still assembles
         base.assemble()
         assert base.stats()["status"] == 0
+
+
+def test_a_base_built_from_host_nodes_gives_the_same_derived_plans():
+    X = NS.disk2d(3000, seed=4)
+    with R.Plan(X, 31, 4, 7, 1.0) as base:  # nodes copied from host memory
+        with base.with_delta(0.4) as q:
+            a = run(q)
+    with R.Plan(torch.from_numpy(X).cuda(), 31, 4, 7, 0.4) as f:
+        b = run(f)
+    same(a, b)
